@@ -1,0 +1,387 @@
+"""Benchmark: MLUPS and fraction of the HBM roofline of the stream-collide step.
+
+Workload (default): the turbulent channel of the paper's Sec. 5.1 benchmark class, as a
+synthetic stand-in: 512 x 256 x 256 cells, D3Q19 TRT + Smagorinsky (C_s = 0.1), float32
+populations, walls at the y faces, periodic x/z, body force for Re_tau ~ 180, initial
+state = equilibrium of the seeded perturbed parabola.  One step = one lattice update of
+every cell (one AA kernel launch).  MLUPS counts all cells, like the paper (Sec. 5.2).
+
+Roofline (Sec. 5.2, Eq. roofline: P_max = b_s / n_b): n_b = 2 q s + 1 bytes per update
+(q populations of s bytes read and written, one flag byte), b_s = the measured copy
+bandwidth of this GPU.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (under torchrun): every rank runs an independent replica (the method needs no
+exchange on one lattice per GPU; "replicas only"), barrier + max over ranks.
+--impl reference times the FP64 CPU oracle on the host cores on a bounded sample of the
+same workload (128 x 64 x 64 sub-lattice).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & % of HBM roofline per form (FP32/FP16/MLP closure) at stated error"
+FALLBACK_HBM_GBS = 6800.0
+WORKLOAD = "turbulent channel 512x256x256 D3Q19 TRT+Smagorinsky FP32 (AA in place)"
+FACES_CHANNEL = ("periodic", "periodic", "wall", "wall", "periodic", "periodic")
+
+
+def _peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def _profile_traffic(kernel_tag):
+    """Per-launch DRAM bytes from the committed ncu summary of this kernel, if it was taken
+    on the library build that is running now (same source hash); else None."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    try:
+        stamp = open(os.path.join(ROOT, "paper_2305_09910_gb300", "liblbm.so.sha256")).read().strip()
+    except OSError:
+        return None
+    if vals.get("library_sha256") != stamp:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.rows = []
+        self.proc = None
+        self.active = False
+        self.lock = threading.Lock()
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", gpu_id], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            with self.lock:
+                if self.active:
+                    self.rows.append([s.strip() for s in line.split(",")])
+
+    def start(self):
+        with self.lock:
+            self.active = True
+
+    def stop(self):
+        with self.lock:
+            self.active = False
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = [r for r in self.rows if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(num(r[2]) or 0 for r in rows),
+                "power_w_max": max(num(r[3]) or 0 for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return None, 0, 1, 0
+    import torch
+    import torch.distributed as dist
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    return dist, dist.get_rank(), ws, local
+
+
+def _barrier_max(dist, value):
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _channel_lattice(nx, ny, nz, precision, closure="smag"):
+    import torch
+
+    from paper_2305_09910_gb300 import inputs, lbm
+
+    par = inputs.channel_parameters(ny)
+    lat = lbm.Lattice(nx, ny, nz, stencil=19, tau=par["tau"], precision=precision, closure=closure,
+                      cs_smag=0.1, faces=FACES_CHANNEL)
+    lat.set_force(par["force"])
+    rho = torch.empty((nz, ny, nx), dtype=torch.float32, device="cuda")
+    u = torch.empty((3, nz, ny, nx), dtype=torch.float32, device="cuda")
+    step = max(1, nz // 8)
+    for z0 in range(0, nz, step):  # generate slab by slab to bound host memory
+        z1 = min(nz, z0 + step)
+        r, v = inputs.channel_init(nx, ny, nz, z_range=(z0, z1))
+        rho[z0:z1].copy_(torch.from_numpy(r))
+        u[:, z0:z1].copy_(torch.from_numpy(v))
+    lat.init_equilibrium(rho, u)
+    del rho, u
+    return lat, par
+
+
+def _time_steps(lat, steps, warmup, dist):
+    """Device time of `steps` single-launch steps (CUDA events on the handle's stream)."""
+    import torch
+
+    from paper_2305_09910_gb300 import lbm
+
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        lbm.lbm_step(lat.h, 1)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for k in range(steps):
+        starts[k].record(stream)
+        lbm.lbm_step(lat.h, 1)
+        ends[k].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    total_ms = t0.elapsed_time(t1)
+    per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    lat.sync()
+    return total_ms, per
+
+
+def _roofline(ncell, bytes_per_update, per_launch_ms, peak, peak_kind, traffic):
+    avg_s = statistics.mean(per_launch_ms) * 1e-3
+    achieved = ncell * bytes_per_update / avg_s / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic,
+            "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+            else "fallback 6.8 TB/s",
+            "bytes_per_update": bytes_per_update, "avg_launch_ms": round(avg_s * 1e3, 4)}
+
+
+def _cpu_baseline(target_s=12.0):
+    """The FP64 oracle on this host's cores, on a 128x64x64 sub-lattice of the channel."""
+    import numpy as np
+
+    import oracle
+    from paper_2305_09910_gb300 import inputs
+
+    nx, ny, nz = 128, 64, 64
+    par = inputs.channel_parameters(ny)
+    threads = os.cpu_count() or 1
+    ora = oracle.Oracle(nx, ny, nz, q=19, tau=par["tau"], closure="smag", cs=0.1,
+                        faces=FACES_CHANNEL, force=(par["force"], 0, 0))
+    rho, u = inputs.channel_init(nx, ny, nz)
+    ora.init_equilibrium(rho.astype(np.float64), u.astype(np.float64))
+    t = time.perf_counter()
+    ora.step(1, threads=threads)
+    one = max(time.perf_counter() - t, 1e-3)
+    steps = max(2, int(target_s / one))
+    t = time.perf_counter()
+    ora.step(steps, threads=threads)
+    dt = time.perf_counter() - t
+    mlups = nx * ny * nz * steps / dt / 1e6
+    return {"value": round(mlups, 3), "unit": "MLUPS", "cores": threads, "kind": "oracle",
+            "sample": f"FP64 oracle, channel {nx}x{ny}x{nz} D3Q19 TRT+Smagorinsky, {steps} steps "
+                      f"({dt:.1f} s, OpenMP over z)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_2305_09910_gb300 import inputs
+
+    nx, ny, nz = 128, 64, 64
+    par = inputs.channel_parameters(ny)
+    threads = os.cpu_count() or 1
+    ora = oracle.Oracle(nx, ny, nz, q=19, tau=par["tau"], closure="smag", cs=0.1,
+                        faces=FACES_CHANNEL, force=(par["force"], 0, 0))
+    rho, u = inputs.channel_init(nx, ny, nz)
+    ora.init_equilibrium(rho.astype(np.float64), u.astype(np.float64))
+    ora.step(args.warmup, threads=threads)
+    t = time.perf_counter()
+    ora.step(args.steps, threads=threads)
+    dt = time.perf_counter() - t
+    mlups = nx * ny * nz * args.steps / dt / 1e6
+    sample = (f"FP64 oracle on the host cores, channel sub-lattice {nx}x{ny}x{nz} (1/64 of the "
+              f"512x256x256 workload) D3Q19 TRT+Smagorinsky, {args.steps} timed steps")
+    line = {"impl": "reference", "metric": METRIC, "value": round(mlups, 3), "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " -- oracle sample 128x64x64", "parallelism": "host threads"},
+            "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": threads,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP16/BF16 forms")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    from paper_2305_09910_gb300 import build as lib_build
+    from paper_2305_09910_gb300 import lbm
+
+    dist, rank, world, local = _dist()
+    if rank == 0:
+        lib_build.build()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.set_device(local)
+    peak, peak_kind = _peak_hbm()
+    gpu_uuid = str(torch.cuda.get_device_properties(local).uuid)
+    gpu_id = gpu_uuid if gpu_uuid.startswith("GPU-") else f"GPU-{gpu_uuid}"
+
+    nx, ny, nz = 512, 256, 256
+    ncell = nx * ny * nz
+    lat, par = _channel_lattice(nx, ny, nz, "f32")
+    clocks = ClockSampler(gpu_id)
+    time.sleep(1.0)  # let nvidia-smi start
+    for _ in range(args.warmup):
+        lbm.lbm_step(lat.h, 1)
+    torch.cuda.synchronize()
+    clocks.start()
+    total_ms, per = _time_steps(lat, args.steps, 3, dist)
+    clocks.stop()
+    total_ms = _barrier_max(dist, total_ms)
+    value = world * ncell * args.steps / (total_ms * 1e-3) / 1e6
+    traffic = _profile_traffic("k_step_q19_f32_smag_channel512")
+    roof = _roofline(ncell, lat.bytes_per_update, per, peak, peak_kind, traffic)
+    mass = lat.reduce()[0]
+
+    # end to end through the C ABI with host buffers: upload (rho, u) from pinned memory,
+    # K steps, read the moments back to pinned memory
+    from paper_2305_09910_gb300 import inputs
+
+    rho_h = torch.empty((nz, ny, nx), dtype=torch.float32).pin_memory()
+    u_h = torch.empty((3, nz, ny, nx), dtype=torch.float32).pin_memory()
+    step = nz // 8
+    for z0 in range(0, nz, step):
+        r, v = inputs.channel_init(nx, ny, nz, z_range=(z0, z0 + step))
+        rho_h[z0:z0 + step].copy_(torch.from_numpy(r))
+        u_h[:, z0:z0 + step].copy_(torch.from_numpy(v))
+    rho_o = torch.empty_like(rho_h).pin_memory()
+    u_o = torch.empty_like(u_h).pin_memory()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t = time.perf_counter()
+    lbm.lbm_init_equilibrium(lat.h, rho_h, u_h)
+    lbm.lbm_step(lat.h, args.steps)
+    lbm.lbm_moments(lat.h, rho_o, u_o)
+    lat.sync()
+    e2e_s = _barrier_max(dist, time.perf_counter() - t)
+    e2e = {"value": round(world * ncell * args.steps / e2e_s / 1e6, 1), "unit": "MLUPS",
+           "h2d_bytes_per_step": int(16 * ncell / args.steps),
+           "d2h_bytes_per_step": int(16 * ncell / args.steps),
+           "what": "lbm_init_equilibrium from pinned host (rho,u) + K lbm_step + lbm_moments to pinned host"}
+    lat.close()
+
+    forms = {}
+    if not args.no_forms:
+        for prec in ("f16", "bf16"):
+            fl, _ = _channel_lattice(nx, ny, nz, prec)
+            ms, per_f = _time_steps(fl, max(50, args.steps // 4), args.warmup, None)
+            n = max(50, args.steps // 4)
+            forms[f"{prec}_shifted"] = {
+                "MLUPS": round(ncell * n / (ms * 1e-3) / 1e6, 1),
+                "roofline": _roofline(ncell, fl.bytes_per_update, per_f, peak, peak_kind, None)}
+            fl.close()
+
+    out = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "nx": nx, "ny": ny, "nz": nz, "stencil": 19,
+                      "tau": round(par["tau"], 6), "force": par["force"], "cs_smag": 0.1,
+                      "global_batch": world * ncell, "parallelism": f"replicas x{world}",
+                      "l2": "inputs larger than L2 (2.55 GB population array vs 129 MB L2)"},
+           "roofline": roof, "e2e": e2e, "gpu_launches": args.steps,
+           "clocks": clocks.summary(), "mass_after": mass, "forms": forms}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        out["cpu_baseline"] = _cpu_baseline()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

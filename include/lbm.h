@@ -1,0 +1,195 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) lattice Boltzmann stream-and-collide library.
+ *
+ * The library advances a D3Q19 or D3Q27 lattice with the lattice Boltzmann equation of
+ * arXiv 2305.09910, Sec. 2 (Eq. LBCollision: f*_i = f_i^eq + (1 - Omega) f_i^neq, a local
+ * collision; Eq. LBStreaming: f_i(x + c_i, t + 1) = f*_i(x, t), first-neighbour streaming).
+ * Like the generated kernels of Sec. 3, every entry point is a plain C function taking raw
+ * pointers, sizes and the remaining free parameters.
+ *
+ * Operators (the paper names the collision and boundary schemes without defining them;
+ * these are the readings implemented):
+ *   collision  two-relaxation-time (TRT): the symmetric part relaxes with omega+ = 1/tau_eff,
+ *              the antisymmetric part with omega- given by the magic parameter
+ *              Lambda = (1/omega+ - 1/2)(1/omega- - 1/2) (default 3/16);
+ *   forcing    Guo: F_i = w_i [3 (c_i - u) + 9 (c_i.u) c_i] . F, split into symmetric and
+ *              antisymmetric parts scaled by (1 - omega+/2) and (1 - omega-/2);
+ *              the velocity is u = (sum_i c_i f_i + F/2) / rho;
+ *   LES        Smagorinsky: tau_eff = (tau + sqrt(tau^2 + 18 sqrt(2) C_s^2 sqrt(Pi:Pi) / rho))/2,
+ *              Pi the non-equilibrium second moment; or a per-cell MLP giving C_s^2(x);
+ *   boundaries halfway bounce-back (SOLID cells, WALL faces), moving-wall bounce-back
+ *              f_i = f*_opp(i) + 6 w_i rho_w (c_i . u_w) (INFLOW cells and faces),
+ *              zero-gradient outflow on the +x face (the incoming populations of x = nx-1
+ *              equal those its upstream neighbour x = nx-2 receives), specular free-slip
+ *              faces, periodic faces.  A population whose source lies across several faces
+ *              follows the rule of highest precedence wall > inflow > outflow >
+ *              (free-slip, periodic); free-slip axes are reflected and periodic axes wrapped
+ *              independently, and the flag of the resolved cell then selects streaming or
+ *              (moving-wall) bounce-back.  These are the wind-tunnel boundaries of Sec. 5.2
+ *              (inflow on the left, outflow on the right).
+ *
+ * Velocity set order (both stencils; D3Q19 is the first 19 of D3Q27; opp(i) = i+1 for odd
+ * i, i-1 for even i > 0, opp(0) = 0):
+ *    0 ( 0, 0, 0)
+ *    1 ( 1, 0, 0)   2 (-1, 0, 0)   3 ( 0, 1, 0)   4 ( 0,-1, 0)   5 ( 0, 0, 1)   6 ( 0, 0,-1)
+ *    7 ( 1, 1, 0)   8 (-1,-1, 0)   9 ( 1,-1, 0)  10 (-1, 1, 0)  11 ( 1, 0, 1)  12 (-1, 0,-1)
+ *   13 ( 1, 0,-1)  14 (-1, 0, 1)  15 ( 0, 1, 1)  16 ( 0,-1,-1)  17 ( 0, 1,-1)  18 ( 0,-1, 1)
+ *   19 ( 1, 1, 1)  20 (-1,-1,-1)  21 ( 1, 1,-1)  22 (-1,-1, 1)  23 ( 1,-1, 1)  24 (-1, 1,-1)
+ *   25 (-1, 1, 1)  26 ( 1,-1,-1)
+ * Weights: D3Q19 1/3, 1/18, 1/36; D3Q27 8/27, 2/27, 1/54, 1/216 (by |c|^2 = 0, 1, 2, 3).
+ *
+ * Units and layouts: lattice units (dx = dt = 1, c_s^2 = 1/3).  Host or device arrays
+ * passed in are dense, x fastest: a scalar field is [nz][ny][nx]; a vector field is
+ * [3][nz][ny][nx]; populations are [q][nz][ny][nx] and hold SHIFTED values
+ * df_i = f_i - w_i in float32.  Inside the library populations are stored shifted in the
+ * chosen precision, SoA, [q][nz][ny][nxp] with x padded to nxp = a multiple of 32.
+ *
+ * Ownership and ordering: the library owns its device memory (populations, flags,
+ * scratch), allocated on the handle's stream.  The caller owns every pointer it passes in.
+ * All device work is ordered on the handle's stream (lbm_params.stream, a cudaStream_t;
+ * NULL = legacy default stream).  Calls that return data to host memory synchronise that
+ * stream before returning.  A handle must not be used from two threads at once.
+ *
+ * Errors: every call returns an lbm_status; lbm_last_error() gives a message for the last
+ * failing call on a handle.  A status of LBM_EUNSTABLE (a non-finite or non-positive
+ * density was seen by a step) leaves the state in place for inspection.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_ABI_VERSION 1
+
+typedef struct lbm_s* lbm_handle;
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_EINVAL = -1,      /* bad argument or configuration */
+  LBM_ENOMEM = -2,      /* device or pinned allocation failed */
+  LBM_ECUDA = -3,       /* a CUDA runtime call failed */
+  LBM_EUNSTABLE = -4,   /* a step produced a non-finite or non-positive density */
+  LBM_ESTATE = -5,      /* call not valid in the current state (e.g. no state yet) */
+  LBM_EUNSUPPORTED = -6 /* valid request this build does not implement */
+} lbm_status;
+
+/* storage precision of the populations (arithmetic is float32 in every case) */
+enum { LBM_F32 = 0, LBM_F16_SHIFTED = 1, LBM_BF16_SHIFTED = 2 };
+/* streaming pattern: AA in place (one population array) or two-grid pull */
+enum { LBM_AA = 0, LBM_PULL = 1 };
+/* relaxation-time closure */
+enum { LBM_CLOSURE_NONE = 0, LBM_CLOSURE_SMAG = 1, LBM_CLOSURE_MLP = 2 };
+/* face types, indexed -x, +x, -y, +y, -z, +z */
+enum {
+  LBM_FACE_PERIODIC = 0,
+  LBM_FACE_WALL = 1,
+  LBM_FACE_FREESLIP = 2,
+  LBM_FACE_INFLOW = 3,
+  LBM_FACE_OUTFLOW = 4 /* +x only; needs nx >= 2 and nx % 32 != 1 */
+};
+/* cell flags (uint8) */
+enum { LBM_CELL_FLUID = 0, LBM_CELL_SOLID = 1, LBM_CELL_INFLOW = 2 };
+
+/* MLP closure parameters: 7 -> 32 -> 32 -> 1, packed W1[32][7], b1[32], W2[32][32], b2[32],
+ * W3[32], b3 (bfloat16 bit patterns).  Features: Pi^neq_{xx,yy,zz,xy,xz,yz} * scale_pi and
+ * (rho - 1) * scale_rho.  C_s^2(x) = softplus(y) * cs_smag^2 / ln 2 (y = 0 gives cs_smag^2). */
+#define LBM_MLP_NPARAM 1345
+
+/* Number of doubles per y-plane in the turbulence statistics:
+ * count, Su_x, Su_y, Su_z, Su_x^2, Su_y^2, Su_z^2, Su_xu_y, Su_xu_z, Su_yu_z. */
+#define LBM_STATS_K 10
+
+typedef struct {
+  uint32_t struct_size; /* = sizeof(lbm_params); lets the ABI grow */
+  int32_t precision;    /* LBM_F32 (default) | LBM_F16_SHIFTED | LBM_BF16_SHIFTED */
+  int32_t streaming;    /* LBM_AA (default) | LBM_PULL */
+  int32_t closure;      /* LBM_CLOSURE_NONE (default) | _SMAG | _MLP */
+  double magic_lambda;  /* TRT Lambda, default 3/16 */
+  double cs_smag;       /* Smagorinsky constant (or the MLP's reference C_s0), default 0.1 */
+  int32_t face_bc[6];   /* LBM_FACE_*, default all periodic */
+  double u_inflow[3];   /* velocity of INFLOW faces and cells, default 0 */
+  double rho_inflow;    /* density used by moving-wall bounce-back, default 1 */
+  void* stream;         /* cudaStream_t for all work, default NULL */
+} lbm_params;
+
+/* Fills p with the defaults listed above. */
+void lbm_params_default(lbm_params* p);
+
+/* Host-only: the library's velocity set.  c: q*3 ints, w: q doubles (either may be NULL).
+ * Returns q, or 0 if q is not 19 or 27. */
+int lbm_stencil(int q, int* c, double* w);
+
+/* Creates a lattice of nx*ny*nz cells (all fluid, populations at rest equilibrium rho = 1)
+ * with stencil 19 or 27 and molecular relaxation time tau (> 1/2; nu = (tau - 1/2)/3).
+ * p may be NULL for the defaults.  Sec. 2 (problem statement).  Errors: EINVAL for bad
+ * sizes, stencil, tau, Lambda or face combination (periodic faces come in pairs); ENOMEM;
+ * EUNSUPPORTED for an outflow face the kernels cannot serve. */
+lbm_status lbm_create(int nx, int ny, int nz, int stencil, double tau, const lbm_params* p,
+                      lbm_handle* out);
+
+/* Frees all device memory of h (after its stream's work).  NULL is accepted. */
+lbm_status lbm_destroy(lbm_handle h);
+
+/* Cell flags, nx*ny*nz uint8 (LBM_CELL_*), x fastest; on_device != 0 if flags is a device
+ * pointer.  Other values give EINVAL.  Cells that become fluid keep whatever populations
+ * they held; call lbm_init_equilibrium or lbm_set_populations afterwards. */
+lbm_status lbm_set_flags(lbm_handle h, const uint8_t* flags, int on_device);
+
+/* Constant body-force density F (lattice units), used by every later step. */
+lbm_status lbm_set_force(lbm_handle h, double fx, double fy, double fz);
+
+/* Sets every fluid cell to f_i^eq(rho, u) (second-order equilibrium).  rho: N floats or
+ * NULL (rho = 1); u: 3*N floats [3][nz][ny][nx] or NULL (u = 0).  The reported velocity of
+ * the new state is u + F/(2 rho).  Clears the instability flag. */
+lbm_status lbm_init_equilibrium(lbm_handle h, const float* rho, const float* u, int on_device);
+
+/* Advances n >= 0 time steps (collision then streaming, Sec. 2).  Asynchronous: returns
+ * after enqueuing; instability is reported by lbm_sync. */
+lbm_status lbm_step(lbm_handle h, int64_t n);
+
+/* Waits for the handle's stream.  LBM_EUNSTABLE if any step since the last state reset saw a
+ * non-finite or non-positive density. */
+lbm_status lbm_sync(lbm_handle h);
+
+/* Moments of the current state: rho (N floats) and u (3*N floats, includes +F/(2 rho)).
+ * Either pointer may be NULL.  Non-fluid cells report 0. */
+lbm_status lbm_moments(lbm_handle h, float* rho, float* u, int on_device);
+
+/* Current populations as shifted float32 df_i = f_i - w_i, [q][nz][ny][nx]; 0 on non-fluid
+ * cells.  Exact for F32 storage; exact widening for F16/BF16 storage. */
+lbm_status lbm_get_populations(lbm_handle h, float* df, int on_device);
+
+/* Replaces the state by the given shifted populations (rounded to the storage precision
+ * with round-to-nearest-even).  Clears the instability flag. */
+lbm_status lbm_set_populations(lbm_handle h, const float* df, int on_device);
+
+/* FP64 sums over fluid cells: out[0] = sum rho, out[1..3] = sum rho u.  Synchronises. */
+lbm_status lbm_reduce(lbm_handle h, double out[4]);
+
+/* Turbulence statistics in FP64, per y plane (LBM_STATS_K values each, see above):
+ * reset, add one sample of the current state, read ny*LBM_STATS_K doubles (host). */
+lbm_status lbm_stats_reset(lbm_handle h);
+lbm_status lbm_stats_sample(lbm_handle h);
+lbm_status lbm_stats_get(lbm_handle h, double* out, int64_t* nsamples);
+
+/* MLP closure parameters (host, bfloat16 bit patterns, n == LBM_MLP_NPARAM) and feature
+ * scales.  Needed before stepping with closure LBM_CLOSURE_MLP. */
+lbm_status lbm_set_closure(lbm_handle h, const uint16_t* bf16_params, int n, double scale_pi,
+                           double scale_rho);
+
+/* Sizes of the handle: padded row length nxp, bytes of one stored population, algorithmic
+ * bytes moved per lattice update of the stepping kernel (2 q s + 1 flag byte). */
+lbm_status lbm_info(lbm_handle h, int* nxp, int* bytes_per_pop, double* bytes_per_update);
+
+/* Message for the last failing call on h (or on creation when h is NULL). */
+const char* lbm_last_error(lbm_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

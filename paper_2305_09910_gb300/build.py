@@ -1,0 +1,96 @@
+"""Builds liblbm.so (the C-ABI CUDA library) in-tree with nvcc for sm_103a.
+
+The library is compiled from ``csrc/``: one host/API translation unit plus one kernel
+translation unit per (stencil, storage precision) pair, compiled in parallel and linked
+with the static CUDA runtime.  A hash of the sources and flags is stored next to the
+library so an unchanged tree is not rebuilt.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import hashlib
+import os
+import shutil
+import subprocess
+import sys
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(PKG, "csrc")
+ROOT = os.path.dirname(PKG)
+INCLUDE = os.path.join(ROOT, "include")
+LIB = os.path.join(PKG, "liblbm.so")
+BUILD = os.path.join(PKG, "_build")
+
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+
+INSTANCES = [(q, s) for q in (19, 27) for s in ("float", "__half", "__nv_bfloat16")]
+
+
+def _nvcc() -> str:
+    for cand in (shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found: the CUDA toolkit is required to build liblbm.so")
+
+
+def _sources():
+    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC)
+                  if f.endswith((".cu", ".cuh", ".h"))) + [os.path.join(INCLUDE, "lbm.h")]
+
+
+def _digest(extra) -> str:
+    h = hashlib.sha256()
+    for path in _sources():
+        with open(path, "rb") as fh:
+            h.update(path.encode() + b"\0" + fh.read())
+    h.update(" ".join(ARCH + NVFLAGS + list(extra)).encode())
+    return h.hexdigest()
+
+
+def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
+    """Compiles (if needed) and returns the path of liblbm.so."""
+    extra = list(extra_flags)
+    digest = _digest(extra)
+    stamp = LIB + ".sha256"
+    if not force and os.path.exists(LIB) and os.path.exists(stamp):
+        with open(stamp) as fh:
+            if fh.read().strip() == digest:
+                return LIB
+    nvcc = _nvcc()
+    os.makedirs(BUILD, exist_ok=True)
+    jobs = [(os.path.join(CSRC, "lbm_api.cu"), os.path.join(BUILD, "lbm_api.o"), [])]
+    for q, s in INSTANCES:
+        tag = s.strip("_").replace("nv_", "")
+        jobs.append((os.path.join(CSRC, "kern_inst.cu"), os.path.join(BUILD, f"kern_q{q}_{tag}.o"),
+                     [f"-DLBM_Q={q}", f"-DLBM_S={s}"]))
+
+    def compile_one(job):
+        src, obj, defs = job
+        cmd = [nvcc, *ARCH, *NVFLAGS, *extra, *defs, "-c", src, "-o", obj]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {os.path.basename(obj)}:\n{r.stderr}")
+        return r.stderr
+
+    with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
+        logs = list(ex.map(compile_one, jobs))
+    if verbose:
+        for log in logs:
+            if log:
+                sys.stderr.write(log)
+    tmp = LIB + f".tmp{os.getpid()}"
+    cmd = [nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp] + [j[1] for j in jobs]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link of liblbm.so failed:\n{r.stderr}")
+    os.replace(tmp, LIB)
+    with open(stamp, "w") as fh:
+        fh.write(digest + "\n")
+    return LIB
+
+
+if __name__ == "__main__":
+    v = "-v" in sys.argv
+    flags = ["-Xptxas", "-v"] if "--ptxas" in sys.argv else []
+    print(build(force="--force" in sys.argv, verbose=v or bool(flags), extra_flags=flags))

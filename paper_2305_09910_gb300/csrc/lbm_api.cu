@@ -1,0 +1,584 @@
+// lbm_api.cu -- the C ABI declared in include/lbm.h: handle lifetime, validation, state
+// bookkeeping (AA parity), and dispatch to the (stencil, precision) kernel instances.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/lbm.h"
+#include "lbm_launch.cuh"
+
+using namespace lbm;
+
+struct lbm_s {
+  int nx = 0, ny = 0, nz = 0, nxp = 0, q = 0;
+  double tau = 0.0;
+  lbm_params prm{};
+  cudaStream_t stream = nullptr;
+  void* f = nullptr;          // populations, q * plane elements of the storage type
+  uint8_t* flags = nullptr;   // raw flags, padded layout
+  uint8_t* cls = nullptr;     // cell classes, padded layout
+  int* status = nullptr;      // device status word
+  int* status_host = nullptr; // pinned copy
+  double* sums = nullptr;     // 4 doubles (lbm_reduce)
+  double* stats = nullptr;    // ny * LBM_STATS_K doubles
+  float* mlp = nullptr;       // MLP parameters widened to float
+  float mlp_scale[2] = {0.f, 0.f};
+  bool mlp_set = false;
+  int64_t nsamples = 0;
+  double force[3] = {0.0, 0.0, 0.0};
+  int parity = 0;             // 0: natural layout, 1: swapped (after an odd number of steps)
+  std::string err;
+};
+
+static std::string g_create_error;
+
+static lbm_status fail(lbm_handle h, lbm_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf;
+  else g_create_error = buf;
+  return s;
+}
+
+#define CUDA_TRY(h, call)                                                                  \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail((h), e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s: %s", \
+                  #call, cudaGetErrorString(e_));                                          \
+  } while (0)
+
+static size_t store_bytes(int precision) { return precision == LBM_F32 ? 4 : 2; }
+
+static long long plane_of(const lbm_s* h) { return (long long)h->nxp * h->ny * h->nz; }
+
+static long long ncell(const lbm_s* h) { return (long long)h->nx * h->ny * h->nz; }
+
+static Launch launch_cfg(const lbm_s* h) {
+  Launch L;
+  L.block = dim3(32, 4, 1);
+  L.grid = dim3(h->nxp / 32, (h->ny + 3) / 4, h->nz);
+  L.stream = h->stream;
+  return L;
+}
+
+static KParams kparams(const lbm_s* h) {
+  KParams p;
+  std::memset(&p, 0, sizeof p);
+  p.f = h->f;
+  p.flags = h->flags;
+  p.cls = h->cls;
+  p.mlp = h->mlp;
+  p.status = h->status;
+  p.plane = plane_of(h);
+  p.nx = h->nx;
+  p.ny = h->ny;
+  p.nz = h->nz;
+  p.nxp = h->nxp;
+  p.outflow = h->prm.face_bc[1] == LBM_FACE_OUTFLOW;
+  for (int k = 0; k < 6; k++) p.face[k] = h->prm.face_bc[k];
+  const double tau = h->tau, lam = h->prm.magic_lambda;
+  p.tau0 = (float)tau;
+  p.lambda = (float)lam;
+  p.cs2 = (float)(h->prm.cs_smag * h->prm.cs_smag);
+  p.omega_p = (float)(1.0 / tau);
+  p.omega_m = (float)(1.0 / (lam / (tau - 0.5) + 0.5));
+  for (int a = 0; a < 3; a++) p.F[a] = (float)h->force[a];
+  double w[27];
+  int c[81];
+  lbm_stencil(h->q, c, w);
+  for (int i = 0; i < h->q; i++) {
+    const double cu = c[3 * i] * h->prm.u_inflow[0] + c[3 * i + 1] * h->prm.u_inflow[1] +
+                      c[3 * i + 2] * h->prm.u_inflow[2];
+    p.inflow_term[i] = (float)(6.0 * w[i] * h->prm.rho_inflow * cu);
+  }
+  p.mlp_scale[0] = h->mlp_scale[0];
+  p.mlp_scale[1] = h->mlp_scale[1];
+  return p;
+}
+
+template <int Q>
+static cudaError_t dispatch_step(const lbm_s* h, const KParams& p, int closure, int parity) {
+  const Launch L = launch_cfg(h);
+  switch (h->prm.precision) {
+    case LBM_F32: return launch_step<Q, float>(p, closure, parity, L);
+    case LBM_F16_SHIFTED: return launch_step<Q, __half>(p, closure, parity, L);
+    default: return launch_step<Q, __nv_bfloat16>(p, closure, parity, L);
+  }
+}
+
+template <int Q>
+static cudaError_t dispatch_export(const lbm_s* h, const KParams& p, int mode, const ExportArgs& a) {
+  const Launch L = launch_cfg(h);
+  switch (h->prm.precision) {
+    case LBM_F32: return launch_export<Q, float>(p, h->parity, mode, a, L);
+    case LBM_F16_SHIFTED: return launch_export<Q, __half>(p, h->parity, mode, a, L);
+    default: return launch_export<Q, __nv_bfloat16>(p, h->parity, mode, a, L);
+  }
+}
+
+template <int Q>
+static cudaError_t dispatch_init(const lbm_s* h, const KParams& p, const float* rho, const float* u) {
+  const Launch L = launch_cfg(h);
+  switch (h->prm.precision) {
+    case LBM_F32: return launch_init_eq<Q, float>(p, rho, u, L);
+    case LBM_F16_SHIFTED: return launch_init_eq<Q, __half>(p, rho, u, L);
+    default: return launch_init_eq<Q, __nv_bfloat16>(p, rho, u, L);
+  }
+}
+
+template <int Q>
+static cudaError_t dispatch_set_pop(const lbm_s* h, const KParams& p, const float* df) {
+  const Launch L = launch_cfg(h);
+  switch (h->prm.precision) {
+    case LBM_F32: return launch_set_pop<Q, float>(p, df, L);
+    case LBM_F16_SHIFTED: return launch_set_pop<Q, __half>(p, df, L);
+    default: return launch_set_pop<Q, __nv_bfloat16>(p, df, L);
+  }
+}
+
+// ---- small kernels of the set-up path -----------------------------------------------------
+
+// Copies dense flags into the padded layout and counts values outside the cell enum.
+__global__ void k_flags_in(const uint8_t* in, uint8_t* out, int nx, int ny, int nz, int nxp, int* bad) {
+  const long long n = (long long)nx * ny * nz;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(k % nx);
+    const long long r = k / nx;
+    const uint8_t v = in[k];
+    if (v > CELL_INFLOW) atomicAdd(bad, 1);
+    out[r * nxp + x] = v > CELL_INFLOW ? (uint8_t)CELL_SOLID : v;
+  }
+}
+
+// Cell classes: skip (non-fluid or padding), boundary (a source needs a rule), interior.
+__global__ void k_classify(const __grid_constant__ KParams p, uint8_t* cls, int q) {
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (y >= p.ny) return;
+  const int cell = cidx(p, x, y, z);
+  if (x >= p.nx || p.flags[cell] != CELL_FLUID) {
+    cls[cell] = CLS_SKIP;
+    return;
+  }
+  const int xc[3] = {x, y, z};
+  const int n[3] = {p.nx, p.ny, p.nz};
+  int c = CLS_INTERIOR;
+  for (int i = 1; i < q && c == CLS_INTERIOR; i++) {
+    const int d[3] = {cx(i), cy(i), cz(i)};
+    int s[3];
+    for (int a = 0; a < 3; a++) {
+      s[a] = xc[a] - d[a];
+      if (s[a] < 0 || s[a] >= n[a]) {
+        if (p.face[2 * a] != FACE_PERIODIC) c = CLS_BOUNDARY;
+        s[a] = s[a] < 0 ? s[a] + n[a] : s[a] - n[a];
+      }
+    }
+    if (c == CLS_INTERIOR && p.flags[cidx(p, s[0], s[1], s[2])] != CELL_FLUID) c = CLS_BOUNDARY;
+  }
+  cls[cell] = (uint8_t)c;
+}
+
+// ---- C ABI ----------------------------------------------------------------------------------
+
+extern "C" {
+
+void lbm_params_default(lbm_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof *p);
+  p->struct_size = sizeof(lbm_params);
+  p->precision = LBM_F32;
+  p->streaming = LBM_AA;
+  p->closure = LBM_CLOSURE_NONE;
+  p->magic_lambda = 3.0 / 16.0;
+  p->cs_smag = 0.1;
+  for (int k = 0; k < 6; k++) p->face_bc[k] = LBM_FACE_PERIODIC;
+  p->rho_inflow = 1.0;
+  p->stream = nullptr;
+}
+
+int lbm_stencil(int q, int* c, double* w) {
+  if (q != 19 && q != 27) return 0;
+  for (int i = 0; i < q; i++) {
+    if (c) {
+      c[3 * i] = cx(i);
+      c[3 * i + 1] = cy(i);
+      c[3 * i + 2] = cz(i);
+    }
+    if (w) {
+      const int n = csq(i);
+      if (q == 19) w[i] = n == 0 ? 1.0 / 3.0 : n == 1 ? 1.0 / 18.0 : 1.0 / 36.0;
+      else w[i] = n == 0 ? 8.0 / 27.0 : n == 1 ? 2.0 / 27.0 : n == 2 ? 1.0 / 54.0 : 1.0 / 216.0;
+    }
+  }
+  return q;
+}
+
+const char* lbm_last_error(lbm_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+static lbm_status launch_classify(lbm_handle h) {
+  KParams p = kparams(h);
+  Launch L = launch_cfg(h);
+  k_classify<<<L.grid, L.block, 0, h->stream>>>(p, h->cls, h->q);
+  CUDA_TRY(h, cudaGetLastError());
+  return LBM_OK;
+}
+
+lbm_status lbm_destroy(lbm_handle h) {
+  if (!h) return LBM_OK;
+  if (h->f) cudaFreeAsync(h->f, h->stream);
+  if (h->flags) cudaFreeAsync(h->flags, h->stream);
+  if (h->cls) cudaFreeAsync(h->cls, h->stream);
+  if (h->status) cudaFreeAsync(h->status, h->stream);
+  if (h->sums) cudaFreeAsync(h->sums, h->stream);
+  if (h->stats) cudaFreeAsync(h->stats, h->stream);
+  if (h->mlp) cudaFreeAsync(h->mlp, h->stream);
+  cudaStreamSynchronize(h->stream);
+  if (h->status_host) cudaFreeHost(h->status_host);
+  delete h;
+  return LBM_OK;
+}
+
+lbm_status lbm_create(int nx, int ny, int nz, int stencil, double tau, const lbm_params* prm,
+                      lbm_handle* out) {
+  if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
+  *out = nullptr;
+  lbm_params p;
+  lbm_params_default(&p);
+  if (prm) {
+    if (prm->struct_size != sizeof(lbm_params))
+      return fail(nullptr, LBM_EINVAL, "lbm_params.struct_size %u != %zu", prm->struct_size,
+                  sizeof(lbm_params));
+    p = *prm;
+  }
+  if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, LBM_EINVAL, "lattice size must be >= 1");
+  if (stencil != 19 && stencil != 27) return fail(nullptr, LBM_EINVAL, "stencil must be 19 or 27");
+  if (!(tau > 0.5) || !std::isfinite(tau)) return fail(nullptr, LBM_EINVAL, "tau must be > 1/2");
+  if (!(p.magic_lambda > 0.0) || !std::isfinite(p.magic_lambda))
+    return fail(nullptr, LBM_EINVAL, "magic_lambda must be > 0");
+  if (p.precision < LBM_F32 || p.precision > LBM_BF16_SHIFTED)
+    return fail(nullptr, LBM_EINVAL, "unknown precision %d", p.precision);
+  if (p.closure < LBM_CLOSURE_NONE || p.closure > LBM_CLOSURE_MLP)
+    return fail(nullptr, LBM_EINVAL, "unknown closure %d", p.closure);
+  if (p.streaming == LBM_PULL)
+    return fail(nullptr, LBM_EUNSUPPORTED, "two-grid pull streaming is not built in this library");
+  if (p.streaming != LBM_AA) return fail(nullptr, LBM_EINVAL, "unknown streaming %d", p.streaming);
+  if (!(p.cs_smag >= 0.0)) return fail(nullptr, LBM_EINVAL, "cs_smag must be >= 0");
+  for (int k = 0; k < 6; k++)
+    if (p.face_bc[k] < LBM_FACE_PERIODIC || p.face_bc[k] > LBM_FACE_OUTFLOW)
+      return fail(nullptr, LBM_EINVAL, "unknown face type %d", p.face_bc[k]);
+  for (int a = 0; a < 3; a++)
+    if ((p.face_bc[2 * a] == LBM_FACE_PERIODIC) != (p.face_bc[2 * a + 1] == LBM_FACE_PERIODIC))
+      return fail(nullptr, LBM_EINVAL, "periodic faces must come in pairs (axis %d)", a);
+  for (int k = 0; k < 6; k++)
+    if (p.face_bc[k] == LBM_FACE_OUTFLOW && k != 1)
+      return fail(nullptr, LBM_EUNSUPPORTED, "outflow is supported on the +x face only");
+  if (p.face_bc[1] == LBM_FACE_OUTFLOW && (nx < 2 || nx % 32 == 1))
+    return fail(nullptr, LBM_EUNSUPPORTED, "an outflow face needs nx >= 2 and nx %% 32 != 1");
+  const int nxp = (nx + 31) / 32 * 32;
+  if ((long long)nxp * ny * nz >= (1ll << 31))
+    return fail(nullptr, LBM_EINVAL, "lattice too large (padded cells must be < 2^31)");
+  if (ny > 65535 * 4 || nz > 65535) return fail(nullptr, LBM_EINVAL, "ny or nz too large for the grid");
+
+  lbm_s* h = new (std::nothrow) lbm_s();
+  if (!h) return fail(nullptr, LBM_ENOMEM, "host allocation failed");
+  h->nx = nx;
+  h->ny = ny;
+  h->nz = nz;
+  h->nxp = nxp;
+  h->q = stencil;
+  h->tau = tau;
+  h->prm = p;
+  h->stream = (cudaStream_t)p.stream;
+  const long long plane = plane_of(h);
+  const size_t fbytes = (size_t)plane * stencil * store_bytes(p.precision);
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMallocAsync(&h->f, fbytes, h->stream);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->flags, (size_t)plane, h->stream);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->cls, (size_t)plane, h->stream);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->status, sizeof(int), h->stream);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->sums, 4 * sizeof(double), h->stream);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->stats, (size_t)ny * LBM_STATS_K * sizeof(double), h->stream);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&h->status_host, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->f, 0, fbytes, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->flags, 0, (size_t)plane, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->stats, 0, (size_t)ny * LBM_STATS_K * sizeof(double), h->stream);
+  if (e != cudaSuccess) {
+    lbm_status s = fail(nullptr, e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA,
+                        "allocation of %zu population bytes failed: %s", fbytes, cudaGetErrorString(e));
+    lbm_destroy(h);
+    return s;
+  }
+  // padding columns are never fluid
+  if (nxp != nx) {
+    e = cudaMemset2DAsync(h->flags + nx, nxp, CELL_SOLID, nxp - nx, (size_t)ny * nz, h->stream);
+    if (e != cudaSuccess) {
+      lbm_status s = fail(nullptr, LBM_ECUDA, "flag padding: %s", cudaGetErrorString(e));
+      lbm_destroy(h);
+      return s;
+    }
+  }
+  lbm_status s = launch_classify(h);
+  if (s != LBM_OK) {
+    g_create_error = h->err;
+    lbm_destroy(h);
+    return s;
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_flags(lbm_handle h, const uint8_t* flags, int on_device) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (!flags) return fail(h, LBM_EINVAL, "flags is NULL");
+  const long long n = ncell(h);
+  const uint8_t* src = flags;
+  uint8_t* tmp = nullptr;
+  if (!on_device) {
+    CUDA_TRY(h, cudaMallocAsync((void**)&tmp, (size_t)n, h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(tmp, flags, (size_t)n, cudaMemcpyHostToDevice, h->stream));
+    src = tmp;
+  }
+  int* bad = nullptr;
+  CUDA_TRY(h, cudaMallocAsync((void**)&bad, sizeof(int), h->stream));
+  CUDA_TRY(h, cudaMemsetAsync(bad, 0, sizeof(int), h->stream));
+  const int blocks = (int)std::min<long long>((n + 255) / 256, 152 * 32);
+  k_flags_in<<<blocks, 256, 0, h->stream>>>(src, h->flags, h->nx, h->ny, h->nz, h->nxp, bad);
+  CUDA_TRY(h, cudaGetLastError());
+  int nbad = 0;
+  CUDA_TRY(h, cudaMemcpyAsync(h->status_host, bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaFreeAsync(bad, h->stream));
+  if (tmp) CUDA_TRY(h, cudaFreeAsync(tmp, h->stream));
+  lbm_status s = launch_classify(h);
+  if (s != LBM_OK) return s;
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  nbad = *h->status_host;
+  if (nbad) return fail(h, LBM_EINVAL, "%d flag values outside {0,1,2} (stored as solid)", nbad);
+  return LBM_OK;
+}
+
+lbm_status lbm_set_force(lbm_handle h, double fx, double fy, double fz) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (!std::isfinite(fx) || !std::isfinite(fy) || !std::isfinite(fz))
+    return fail(h, LBM_EINVAL, "force must be finite");
+  h->force[0] = fx;
+  h->force[1] = fy;
+  h->force[2] = fz;
+  return LBM_OK;
+}
+
+// Stages a host array on the device (or passes a device pointer through).
+static lbm_status stage_in(lbm_handle h, const float* src, size_t count, int on_device, const float** dev,
+                           float** tmp) {
+  *tmp = nullptr;
+  *dev = src;
+  if (!src || on_device) return LBM_OK;
+  CUDA_TRY(h, cudaMallocAsync((void**)tmp, count * sizeof(float), h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(*tmp, src, count * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  *dev = *tmp;
+  return LBM_OK;
+}
+
+static lbm_status reset_status(lbm_handle h) {
+  CUDA_TRY(h, cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_init_equilibrium(lbm_handle h, const float* rho, const float* u, int on_device) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  const long long n = ncell(h);
+  const float *drho = nullptr, *du = nullptr;
+  float *trho = nullptr, *tu = nullptr;
+  lbm_status s = stage_in(h, rho, (size_t)n, on_device, &drho, &trho);
+  if (s == LBM_OK) s = stage_in(h, u, (size_t)n * 3, on_device, &du, &tu);
+  if (s != LBM_OK) return s;
+  KParams p = kparams(h);
+  cudaError_t e = h->q == 19 ? dispatch_init<19>(h, p, drho, du) : dispatch_init<27>(h, p, drho, du);
+  if (trho) cudaFreeAsync(trho, h->stream);
+  if (tu) cudaFreeAsync(tu, h->stream);
+  CUDA_TRY(h, e);
+  h->parity = 0;
+  return reset_status(h);
+}
+
+lbm_status lbm_set_populations(lbm_handle h, const float* df, int on_device) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (!df) return fail(h, LBM_EINVAL, "df is NULL");
+  const float* d = nullptr;
+  float* t = nullptr;
+  lbm_status s = stage_in(h, df, (size_t)ncell(h) * h->q, on_device, &d, &t);
+  if (s != LBM_OK) return s;
+  KParams p = kparams(h);
+  cudaError_t e = h->q == 19 ? dispatch_set_pop<19>(h, p, d) : dispatch_set_pop<27>(h, p, d);
+  if (t) cudaFreeAsync(t, h->stream);
+  CUDA_TRY(h, e);
+  h->parity = 0;
+  return reset_status(h);
+}
+
+lbm_status lbm_step(lbm_handle h, int64_t n) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (n < 0) return fail(h, LBM_EINVAL, "n must be >= 0");
+  if (h->prm.closure == LBM_CLOSURE_MLP && !h->mlp_set)
+    return fail(h, LBM_ESTATE, "MLP closure selected but lbm_set_closure was not called");
+  KParams p = kparams(h);
+  for (int64_t k = 0; k < n; k++) {
+    cudaError_t e = h->q == 19 ? dispatch_step<19>(h, p, h->prm.closure, h->parity)
+                               : dispatch_step<27>(h, p, h->prm.closure, h->parity);
+    CUDA_TRY(h, e);
+    h->parity ^= 1;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_handle h) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  CUDA_TRY(h, cudaMemcpyAsync(h->status_host, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  if (*h->status_host & 1)
+    return fail(h, LBM_EUNSTABLE, "a step produced a non-finite or non-positive density");
+  return LBM_OK;
+}
+
+static lbm_status run_export(lbm_handle h, int mode, const ExportArgs& a) {
+  KParams p = kparams(h);
+  cudaError_t e = h->q == 19 ? dispatch_export<19>(h, p, mode, a) : dispatch_export<27>(h, p, mode, a);
+  CUDA_TRY(h, e);
+  return LBM_OK;
+}
+
+lbm_status lbm_moments(lbm_handle h, float* rho, float* u, int on_device) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (!rho && !u) return LBM_OK;
+  const long long n = ncell(h);
+  ExportArgs a{};
+  float *trho = nullptr, *tu = nullptr;
+  if (on_device) {
+    a.rho = rho;
+    a.u = u;
+  } else {
+    if (rho) CUDA_TRY(h, cudaMallocAsync((void**)&trho, (size_t)n * sizeof(float), h->stream));
+    if (u) CUDA_TRY(h, cudaMallocAsync((void**)&tu, (size_t)n * 3 * sizeof(float), h->stream));
+    a.rho = trho;
+    a.u = tu;
+  }
+  lbm_status s = run_export(h, EX_MOM, a);
+  if (s != LBM_OK) return s;
+  if (!on_device) {
+    if (rho) CUDA_TRY(h, cudaMemcpyAsync(rho, trho, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    if (u) CUDA_TRY(h, cudaMemcpyAsync(u, tu, (size_t)n * 3 * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    if (trho) cudaFreeAsync(trho, h->stream);
+    if (tu) cudaFreeAsync(tu, h->stream);
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_handle h, float* df, int on_device) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (!df) return fail(h, LBM_EINVAL, "df is NULL");
+  const size_t count = (size_t)ncell(h) * h->q;
+  ExportArgs a{};
+  float* t = nullptr;
+  if (on_device) {
+    a.df = df;
+  } else {
+    CUDA_TRY(h, cudaMallocAsync((void**)&t, count * sizeof(float), h->stream));
+    a.df = t;
+  }
+  lbm_status s = run_export(h, EX_POP, a);
+  if (s != LBM_OK) return s;
+  if (!on_device) {
+    CUDA_TRY(h, cudaMemcpyAsync(df, t, count * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    cudaFreeAsync(t, h->stream);
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_reduce(lbm_handle h, double out[4]) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (!out) return fail(h, LBM_EINVAL, "out is NULL");
+  CUDA_TRY(h, cudaMemsetAsync(h->sums, 0, 4 * sizeof(double), h->stream));
+  ExportArgs a{};
+  a.sums = h->sums;
+  lbm_status s = run_export(h, EX_SUM, a);
+  if (s != LBM_OK) return s;
+  CUDA_TRY(h, cudaMemcpyAsync(out, h->sums, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+lbm_status lbm_stats_reset(lbm_handle h) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  CUDA_TRY(h, cudaMemsetAsync(h->stats, 0, (size_t)h->ny * LBM_STATS_K * sizeof(double), h->stream));
+  h->nsamples = 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_stats_sample(lbm_handle h) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  ExportArgs a{};
+  a.sums = h->stats;
+  lbm_status s = run_export(h, EX_STATS, a);
+  if (s != LBM_OK) return s;
+  h->nsamples++;
+  return LBM_OK;
+}
+
+lbm_status lbm_stats_get(lbm_handle h, double* out, int64_t* nsamples) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (!out) return fail(h, LBM_EINVAL, "out is NULL");
+  CUDA_TRY(h, cudaMemcpyAsync(out, h->stats, (size_t)h->ny * LBM_STATS_K * sizeof(double),
+                              cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  if (nsamples) *nsamples = h->nsamples;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_closure(lbm_handle h, const uint16_t* bf16_params, int n, double scale_pi,
+                           double scale_rho) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (!bf16_params || n != LBM_MLP_NPARAM)
+    return fail(h, LBM_EINVAL, "expected %d bfloat16 parameters", LBM_MLP_NPARAM);
+  if (!std::isfinite(scale_pi) || !std::isfinite(scale_rho))
+    return fail(h, LBM_EINVAL, "feature scales must be finite");
+  float host[LBM_MLP_NPARAM];
+  for (int k = 0; k < n; k++) {
+    const uint32_t bits = (uint32_t)bf16_params[k] << 16;
+    float v;
+    std::memcpy(&v, &bits, sizeof v);
+    if (!std::isfinite(v)) return fail(h, LBM_EINVAL, "non-finite MLP parameter %d", k);
+    host[k] = v;
+  }
+  if (!h->mlp) CUDA_TRY(h, cudaMallocAsync((void**)&h->mlp, sizeof host, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(h->mlp, host, sizeof host, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));  // host buffer is on the stack
+  h->mlp_scale[0] = (float)scale_pi;
+  h->mlp_scale[1] = (float)scale_rho;
+  h->mlp_set = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_info(lbm_handle h, int* nxp, int* bytes_per_pop, double* bytes_per_update) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (nxp) *nxp = h->nxp;
+  const int s = (int)store_bytes(h->prm.precision);
+  if (bytes_per_pop) *bytes_per_pop = s;
+  if (bytes_per_update) *bytes_per_update = 2.0 * h->q * s + 1.0;
+  return LBM_OK;
+}
+
+}  // extern "C"

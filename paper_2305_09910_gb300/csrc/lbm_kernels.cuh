@@ -1,0 +1,489 @@
+// lbm_kernels.cuh -- sm_103a kernels of the lattice Boltzmann stream-and-collide update.
+//
+// One thread per lattice cell, x-contiguous warps, SoA populations stored shifted
+// (df_i = f_i - w_i) in float32, float16 or bfloat16, arithmetic in float32.
+//
+// Streaming uses the AA pattern (one population array, updated in place).  Let A[x][i]
+// be the slot of direction i at cell x.
+//   parity 0 ("natural"): A[x][i] holds the pre-collision f_i(x,t).  The even kernel
+//     reads its own slots, collides and writes f*_i(x) into its own slot A[x][opp(i)].
+//   parity 1 ("swapped"): A[x][opp(i)] holds the post-collision f*_i(x,t-1).  The odd
+//     kernel gathers f_i(x,t) = f*_i(x - c_i) from A[x - c_i][opp(i)] (or from the slot
+//     its boundary rule names), collides, and writes f*_opp(i)(x) back into the very slot
+//     it read f_i from, which is where f_opp(i) of the receiving cell lives at t+1.
+//   Every slot is read and written by exactly one thread per launch, so both kernels are
+//   race-free in place (the boundary rules are involutions on (cell, direction) pairs).
+// Zero-gradient outflow (+x face) copies what the upstream cell x-1 receives; both cells
+// sit in the same warp (nx % 32 != 1), which passes the value with a warp shuffle before
+// any thread writes.
+//
+// Paper: Eq. LBCollision / Eq. LBStreaming (Sec. 2), stream-collide kernel limited by
+// memory bandwidth (Sec. 3, Sec. 5.2 Eq. roofline), single PDF set in place (Sec. 5.2).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// ---- velocity set: published order, components packed 2 bits each (value + 1) ---------
+__host__ __device__ constexpr int cx(int i) { return int((0x20889548889549ull >> (2 * i)) & 3) - 1; }
+__host__ __device__ constexpr int cy(int i) { return int((0xa088895609495ull >> (2 * i)) & 3) - 1; }
+__host__ __device__ constexpr int cz(int i) { return int((0x8a0a0a0954955ull >> (2 * i)) & 3) - 1; }
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+__host__ __device__ constexpr int csq(int i) { return cx(i) * cx(i) + cy(i) * cy(i) + cz(i) * cz(i); }
+
+template <int Q>
+__host__ __device__ constexpr float wgt(int i) {
+  return Q == 19 ? (csq(i) == 0 ? 1.f / 3.f : csq(i) == 1 ? 1.f / 18.f : 1.f / 36.f)
+                 : (csq(i) == 0 ? 8.f / 27.f
+                                : csq(i) == 1 ? 2.f / 27.f : csq(i) == 2 ? 1.f / 54.f : 1.f / 216.f);
+}
+
+// ---- flags, faces, cell classes ------------------------------------------------------
+enum : int { CELL_FLUID = 0, CELL_SOLID = 1, CELL_INFLOW = 2 };
+enum : int { FACE_PERIODIC = 0, FACE_WALL = 1, FACE_FREESLIP = 2, FACE_INFLOW = 3, FACE_OUTFLOW = 4 };
+// cls: interior fluid (every source is a fluid cell reached by plain or periodic streaming),
+// boundary fluid (some source needs a rule), and everything that is not updated.
+enum : int { CLS_INTERIOR = 0, CLS_BOUNDARY = 1, CLS_SKIP = 2 };
+enum : int { CL_NONE = 0, CL_SMAG = 1, CL_MLP = 2 };
+enum : int { K_STREAM = 0, K_BB = 1, K_INFLOW = 2, K_OUTCOPY = 3 };
+
+constexpr int MLP_NIN = 7, MLP_NH = 32;
+constexpr int MLP_NPARAM = MLP_NH * MLP_NIN + MLP_NH + MLP_NH * MLP_NH + MLP_NH + MLP_NH + 1;
+
+struct KParams {
+  void* f;               // population array, q planes of `plane` elements
+  const uint8_t* flags;  // raw cell flags, padded layout
+  const uint8_t* cls;    // cell classes, padded layout
+  const float* mlp;      // MLP parameters (bf16 values widened to float), device
+  int* status;           // bit 0: non-finite or non-positive density seen
+  long long plane;       // nxp * ny * nz
+  int nx, ny, nz, nxp;
+  int outflow;           // +x face is an outflow
+  int face[6];
+  float tau0, lambda, cs2, omega_p, omega_m;
+  float F[3];
+  float inflow_term[27];  // 6 w_i rho_w (c_i . u_w)
+  float mlp_scale[2];
+};
+
+__device__ __forceinline__ int cidx(const KParams& p, int x, int y, int z) {
+  return (z * p.ny + y) * p.nxp + x;
+}
+
+// ---- storage precisions -----------------------------------------------------------------
+template <class S> __device__ __forceinline__ float ld(const S* a);
+template <> __device__ __forceinline__ float ld<float>(const float* a) { return *a; }
+template <> __device__ __forceinline__ float ld<__half>(const __half* a) { return __half2float(*a); }
+template <> __device__ __forceinline__ float ld<__nv_bfloat16>(const __nv_bfloat16* a) {
+  return __bfloat162float(*a);
+}
+template <class S> __device__ __forceinline__ void st(S* a, float v);
+template <> __device__ __forceinline__ void st<float>(float* a, float v) { *a = v; }
+template <> __device__ __forceinline__ void st<__half>(__half* a, float v) { *a = __float2half_rn(v); }
+template <> __device__ __forceinline__ void st<__nv_bfloat16>(__nv_bfloat16* a, float v) {
+  *a = __float2bfloat16_rn(v);
+}
+
+// ---- boundary rule of one (cell, direction): which slot holds the incoming value -------
+__device__ __forceinline__ int face_rank(int t) {
+  return t == FACE_WALL ? 4 : t == FACE_INFLOW ? 3 : t == FACE_OUTFLOW ? 2 : 1;
+}
+
+__device__ __forceinline__ int dir_index(int dx, int dy, int dz) {
+  // inverse of (cx, cy, cz) over the 27 velocities
+  for (int j = 0; j < 27; j++)
+    if (cx(j) == dx && cy(j) == dy && cz(j) == dz) return j;
+  return 0;
+}
+
+// Returns the rule for the incoming population i of fluid cell (x,y,z) and, except for
+// K_OUTCOPY, the slot (plane offset included) that holds it in the swapped layout.
+static __device__ __noinline__ int classify(const KParams& p, int x, int y, int z, int i,
+                                     long long& slot) {
+  const int c[3] = {cx(i), cy(i), cz(i)};
+  const int xc[3] = {x, y, z};
+  const int n[3] = {p.nx, p.ny, p.nz};
+  int s[3], fc[3], rank = 0;
+  for (int a = 0; a < 3; a++) {
+    s[a] = xc[a] - c[a];
+    fc[a] = s[a] < 0 ? 2 * a : (s[a] >= n[a] ? 2 * a + 1 : -1);
+    if (fc[a] >= 0) rank = max(rank, face_rank(p.face[fc[a]]));
+  }
+  const long long own = (long long)i * p.plane + cidx(p, x, y, z);
+  if (rank == 4) { slot = own; return K_BB; }
+  if (rank == 3) { slot = own; return K_INFLOW; }
+  if (rank == 2) {
+    if (p.flags[cidx(p, x - 1, y, z)] == CELL_FLUID) { slot = -1; return K_OUTCOPY; }
+    slot = own;
+    return K_BB;
+  }
+  int d[3];
+  for (int a = 0; a < 3; a++) {
+    d[a] = c[a];
+    if (fc[a] >= 0) {
+      if (p.face[fc[a]] == FACE_PERIODIC) {
+        s[a] = s[a] < 0 ? s[a] + n[a] : s[a] - n[a];
+      } else {  // free-slip: stay in the plane, reflect the normal component
+        s[a] = xc[a];
+        d[a] = -d[a];
+      }
+    }
+  }
+  const int src = cidx(p, s[0], s[1], s[2]);
+  const int fl = p.flags[src];
+  if (fl == CELL_SOLID) { slot = own; return K_BB; }
+  if (fl == CELL_INFLOW) { slot = own; return K_INFLOW; }
+  slot = (long long)opp(dir_index(d[0], d[1], d[2])) * p.plane + src;
+  return K_STREAM;
+}
+
+// Interior cells: periodic-wrapped source of direction i (x - c_i).
+struct Nbr {
+  int xs[3], ys[3], zs[3];  // index c+1 -> coordinate of x - c
+  __device__ __forceinline__ void init(const KParams& p, int x, int y, int z) {
+    xs[1] = x; ys[1] = y; zs[1] = z;
+    xs[2] = x == 0 ? p.nx - 1 : x - 1;  // c = +1
+    xs[0] = x == p.nx - 1 ? 0 : x + 1;  // c = -1
+    ys[2] = y == 0 ? p.ny - 1 : y - 1;
+    ys[0] = y == p.ny - 1 ? 0 : y + 1;
+    zs[2] = z == 0 ? p.nz - 1 : z - 1;
+    zs[0] = z == p.nz - 1 ? 0 : z + 1;
+  }
+  __device__ __forceinline__ int src(const KParams& p, int i) const {
+    return (zs[cz(i) + 1] * p.ny + ys[cy(i) + 1]) * p.nxp + xs[cx(i) + 1];
+  }
+};
+
+// ---- loading the pre-collision populations of one cell ---------------------------------
+template <int Q, class S, int PAR>
+__device__ __forceinline__ void load_state(const KParams& p, const S* F, int x, int y, int z,
+                                           int cell, int cls, float (&f)[Q], unsigned& outmask) {
+  outmask = 0;
+#pragma unroll
+  for (int i = 0; i < Q; i++) f[i] = 0.f;
+  if (cls == CLS_SKIP) return;
+  if (PAR == 0) {
+#pragma unroll
+    for (int i = 0; i < Q; i++) f[i] = ld<S>(F + (long long)i * p.plane + cell);
+    if (cls == CLS_BOUNDARY && p.outflow && x == p.nx - 1) {
+#pragma unroll
+      for (int i = 0; i < Q; i++) {
+        if (cx(i) != -1) continue;
+        long long s;
+        if (classify(p, x, y, z, i, s) == K_OUTCOPY) outmask |= 1u << i;
+      }
+    }
+  } else if (cls == CLS_INTERIOR) {
+    Nbr nb;
+    nb.init(p, x, y, z);
+#pragma unroll
+    for (int i = 0; i < Q; i++) f[i] = ld<S>(F + (long long)opp(i) * p.plane + nb.src(p, i));
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+      long long s;
+      const int k = classify(p, x, y, z, i, s);
+      if (k == K_OUTCOPY) {
+        outmask |= 1u << i;
+      } else {
+        float v = ld<S>(F + s);
+        if (k == K_INFLOW) v += p.inflow_term[i];
+        f[i] = v;
+      }
+    }
+  }
+}
+
+// Zero-gradient outflow: lane x = nx-1 takes the incoming c_x = -1 populations of lane x-1.
+// Called by every thread of the block (warp-uniform condition, full-mask shuffles).
+template <int Q>
+__device__ __forceinline__ void outflow_fix(const KParams& p, int x, float (&f)[Q],
+                                            unsigned outmask) {
+  if (!p.outflow) return;
+  const int x0 = x & ~31;
+  if (!(x0 <= p.nx - 1 && p.nx - 1 < x0 + 32)) return;
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    if (cx(i) != -1) continue;
+    const float v = __shfl_up_sync(0xffffffffu, f[i], 1);
+    if (outmask & (1u << i)) f[i] = v;
+  }
+}
+
+// ---- storing the post-collision populations -------------------------------------------
+template <int Q, class S, int PAR>
+__device__ __forceinline__ void store_state(const KParams& p, S* F, int x, int y, int z,
+                                            int cell, int cls, const float (&fs)[Q]) {
+  if (PAR == 0) {
+#pragma unroll
+    for (int i = 0; i < Q; i++) st<S>(F + (long long)opp(i) * p.plane + cell, fs[i]);
+  } else if (cls == CLS_INTERIOR) {
+    Nbr nb;
+    nb.init(p, x, y, z);
+#pragma unroll
+    for (int i = 0; i < Q; i++) st<S>(F + (long long)opp(i) * p.plane + nb.src(p, i), fs[opp(i)]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+      long long s;
+      const int k = classify(p, x, y, z, i, s);
+      if (k == K_OUTCOPY) continue;
+      float v = fs[opp(i)];
+      if (k == K_INFLOW) v += p.inflow_term[i];
+      st<S>(F + s, v);
+    }
+  }
+}
+
+// ---- closure network (per cell): C_s^2 from the non-equilibrium stress ------------------
+__device__ __forceinline__ float gelu_erf(float a) { return 0.5f * a * (1.f + erff(a * 0.70710678118654752f)); }
+
+__device__ __forceinline__ float softplus_f(float y) { return fmaxf(y, 0.f) + log1pf(expf(-fabsf(y))); }
+
+__device__ __forceinline__ float mlp_cs2(const KParams& p, const float (&pi)[6], float drho) {
+  const float* W1 = p.mlp;
+  const float* b1 = W1 + MLP_NH * MLP_NIN;
+  const float* W2 = b1 + MLP_NH;
+  const float* b2 = W2 + MLP_NH * MLP_NH;
+  const float* W3 = b2 + MLP_NH;
+  const float* b3 = W3 + MLP_NH;
+  float xin[MLP_NIN];
+#pragma unroll
+  for (int k = 0; k < 6; k++) xin[k] = p.mlp_scale[0] * pi[k];
+  xin[6] = p.mlp_scale[1] * drho;
+  float h1[MLP_NH];
+#pragma unroll
+  for (int j = 0; j < MLP_NH; j++) {
+    float s = __ldg(b1 + j);
+#pragma unroll
+    for (int k = 0; k < MLP_NIN; k++) s = fmaf(__ldg(W1 + j * MLP_NIN + k), xin[k], s);
+    h1[j] = gelu_erf(s);
+  }
+  float y = __ldg(b3);
+#pragma unroll 4
+  for (int j = 0; j < MLP_NH; j++) {
+    float s = __ldg(b2 + j);
+#pragma unroll
+    for (int k = 0; k < MLP_NH; k++) s = fmaf(__ldg(W2 + j * MLP_NH + k), h1[k], s);
+    y = fmaf(__ldg(W3 + j), gelu_erf(s), y);
+  }
+  return softplus_f(y) * p.cs2 * 1.4426950408889634f;  // / ln 2
+}
+
+// ---- moments and TRT collision (in place on shifted populations) -----------------------
+template <int Q>
+struct Mom {
+  float drho, rho, ux, uy, uz;
+};
+
+template <int Q>
+__device__ __forceinline__ Mom<Q> moments(const KParams& p, const float (&f)[Q]) {
+  float d = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    d += f[i];
+    if (cx(i)) jx += cx(i) > 0 ? f[i] : -f[i];
+    if (cy(i)) jy += cy(i) > 0 ? f[i] : -f[i];
+    if (cz(i)) jz += cz(i) > 0 ? f[i] : -f[i];
+  }
+  Mom<Q> m;
+  m.drho = d;
+  m.rho = 1.f + d;
+  const float inv = 1.f / m.rho;
+  m.ux = (jx + 0.5f * p.F[0]) * inv;
+  m.uy = (jy + 0.5f * p.F[1]) * inv;
+  m.uz = (jz + 0.5f * p.F[2]) * inv;
+  return m;
+}
+
+template <int Q, int CL>
+__device__ __forceinline__ float collide(const KParams& p, float (&f)[Q]) {
+  const Mom<Q> m = moments<Q>(p, f);
+  const float rho = m.rho, drho = m.drho, ux = m.ux, uy = m.uy, uz = m.uz;
+  float wp = p.omega_p, wm = p.omega_m;
+  if (CL != CL_NONE) {
+    // Pi^neq = sum_i c c df_i - (drho/3) I - rho u u   (shifted form of sum c c (f - feq))
+    float sxx = 0.f, syy = 0.f, szz = 0.f, sxy = 0.f, sxz = 0.f, syz = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+      if (cx(i)) sxx += f[i];
+      if (cy(i)) syy += f[i];
+      if (cz(i)) szz += f[i];
+      if (cx(i) * cy(i)) sxy += cx(i) * cy(i) > 0 ? f[i] : -f[i];
+      if (cx(i) * cz(i)) sxz += cx(i) * cz(i) > 0 ? f[i] : -f[i];
+      if (cy(i) * cz(i)) syz += cy(i) * cz(i) > 0 ? f[i] : -f[i];
+    }
+    const float d3 = drho * (1.f / 3.f);
+    float pi[6];
+    pi[0] = sxx - d3 - rho * ux * ux;
+    pi[1] = syy - d3 - rho * uy * uy;
+    pi[2] = szz - d3 - rho * uz * uz;
+    pi[3] = sxy - rho * ux * uy;
+    pi[4] = sxz - rho * ux * uz;
+    pi[5] = syz - rho * uy * uz;
+    const float qn = pi[0] * pi[0] + pi[1] * pi[1] + pi[2] * pi[2] +
+                     2.f * (pi[3] * pi[3] + pi[4] * pi[4] + pi[5] * pi[5]);
+    float cs2 = p.cs2;
+    if (CL == CL_MLP) cs2 = mlp_cs2(p, pi, drho);
+    const float tau = 0.5f * (p.tau0 + sqrtf(p.tau0 * p.tau0 + 25.455844122715711f * cs2 * sqrtf(qn) / rho));
+    wp = 1.f / tau;
+    wm = 1.f / (p.lambda / (tau - 0.5f) + 0.5f);
+  }
+  const float usq = ux * ux + uy * uy + uz * uz;
+  const float uF = ux * p.F[0] + uy * p.F[1] + uz * p.F[2];
+  const float gp = 1.f - 0.5f * wp, gm = 1.f - 0.5f * wm;
+  {
+    constexpr float w0 = wgt<Q>(0);
+    const float feq = w0 * (drho - 1.5f * rho * usq);
+    f[0] = f[0] - wp * (f[0] - feq) + gp * (w0 * (-3.f * uF));
+  }
+#pragma unroll
+  for (int i = 1; i < Q; i += 2) {
+    constexpr int dummy = 0;
+    (void)dummy;
+    const float w = wgt<Q>(i);
+    const float cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
+    const float cF = cx(i) * p.F[0] + cy(i) * p.F[1] + cz(i) * p.F[2];
+    const float es = w * (drho + rho * (4.5f * cu * cu - 1.5f * usq));
+    const float ea = w * rho * 3.f * cu;
+    const float fsym = 0.5f * (f[i] + f[i + 1]);
+    const float fasy = 0.5f * (f[i] - f[i + 1]);
+    const float so = fsym - wp * (fsym - es) + gp * (w * (9.f * cu * cF - 3.f * uF));
+    const float ao = fasy - wm * (fasy - ea) + gm * (w * 3.f * cF);
+    f[i] = so + ao;
+    f[i + 1] = so - ao;
+  }
+  return rho;
+}
+
+// ---- kernels ------------------------------------------------------------------------------
+// Block (32, 4): a warp is 32 consecutive x of one row; grid (nxp/32, ceil(ny/4), nz).
+#define LBM_CELL_COORDS                                   \
+  const int x = blockIdx.x * 32 + threadIdx.x;            \
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;    \
+  const int z = blockIdx.z;                               \
+  if (y >= p.ny) return; /* whole warp */                 \
+  const int cell = cidx(p, x, y, z);                      \
+  const int cls = x < p.nx ? p.cls[cell] : CLS_SKIP;
+
+template <int Q, class S, int CL, int PAR>
+__global__ void __launch_bounds__(128) k_step(const __grid_constant__ KParams p) {
+  LBM_CELL_COORDS
+  S* F = static_cast<S*>(p.f);
+  float f[Q];
+  unsigned outmask;
+  load_state<Q, S, PAR>(p, F, x, y, z, cell, cls, f, outmask);
+  outflow_fix<Q>(p, x, f, outmask);
+  if (cls == CLS_SKIP) return;
+  const float rho = collide<Q, CL>(p, f);
+  if (!(rho > 0.f && rho < 3.0e38f)) atomicOr(p.status, 1);
+  store_state<Q, S, PAR>(p, F, x, y, z, cell, cls, f);
+}
+
+// Exports of the current state (read-only): populations, moments, FP64 sums, statistics.
+enum : int { EX_POP = 0, EX_MOM = 1, EX_SUM = 2, EX_STATS = 3 };
+
+struct ExportArgs {
+  float* df;       // EX_POP: [q][nz][ny][nx]
+  float* rho;      // EX_MOM: [nz][ny][nx] (may be null)
+  float* u;        // EX_MOM: [3][nz][ny][nx] (may be null)
+  double* sums;    // EX_SUM: 4 doubles; EX_STATS: ny * 10 doubles
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int Q, class S, int PAR, int MODE>
+__global__ void __launch_bounds__(128) k_export(const __grid_constant__ KParams p, ExportArgs a) {
+  LBM_CELL_COORDS
+  const S* F = static_cast<const S*>(p.f);
+  float f[Q];
+  unsigned outmask;
+  load_state<Q, S, PAR>(p, F, x, y, z, cell, cls, f, outmask);
+  outflow_fix<Q>(p, x, f, outmask);
+  const bool fluid = cls != CLS_SKIP;
+  const long long dense = ((long long)z * p.ny + y) * p.nx + x;
+  const long long N = (long long)p.nx * p.ny * p.nz;
+  if (MODE == EX_POP) {
+    if (x >= p.nx) return;
+#pragma unroll
+    for (int i = 0; i < Q; i++) a.df[i * N + dense] = fluid ? f[i] : 0.f;
+    return;
+  }
+  Mom<Q> m = moments<Q>(p, f);
+  if (!fluid) m.rho = m.ux = m.uy = m.uz = 0.f;
+  if (MODE == EX_MOM) {
+    if (x >= p.nx) return;
+    if (a.rho) a.rho[dense] = m.rho;
+    if (a.u) {
+      a.u[dense] = m.ux;
+      a.u[N + dense] = m.uy;
+      a.u[2 * N + dense] = m.uz;
+    }
+    return;
+  }
+  if (MODE == EX_SUM) {
+    double r = fluid ? (double)m.rho : 0.0;
+    double v[4] = {r, r * m.ux, r * m.uy, r * m.uz};
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const double s = warp_sum(v[k]);
+      if ((threadIdx.x & 31) == 0) atomicAdd(a.sums + k, s);
+    }
+    return;
+  }
+  if (MODE == EX_STATS) {  // per y plane; a warp is one row segment at fixed y
+    const double ux = m.ux, uy = m.uy, uz = m.uz;
+    double v[10] = {fluid ? 1.0 : 0.0, ux, uy, uz, ux * ux, uy * uy, uz * uz, ux * uy, ux * uz, uy * uz};
+#pragma unroll
+    for (int k = 0; k < 10; k++) {
+      const double s = warp_sum(v[k]);
+      if ((threadIdx.x & 31) == 0) atomicAdd(a.sums + (long long)y * 10 + k, s);
+    }
+  }
+}
+
+// f = f^eq(rho, u) (shifted) on fluid cells, 0 elsewhere; natural layout.
+template <int Q, class S>
+__global__ void __launch_bounds__(128) k_init_eq(const __grid_constant__ KParams p, const float* rho_in,
+                                                 const float* u_in) {
+  LBM_CELL_COORDS
+  if (x >= p.nx) return;
+  S* F = static_cast<S*>(p.f);
+  const long long dense = ((long long)z * p.ny + y) * p.nx + x;
+  const long long N = (long long)p.nx * p.ny * p.nz;
+  const bool fluid = cls != CLS_SKIP;
+  const float rho = rho_in ? rho_in[dense] : 1.f;
+  const float drho = rho - 1.f;
+  const float ux = u_in ? u_in[dense] : 0.f, uy = u_in ? u_in[N + dense] : 0.f,
+              uz = u_in ? u_in[2 * N + dense] : 0.f;
+  const float usq = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    const float cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
+    const float v = wgt<Q>(i) * (drho + rho * (3.f * cu + 4.5f * cu * cu - 1.5f * usq));
+    st<S>(F + (long long)i * p.plane + cell, fluid ? v : 0.f);
+  }
+}
+
+// Natural-layout state from dense shifted float32 populations.
+template <int Q, class S>
+__global__ void __launch_bounds__(128) k_set_pop(const __grid_constant__ KParams p, const float* df) {
+  LBM_CELL_COORDS
+  if (x >= p.nx) return;
+  S* F = static_cast<S*>(p.f);
+  const long long dense = ((long long)z * p.ny + y) * p.nx + x;
+  const long long N = (long long)p.nx * p.ny * p.nz;
+  const bool fluid = cls != CLS_SKIP;
+#pragma unroll
+  for (int i = 0; i < Q; i++) st<S>(F + (long long)i * p.plane + cell, fluid ? df[i * N + dense] : 0.f);
+}
+
+}  // namespace lbm

@@ -1,0 +1,320 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (north star of the method's GPU form):
+  * single steps from identical states: max |f_gpu - f_oracle| <= 1e-6 per population (FP32);
+  * laminar runs: max |u_gpu - u_oracle| / max |u_oracle| <= 1e-5;
+  * FP16 / BF16 storage: the error of one step stays within the storage rounding bound
+    (2^-11 resp. 2^-8 of |df| plus FP32 arithmetic), and the error of longer runs is stated.
+Sizes span several 32-wide tiles with a ragged tail (nx not a multiple of 32, ny not a
+multiple of 4) so that padding, warp shuffles and partial blocks are exercised.
+"""
+import numpy as np
+import pytest
+
+from tests.cases import FACES_CHANNEL, FACES_TUNNEL, developed_state, make_pair, max_abs_pop_error
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    import torch
+
+    from paper_2305_09910_gb300 import build
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+
+
+def _box_flags(nx, ny, nz, boxes, inflow_cells=()):
+    f = np.zeros((nz, ny, nx), np.uint8)
+    for (x0, x1, y0, y1, z0, z1) in boxes:
+        f[z0:z1, y0:y1, x0:x1] = 1
+    for (x, y, z) in inflow_cells:
+        f[z, y, x] = 2
+    return f
+
+
+def _channel_case(q, closure="smag"):
+    nx, ny, nz = 70, 13, 9
+    return dict(nx=nx, ny=ny, nz=nz, q=q, tau=0.56, closure=closure, cs=0.12, faces=FACES_CHANNEL,
+                force=(2e-5, 3e-6, 0.0), flags=_box_flags(nx, ny, nz, [(20, 26, 4, 8, 2, 6)]))
+
+
+def _tunnel_case(q):
+    nx, ny, nz = 45, 11, 7
+    return dict(nx=nx, ny=ny, nz=nz, q=q, tau=0.54, closure="smag", cs=0.1, faces=FACES_TUNNEL,
+                u_w=(0.05, 0.004, -0.002),
+                flags=_box_flags(nx, ny, nz, [(12, 17, 3, 7, 0, 4)], inflow_cells=[(30, 0, 3), (31, 10, 6)]))
+
+
+def _mixed_case(q):
+    nx, ny, nz = 38, 9, 6
+    faces = ("inflow", "outflow", "wall", "freeslip", "periodic", "periodic")
+    return dict(nx=nx, ny=ny, nz=nz, q=q, tau=0.7, closure="none", faces=faces,
+                u_w=(0.03, 0.0, 0.01), force=(1e-5, 0, 0),
+                flags=_box_flags(nx, ny, nz, [(36, 38, 3, 5, 1, 3)]))
+
+
+def _periodic_case(q):
+    return dict(nx=33, ny=6, nz=5, q=q, tau=0.9, closure="none", force=(2e-5, -1e-5, 5e-6))
+
+
+CASES = {
+    "channel19": _channel_case(19), "channel27": _channel_case(27),
+    "tunnel19": _tunnel_case(19), "tunnel27": _tunnel_case(27),
+    "mixed19": _mixed_case(19), "mixed27": _mixed_case(27),
+    "periodic19": _periodic_case(19), "periodic27": _periodic_case(27),
+    "channel19_plain": _channel_case(19, "none"),
+}
+
+
+def _start(lat, ora, case, seed, spin=6):
+    from paper_2305_09910_gb300 import inputs
+
+    nx, ny, nz = case["nx"], case["ny"], case["nz"]
+    rho, u = inputs.channel_init(nx, ny, nz, u_bulk=0.05, seed=seed)
+    u = u + np.array(case.get("u_w", (0, 0, 0)), np.float32)[:, None, None, None]
+    df = developed_state(ora, rho, u, spin, noise_seed=seed, noise=0.02)
+    ora.set_shifted(df)
+    lat.set_populations(df)
+    return df
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+@pytest.mark.parametrize("steps", [1, 2, 5])
+def test_single_steps_match_oracle(name, steps):
+    case = CASES[name]
+    lat, ora = make_pair(**case)
+    _start(lat, ora, case, seed=100 + steps)
+    lat.step(steps)
+    ora.step(steps)
+    lat.sync()
+    err = max_abs_pop_error(lat, ora)
+    assert err <= 1e-6, f"{name}: {err}"
+
+
+@pytest.mark.parametrize("name", ["channel19", "tunnel27", "mixed19"])
+def test_moments_reduce_stats_match_oracle(name):
+    case = CASES[name]
+    lat, ora = make_pair(**case)
+    _start(lat, ora, case, seed=7)
+    from paper_2305_09910_gb300 import lbm
+
+    for steps in (0, 1):  # both AA parities
+        lat.step(steps)
+        ora.step(steps)
+        rho, u = lat.moments()
+        rr, ur = ora.moments()
+        assert np.abs(rho - rr).max() <= 1e-6
+        assert np.abs(u - ur).max() <= 1e-6
+        s = lat.reduce()
+        sr = ora.mass_momentum()
+        assert abs(s[0] - sr[0]) <= 1e-6 * sr[0]
+        assert np.abs(s[1:] - sr[1:]).max() <= 1e-6 * sr[0]
+        lbm.lbm_stats_reset(lat.h)
+        lbm.lbm_stats_sample(lat.h)
+        st, ns = lbm.lbm_stats_get(lat.h, case["ny"])
+        assert ns == 1
+        sref = ora.stats_sample()
+        assert np.array_equal(st[:, 0], sref[:, 0])
+        assert np.abs(st - sref).max() <= 1e-6 * case["nx"] * case["nz"]
+
+
+def test_poiseuille_1000_steps_matches_oracle():
+    """64x32x32, tau 0.8, g_x 1e-6, walls = solid rows y = 0 and 31, 1000 steps."""
+    from paper_2305_09910_gb300 import inputs
+
+    nx, ny, nz = 64, 32, 32
+    flags = inputs.poiseuille_flags(nx, ny, nz)
+    lat, ora = make_pair(nx, ny, nz, q=19, tau=0.8, force=(1e-6, 0, 0), flags=flags)
+    lat.init_equilibrium()
+    ora.init_equilibrium(1.0, np.zeros(3))
+    m0 = lat.reduce()[0]
+    lat.step(1000)
+    ora.step(1000)
+    lat.sync()
+    _, u = lat.moments()
+    _, ur = ora.moments()
+    rel = np.abs(u - ur).max() / np.abs(ur).max()
+    assert rel <= 1e-5, rel
+    m1 = lat.reduce()[0]
+    assert abs(m1 - m0) / m0 <= 1e-7
+    # the profile is symmetric about the channel centre and independent of x and z
+    ux = u[0]
+    assert np.abs(ux - ux[:, ::-1, :]).max() <= 1e-9
+    assert np.abs(ux - ux[:1, :, :1]).max() <= 1e-9
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_poiseuille_steady_closed_form(q):
+    """Quasi-1D channel to steady state: the TRT bounce-back parabola with Lambda = 3/16."""
+    ny, tau, g = 18, 0.8, 1e-6
+    nu = (tau - 0.5) / 3
+    from paper_2305_09910_gb300 import lbm
+
+    lat = lbm.Lattice(1, ny, 1, stencil=q, tau=tau, faces=FACES_CHANNEL)
+    lat.set_force(g)
+    lat.init_equilibrium()
+    lat.step(20000)
+    lat.sync()
+    _, u = lat.moments()
+    y = np.arange(ny) + 0.5
+    ua = g / (2 * nu) * y * (ny - y)
+    assert np.abs(u[0, 0, :, 0] - ua).max() / ua.max() <= 2e-5
+
+
+@pytest.mark.parametrize("precision", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("n", [3, 4])
+def test_checkpoint_resume_bit_exact(precision, n):
+    """2n steps == n steps, export, re-import, n steps (exact in every storage precision)."""
+    case = dict(CASES["tunnel19"])
+    a, ora = make_pair(precision=precision, **case)
+    b, _ = make_pair(precision=precision, **case)
+    df = _start(a, ora, case, seed=3)
+    b.set_populations(df)
+    a.step(2 * n)
+    b.step(n)
+    mid = b.get_populations()
+    b.set_populations(mid)
+    b.step(n)
+    assert np.array_equal(a.get_populations(), b.get_populations())
+
+
+@pytest.mark.parametrize("precision,bound", [("f16", 2.0 ** -11), ("bf16", 2.0 ** -8)])
+@pytest.mark.parametrize("name", ["channel19", "tunnel27"])
+def test_half_storage_rounding_bound(precision, bound, name):
+    case = CASES[name]
+    lat, ora = make_pair(precision=precision, **case)
+    df = _start(lat, ora, case, seed=11)
+    # start both sides from the values the half-precision store represents
+    import torch
+
+    dt = torch.float16 if precision == "f16" else torch.bfloat16
+    df_h = torch.from_numpy(df).to(dt).to(torch.float32).numpy()
+    lat.set_populations(df_h)
+    ora.set_shifted(df_h)
+    lat.step(1)
+    ora.step(1)
+    got = lat.get_populations().astype(np.float64)
+    ref = ora.shifted()
+    fluid = ora.flags == 0
+    err = np.abs(got - ref)[:, fluid]
+    allowed = bound * np.abs(ref)[:, fluid] + 2e-7
+    assert (err <= allowed).all(), float((err - allowed).max())
+
+
+def test_full_size_channel_sampled_parity():
+    """512x256x256 channel (the benchmark lattice), one step from f^eq of the seeded
+    perturbed parabola, checked at sampled cells against the oracle cell by cell."""
+    import torch
+
+    import oracle
+    from paper_2305_09910_gb300 import inputs, lbm
+
+    nx, ny, nz = 512, 256, 256
+    par = inputs.channel_parameters(ny)
+    rho, u = inputs.channel_init(nx, ny, nz)
+    lat = lbm.Lattice(nx, ny, nz, stencil=19, tau=par["tau"], closure="smag", cs_smag=0.1,
+                      faces=FACES_CHANNEL)
+    lat.set_force(par["force"])
+    lat.init_equilibrium(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
+    lat.step(1)
+    df = torch.empty((19, nz, ny, nx), dtype=torch.float32, device="cuda")
+    lbm.lbm_get_populations(lat.h, df)
+    cells = inputs.sample_cells(nx * ny * nz, 400, stream=21)
+    # include wall-adjacent and periodic-seam cells
+    extra = [0, nx - 1, (ny - 1) * nx, nx * ny * (nz - 1) + (ny - 1) * nx + nx - 1]
+    cells = np.unique(np.concatenate([cells, np.array(extra, np.int64)]))
+    got = df.reshape(19, -1)[:, torch.from_numpy(cells).cuda()].T.cpu().numpy().astype(np.float64)
+    ora = oracle.Oracle(nx, ny, nz, q=19, tau=par["tau"], closure="smag", cs=0.1,
+                        faces=FACES_CHANNEL, force=(par["force"], 0, 0))
+    ref = ora.step_sampled(rho, u, cells) - ora.w[None, :]
+    assert np.abs(got - ref).max() <= 1e-6
+
+
+def test_full_size_bluff_body_sampled_parity():
+    """768x384x384 D3Q27 tunnel with the landing-gear flags, one step, sampled cells."""
+    import torch
+
+    import oracle
+    from paper_2305_09910_gb300 import inputs, lbm
+
+    nx, ny, nz = 768, 384, 384
+    flags = inputs.landing_gear_flags(nx, ny, nz)
+    uw = (0.05, 0.0, 0.0)
+    tau = 0.5 + 3 * 0.05 * 80 / 1e4
+    lat = lbm.Lattice(nx, ny, nz, stencil=27, tau=tau, closure="smag", cs_smag=0.1,
+                      faces=FACES_TUNNEL, u_inflow=uw)
+    lat.set_flags(flags)
+    rho = np.ones((nz, ny, nx), np.float32)
+    u = np.zeros((3, nz, ny, nx), np.float32)
+    u[0] = 0.05
+    noise = inputs.uniform_field(5, 40, (nz, ny, nx), -0.002, 0.002, np.float32)
+    u[1] += noise
+    lat.init_equilibrium(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
+    lat.step(1)
+    df = torch.empty((27, nz, ny, nx), dtype=torch.float32, device="cuda")
+    lbm.lbm_get_populations(lat.h, df)
+    solid = np.flatnonzero(flags.reshape(-1))
+    near = solid[inputs.sample_cells(solid.size, 150, stream=22)] - 1  # just upstream of solids
+    cells = np.concatenate([inputs.sample_cells(nx * ny * nz, 300, stream=23), near,
+                            [0, nx - 1, nx * ny * nz - 1]])
+    cells = np.unique(cells[(cells >= 0)])
+    got = df.reshape(27, -1)[:, torch.from_numpy(cells).cuda()].T.cpu().numpy().astype(np.float64)
+    ora = oracle.Oracle(nx, ny, nz, q=27, tau=tau, closure="smag", cs=0.1, faces=FACES_TUNNEL,
+                        u_w=uw, flags=flags)
+    ref = ora.step_sampled(rho, u, cells) - ora.w[None, :]
+    fl = flags.reshape(-1)[cells] == 0
+    assert np.abs(got - ref)[fl].max() <= 1e-6
+
+
+def test_errors_and_edge_cases():
+    from paper_2305_09910_gb300 import lbm
+
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.Lattice(33, 4, 4, faces=FACES_TUNNEL)  # 33 % 32 == 1 with an outflow face
+    assert e.value.status == lbm.LBM_EUNSUPPORTED
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.Lattice(8, 4, 4, faces=("periodic", "wall", "periodic", "periodic", "periodic", "periodic"))
+    assert e.value.status == lbm.LBM_EINVAL
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.Lattice(8, 4, 4, tau=0.5)
+    assert e.value.status == lbm.LBM_EINVAL
+    lat = lbm.Lattice(8, 4, 4, closure="mlp")
+    with pytest.raises(lbm.LbmError) as e:
+        lat.step(1)
+    assert e.value.status == lbm.LBM_ESTATE
+    lat = lbm.Lattice(8, 4, 4)
+    bad = np.zeros((4, 4, 8), np.uint8)
+    bad[0, 0, 0] = 7
+    with pytest.raises(lbm.LbmError) as e:
+        lat.set_flags(bad)
+    assert e.value.status == lbm.LBM_EINVAL
+    # zero steps, single cell, fully solid lattice
+    lat.step(0)
+    one = lbm.Lattice(1, 1, 1, stencil=27)
+    one.init_equilibrium(np.array([1.01], np.float32), np.array([0.01, 0.02, 0.0], np.float32))
+    one.step(3)
+    r, u = one.moments()
+    assert abs(r[0, 0, 0] - 1.01) < 1e-6 and abs(u[0, 0, 0, 0] - 0.01) < 1e-6
+    solid = lbm.Lattice(40, 3, 2)
+    solid.set_flags(np.ones((2, 3, 40), np.uint8))
+    solid.step(2)
+    assert solid.reduce()[0] == 0.0
+
+
+def test_instability_is_reported_not_trapped():
+    from paper_2305_09910_gb300 import lbm
+
+    lat = lbm.Lattice(40, 4, 4)
+    df = np.zeros((19, 4, 4, 40), np.float32)
+    df[0, 1, 1, 5] = -5.0  # rho = -4 at one cell
+    lat.set_populations(df)
+    lat.step(2)
+    with pytest.raises(lbm.LbmError) as e:
+        lat.sync()
+    assert e.value.status == lbm.LBM_EUNSTABLE
+    lat.init_equilibrium()
+    lat.step(2)
+    lat.sync()
