@@ -288,6 +288,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16/BF16 forms")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    ap.add_argument("--size", default="512x256x256", help="lattice NXxNYxNZ (profiling runs)")
+    ap.add_argument("--form", default="f32", choices=["f32", "f16", "bf16"],
+                    help="storage precision of the main line (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -309,9 +312,9 @@ def main():
     gpu_uuid = str(torch.cuda.get_device_properties(local).uuid)
     gpu_id = gpu_uuid if gpu_uuid.startswith("GPU-") else f"GPU-{gpu_uuid}"
 
-    nx, ny, nz = 512, 256, 256
+    nx, ny, nz = (int(v) for v in args.size.lower().split("x"))
     ncell = nx * ny * nz
-    lat, par = _channel_lattice(nx, ny, nz, "f32")
+    lat, par = _channel_lattice(nx, ny, nz, args.form)
     clocks = ClockSampler(gpu_id)
     time.sleep(1.0)  # let nvidia-smi start
     for _ in range(args.warmup):
@@ -322,9 +325,10 @@ def main():
     clocks.stop()
     total_ms = _barrier_max(dist, total_ms)
     value = world * ncell * args.steps / (total_ms * 1e-3) / 1e6
-    traffic = _profile_traffic("k_step_q19_f32_smag_channel512")
+    traffic = _profile_traffic(f"k_step_q19_{args.form}_smag_channel{nx}")
     roof = _roofline(ncell, lat.bytes_per_update, per, peak, peak_kind, traffic)
     mass = lat.reduce()[0]
+    lat_bytes = ncell * 19 * lat.bytes_per_pop
 
     # end to end through the C ABI with host buffers: upload (rho, u) from pinned memory,
     # K steps, read the moments back to pinned memory
@@ -332,11 +336,12 @@ def main():
 
     rho_h = torch.empty((nz, ny, nx), dtype=torch.float32).pin_memory()
     u_h = torch.empty((3, nz, ny, nx), dtype=torch.float32).pin_memory()
-    step = nz // 8
+    step = max(1, nz // 8)
     for z0 in range(0, nz, step):
-        r, v = inputs.channel_init(nx, ny, nz, z_range=(z0, z0 + step))
-        rho_h[z0:z0 + step].copy_(torch.from_numpy(r))
-        u_h[:, z0:z0 + step].copy_(torch.from_numpy(v))
+        z1 = min(nz, z0 + step)
+        r, v = inputs.channel_init(nx, ny, nz, z_range=(z0, z1))
+        rho_h[z0:z1].copy_(torch.from_numpy(r))
+        u_h[:, z0:z1].copy_(torch.from_numpy(v))
     rho_o = torch.empty_like(rho_h).pin_memory()
     u_o = torch.empty_like(u_h).pin_memory()
     torch.cuda.synchronize()
@@ -365,14 +370,16 @@ def main():
                 "roofline": _roofline(ncell, fl.bytes_per_update, per_f, peak, peak_kind, None)}
             fl.close()
 
+    workload = WORKLOAD if (nx, ny, nz, args.form) == (512, 256, 256, "f32") else \
+        f"turbulent channel {nx}x{ny}x{nz} D3Q19 TRT+Smagorinsky {args.form} (AA in place)"
     out = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "nx": nx, "ny": ny, "nz": nz, "stencil": 19,
+           "config": {"workload": workload, "storage": args.form, "nx": nx, "ny": ny, "nz": nz, "stencil": 19,
                       "tau": round(par["tau"], 6), "force": par["force"], "cs_smag": 0.1,
                       "global_batch": world * ncell, "parallelism": f"replicas x{world}",
-                      "l2": "inputs larger than L2 (2.55 GB population array vs 129 MB L2)"},
+                      "l2": f"inputs larger than L2 ({lat_bytes / 1e9:.2f} GB population array vs 129 MB L2)"},
            "roofline": roof, "e2e": e2e, "gpu_launches": args.steps,
            "clocks": clocks.summary(), "mass_after": mass, "forms": forms}
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -33,6 +33,7 @@ struct lbm_s {
   int64_t nsamples = 0;
   double force[3] = {0.0, 0.0, 0.0};
   int parity = 0;             // 0: natural layout, 1: swapped (after an odd number of steps)
+  int nat_valid = 1;          // natural layout came from an import (outflow slots hold values)
   std::string err;
 };
 
@@ -75,6 +76,12 @@ static KParams kparams(const lbm_s* h) {
   KParams p;
   std::memset(&p, 0, sizeof p);
   p.f = h->f;
+  {
+    const size_t sb = store_bytes(h->prm.precision);
+    for (int i = 0; i < 27; i++)
+      p.fp[i] = i < h->q ? (void*)((char*)h->f + (size_t)i * (size_t)plane_of(h) * sb) : nullptr;
+  }
+  p.nat_valid = h->nat_valid;
   p.flags = h->flags;
   p.cls = h->cls;
   p.mlp = h->mlp;
@@ -410,6 +417,7 @@ lbm_status lbm_init_equilibrium(lbm_handle h, const float* rho, const float* u, 
   if (tu) cudaFreeAsync(tu, h->stream);
   CUDA_TRY(h, e);
   h->parity = 0;
+  h->nat_valid = 1;
   return reset_status(h);
 }
 
@@ -425,6 +433,7 @@ lbm_status lbm_set_populations(lbm_handle h, const float* df, int on_device) {
   if (t) cudaFreeAsync(t, h->stream);
   CUDA_TRY(h, e);
   h->parity = 0;
+  h->nat_valid = 1;
   return reset_status(h);
 }
 
@@ -435,9 +444,11 @@ lbm_status lbm_step(lbm_handle h, int64_t n) {
     return fail(h, LBM_ESTATE, "MLP closure selected but lbm_set_closure was not called");
   KParams p = kparams(h);
   for (int64_t k = 0; k < n; k++) {
+    p.nat_valid = h->nat_valid;
     cudaError_t e = h->q == 19 ? dispatch_step<19>(h, p, h->prm.closure, h->parity)
                                : dispatch_step<27>(h, p, h->prm.closure, h->parity);
     CUDA_TRY(h, e);
+    if (h->parity == 1) h->nat_valid = 0;  // an odd step leaves the outflow slots unwritten
     h->parity ^= 1;
   }
   return LBM_OK;

@@ -26,6 +26,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace lbm {
 
 // ---- velocity set: published order, components packed 2 bits each (value + 1) ---------
@@ -56,6 +58,7 @@ constexpr int MLP_NPARAM = MLP_NH * MLP_NIN + MLP_NH + MLP_NH * MLP_NH + MLP_NH 
 
 struct KParams {
   void* f;               // population array, q planes of `plane` elements
+  void* fp[27];          // fp[i] = start of plane i (per-direction base pointers)
   const uint8_t* flags;  // raw cell flags, padded layout
   const uint8_t* cls;    // cell classes, padded layout
   const float* mlp;      // MLP parameters (bf16 values widened to float), device
@@ -63,6 +66,7 @@ struct KParams {
   long long plane;       // nxp * ny * nz
   int nx, ny, nz, nxp;
   int outflow;           // +x face is an outflow
+  int nat_valid;         // natural layout holds imported values in the outflow slots
   int face[6];
   float tau0, lambda, cs2, omega_p, omega_m;
   float F[3];
@@ -88,6 +92,14 @@ template <> __device__ __forceinline__ void st<__nv_bfloat16>(__nv_bfloat16* a, 
   *a = __float2bfloat16_rn(v);
 }
 
+// Value after a round trip through the storage precision.
+template <class S> __device__ __forceinline__ float rnd(float v);
+template <> __device__ __forceinline__ float rnd<float>(float v) { return v; }
+template <> __device__ __forceinline__ float rnd<__half>(float v) { return __half2float(__float2half_rn(v)); }
+template <> __device__ __forceinline__ float rnd<__nv_bfloat16>(float v) {
+  return __bfloat162float(__float2bfloat16_rn(v));
+}
+
 // ---- boundary rule of one (cell, direction): which slot holds the incoming value -------
 __device__ __forceinline__ int face_rank(int t) {
   return t == FACE_WALL ? 4 : t == FACE_INFLOW ? 3 : t == FACE_OUTFLOW ? 2 : 1;
@@ -101,9 +113,9 @@ __device__ __forceinline__ int dir_index(int dx, int dy, int dz) {
 }
 
 // Returns the rule for the incoming population i of fluid cell (x,y,z) and, except for
-// K_OUTCOPY, the slot (plane offset included) that holds it in the swapped layout.
+// K_OUTCOPY, the slot (plane, cell) that holds it in the swapped layout.
 static __device__ __noinline__ int classify(const KParams& p, int x, int y, int z, int i,
-                                     long long& slot) {
+                                            int& plane, int& cell) {
   const int c[3] = {cx(i), cy(i), cz(i)};
   const int xc[3] = {x, y, z};
   const int n[3] = {p.nx, p.ny, p.nz};
@@ -113,14 +125,11 @@ static __device__ __noinline__ int classify(const KParams& p, int x, int y, int 
     fc[a] = s[a] < 0 ? 2 * a : (s[a] >= n[a] ? 2 * a + 1 : -1);
     if (fc[a] >= 0) rank = max(rank, face_rank(p.face[fc[a]]));
   }
-  const long long own = (long long)i * p.plane + cidx(p, x, y, z);
-  if (rank == 4) { slot = own; return K_BB; }
-  if (rank == 3) { slot = own; return K_INFLOW; }
-  if (rank == 2) {
-    if (p.flags[cidx(p, x - 1, y, z)] == CELL_FLUID) { slot = -1; return K_OUTCOPY; }
-    slot = own;
-    return K_BB;
-  }
+  plane = i;
+  cell = cidx(p, x, y, z);
+  if (rank == 4) return K_BB;
+  if (rank == 3) return K_INFLOW;
+  if (rank == 2) return p.flags[cidx(p, x - 1, y, z)] == CELL_FLUID ? K_OUTCOPY : K_BB;
   int d[3];
   for (int a = 0; a < 3; a++) {
     d[a] = c[a];
@@ -135,10 +144,16 @@ static __device__ __noinline__ int classify(const KParams& p, int x, int y, int 
   }
   const int src = cidx(p, s[0], s[1], s[2]);
   const int fl = p.flags[src];
-  if (fl == CELL_SOLID) { slot = own; return K_BB; }
-  if (fl == CELL_INFLOW) { slot = own; return K_INFLOW; }
-  slot = (long long)opp(dir_index(d[0], d[1], d[2])) * p.plane + src;
+  if (fl == CELL_SOLID) return K_BB;
+  if (fl == CELL_INFLOW) return K_INFLOW;
+  plane = opp(dir_index(d[0], d[1], d[2]));
+  cell = src;
   return K_STREAM;
+}
+
+template <class S>
+__device__ __forceinline__ S* plane_ptr(const KParams& p, int i) {
+  return static_cast<S*>(p.fp[i]);
 }
 
 // Interior cells: periodic-wrapped source of direction i (x - c_i).
@@ -160,38 +175,41 @@ struct Nbr {
 
 // ---- loading the pre-collision populations of one cell ---------------------------------
 template <int Q, class S, int PAR>
-__device__ __forceinline__ void load_state(const KParams& p, const S* F, int x, int y, int z,
-                                           int cell, int cls, float (&f)[Q], unsigned& outmask) {
+__device__ __forceinline__ void load_state(const KParams& p, int x, int y, int z, int cell, int cls,
+                                           float (&f)[Q], unsigned& outmask) {
   outmask = 0;
 #pragma unroll
   for (int i = 0; i < Q; i++) f[i] = 0.f;
   if (cls == CLS_SKIP) return;
   if (PAR == 0) {
 #pragma unroll
-    for (int i = 0; i < Q; i++) f[i] = ld<S>(F + (long long)i * p.plane + cell);
-    if (cls == CLS_BOUNDARY && p.outflow && x == p.nx - 1) {
+    for (int i = 0; i < Q; i++) f[i] = ld<S>(plane_ptr<S>(p, i) + cell);
+    // after a streaming step the outflow slots of x = nx-1 were not written (they are
+    // copies of the upstream cell); after an import they hold the imported values
+    if (cls == CLS_BOUNDARY && p.outflow && !p.nat_valid && x == p.nx - 1) {
 #pragma unroll
       for (int i = 0; i < Q; i++) {
         if (cx(i) != -1) continue;
-        long long s;
-        if (classify(p, x, y, z, i, s) == K_OUTCOPY) outmask |= 1u << i;
+        int pl, ce;
+        if (classify(p, x, y, z, i, pl, ce) == K_OUTCOPY) outmask |= 1u << i;
       }
     }
   } else if (cls == CLS_INTERIOR) {
     Nbr nb;
     nb.init(p, x, y, z);
 #pragma unroll
-    for (int i = 0; i < Q; i++) f[i] = ld<S>(F + (long long)opp(i) * p.plane + nb.src(p, i));
+    for (int i = 0; i < Q; i++) f[i] = ld<S>(plane_ptr<S>(p, opp(i)) + nb.src(p, i));
   } else {
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-      long long s;
-      const int k = classify(p, x, y, z, i, s);
+      int pl, ce;
+      const int k = classify(p, x, y, z, i, pl, ce);
       if (k == K_OUTCOPY) {
         outmask |= 1u << i;
       } else {
-        float v = ld<S>(F + s);
-        if (k == K_INFLOW) v += p.inflow_term[i];
+        float v = ld<S>(plane_ptr<S>(p, pl) + ce);
+        // moving-wall value rounded like the natural-layout slot that holds it
+        if (k == K_INFLOW) v = rnd<S>(v + p.inflow_term[i]);
         f[i] = v;
       }
     }
@@ -216,25 +234,25 @@ __device__ __forceinline__ void outflow_fix(const KParams& p, int x, float (&f)[
 
 // ---- storing the post-collision populations -------------------------------------------
 template <int Q, class S, int PAR>
-__device__ __forceinline__ void store_state(const KParams& p, S* F, int x, int y, int z,
-                                            int cell, int cls, const float (&fs)[Q]) {
+__device__ __forceinline__ void store_state(const KParams& p, int x, int y, int z, int cell, int cls,
+                                            const float (&fs)[Q]) {
   if (PAR == 0) {
 #pragma unroll
-    for (int i = 0; i < Q; i++) st<S>(F + (long long)opp(i) * p.plane + cell, fs[i]);
+    for (int i = 0; i < Q; i++) st<S>(plane_ptr<S>(p, opp(i)) + cell, fs[i]);
   } else if (cls == CLS_INTERIOR) {
     Nbr nb;
     nb.init(p, x, y, z);
 #pragma unroll
-    for (int i = 0; i < Q; i++) st<S>(F + (long long)opp(i) * p.plane + nb.src(p, i), fs[opp(i)]);
+    for (int i = 0; i < Q; i++) st<S>(plane_ptr<S>(p, opp(i)) + nb.src(p, i), fs[opp(i)]);
   } else {
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-      long long s;
-      const int k = classify(p, x, y, z, i, s);
+      int pl, ce;
+      const int k = classify(p, x, y, z, i, pl, ce);
       if (k == K_OUTCOPY) continue;
       float v = fs[opp(i)];
-      if (k == K_INFLOW) v += p.inflow_term[i];
-      st<S>(F + s, v);
+      if (k == K_INFLOW) v = rnd<S>(v) + p.inflow_term[i];  // same rounding as the swapped path
+      st<S>(plane_ptr<S>(p, pl) + ce, v);
     }
   }
 }
@@ -276,10 +294,19 @@ __device__ __forceinline__ float mlp_cs2(const KParams& p, const float (&pi)[6],
 
 // ---- moments and TRT collision (in place on shifted populations) -----------------------
 template <int Q>
+__host__ __device__ constexpr double wgt_d(int i) {
+  return Q == 19 ? (csq(i) == 0 ? 1.0 / 3.0 : csq(i) == 1 ? 1.0 / 18.0 : 1.0 / 36.0)
+                 : (csq(i) == 0 ? 8.0 / 27.0
+                                : csq(i) == 1 ? 2.0 / 27.0 : csq(i) == 2 ? 1.0 / 54.0 : 1.0 / 216.0);
+}
+
+template <int Q>
 struct Mom {
-  float drho, rho, ux, uy, uz;
+  float drho, rho, jx, jy, jz, ux, uy, uz;  // j = sum c df + F/2 = rho u
 };
 
+// Moments from the populations (used by the exports; the collision forms them from pair
+// sums).  Reciprocal of rho with the fast approximate division (relative error < 2^-22).
 template <int Q>
 __device__ __forceinline__ Mom<Q> moments(const KParams& p, const float (&f)[Q]) {
   float d = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
@@ -293,70 +320,132 @@ __device__ __forceinline__ Mom<Q> moments(const KParams& p, const float (&f)[Q])
   Mom<Q> m;
   m.drho = d;
   m.rho = 1.f + d;
-  const float inv = 1.f / m.rho;
-  m.ux = (jx + 0.5f * p.F[0]) * inv;
-  m.uy = (jy + 0.5f * p.F[1]) * inv;
-  m.uz = (jz + 0.5f * p.F[2]) * inv;
+  m.jx = jx + 0.5f * p.F[0];
+  m.jy = jy + 0.5f * p.F[1];
+  m.jz = jz + 0.5f * p.F[2];
+  const float inv = __fdividef(1.f, m.rho);
+  m.ux = m.jx * inv;
+  m.uy = m.jy * inv;
+  m.uz = m.jz * inv;
   return m;
 }
 
+struct CollCtx {
+  float rho, drho, ux, uy, uz, jx, jy, jz, usq, uF, Fx, Fy, Fz, wp, wm, gp, gm;
+};
+
+// Sums over the +/- pairs: s_P = f_i + f_opp(i), d_P = f_i - f_opp(i) (i = 2P+1).
+template <int Q, int I>
+__device__ __forceinline__ void pair_moments(const float (&f)[Q], float (&m)[10]) {
+  constexpr int X = cx(I), Y = cy(I), Z = cz(I);
+  const float s = f[I] + f[I + 1];
+  const float d = f[I] - f[I + 1];
+  m[0] += s;
+  if (X) m[1] += X > 0 ? d : -d;
+  if (Y) m[2] += Y > 0 ? d : -d;
+  if (Z) m[3] += Z > 0 ? d : -d;
+  if (X) m[4] += s;
+  if (Y) m[5] += s;
+  if (Z) m[6] += s;
+  if (X * Y) m[7] += X * Y > 0 ? s : -s;
+  if (X * Z) m[8] += X * Z > 0 ? s : -s;
+  if (Y * Z) m[9] += Y * Z > 0 ? s : -s;
+}
+
+template <int Q, int... P>
+__device__ __forceinline__ void all_pair_moments(const float (&f)[Q], float (&m)[10],
+                                                 std::integer_sequence<int, P...>) {
+  (pair_moments<Q, 2 * P + 1>(f, m), ...);
+}
+
+// One +/- pair (I, I+1) of the TRT collision, written as f* = f + delta so that the only
+// rounding at the magnitude of f is the final addition.  The antisymmetric equilibrium
+// 3 w (c.j) is carried as an unevaluated sum hi + lo (the FMA recovers the product's
+// rounding error exactly), and the non-equilibrium parts are formed by subtracting it
+// from f first, where the operands nearly cancel.  This keeps the per-step momentum error
+// at the level of one rounding of f, which matters at the small velocities of laminar runs.
+template <int Q, int I>
+__device__ __forceinline__ void trt_pair(float (&f)[Q], const CollCtx& c) {
+  constexpr int X = cx(I), Y = cy(I), Z = cz(I);
+  constexpr float w = (float)wgt_d<Q>(I);
+  constexpr float khi = (float)(3.0 * wgt_d<Q>(I));
+  constexpr float klo = (float)(3.0 * wgt_d<Q>(I) - (double)khi);
+  const float cu = X * c.ux + Y * c.uy + Z * c.uz;
+  const float cj = X * c.jx + Y * c.jy + Z * c.jz;
+  const float cF = X * c.Fx + Y * c.Fy + Z * c.Fz;
+  const float eh = cj * khi;
+  const float el = fmaf(cj, klo, fmaf(cj, khi, -eh));
+  const float es = w * (c.drho + c.rho * (4.5f * cu * cu - 1.5f * c.usq));
+  const float ni = ((f[I] - eh) - el) - es;
+  const float nj = ((f[I + 1] + eh) + el) - es;
+  const float ds = -c.wp * (0.5f * (ni + nj)) + c.gp * (w * (9.f * cu * cF - 3.f * c.uF));
+  const float da = -c.wm * (0.5f * (ni - nj)) + c.gm * (w * 3.f * cF);
+  f[I] = f[I] + (ds + da);
+  f[I + 1] = f[I + 1] + (ds - da);
+}
+
+template <int Q, int... P>
+__device__ __forceinline__ void trt_pairs(float (&f)[Q], const CollCtx& c, std::integer_sequence<int, P...>) {
+  (trt_pair<Q, 2 * P + 1>(f, c), ...);
+}
+
+// sqrt of a non-negative value from the hardware reciprocal square root (x = 0 gives 0).
+__device__ __forceinline__ float fast_sqrt(float x) { return x * rsqrtf(fmaxf(x, 1e-37f)); }
+
 template <int Q, int CL>
 __device__ __forceinline__ float collide(const KParams& p, float (&f)[Q]) {
-  const Mom<Q> m = moments<Q>(p, f);
-  const float rho = m.rho, drho = m.drho, ux = m.ux, uy = m.uy, uz = m.uz;
+  using Pairs = std::make_integer_sequence<int, (Q - 1) / 2>;
+  // m: sum s, j_x, j_y, j_z (without F/2), sum c_x^2 f, c_y^2 f, c_z^2 f, c_xc_y f, c_xc_z f, c_yc_z f
+  float m[10] = {f[0], 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  all_pair_moments<Q>(f, m, Pairs{});
+  const float drho = m[0];
+  const float rho = 1.f + drho;
+  const float jx = m[1] + 0.5f * p.F[0], jy = m[2] + 0.5f * p.F[1], jz = m[3] + 0.5f * p.F[2];
+  const float inv = __fdividef(1.f, rho);
+  const float ux = jx * inv, uy = jy * inv, uz = jz * inv;
   float wp = p.omega_p, wm = p.omega_m;
   if (CL != CL_NONE) {
-    // Pi^neq = sum_i c c df_i - (drho/3) I - rho u u   (shifted form of sum c c (f - feq))
-    float sxx = 0.f, syy = 0.f, szz = 0.f, sxy = 0.f, sxz = 0.f, syz = 0.f;
-#pragma unroll
-    for (int i = 0; i < Q; i++) {
-      if (cx(i)) sxx += f[i];
-      if (cy(i)) syy += f[i];
-      if (cz(i)) szz += f[i];
-      if (cx(i) * cy(i)) sxy += cx(i) * cy(i) > 0 ? f[i] : -f[i];
-      if (cx(i) * cz(i)) sxz += cx(i) * cz(i) > 0 ? f[i] : -f[i];
-      if (cy(i) * cz(i)) syz += cy(i) * cz(i) > 0 ? f[i] : -f[i];
-    }
+    // Pi^neq = sum_i c c df_i - (drho/3) I - j u   (shifted form of sum c c (f - feq))
     const float d3 = drho * (1.f / 3.f);
     float pi[6];
-    pi[0] = sxx - d3 - rho * ux * ux;
-    pi[1] = syy - d3 - rho * uy * uy;
-    pi[2] = szz - d3 - rho * uz * uz;
-    pi[3] = sxy - rho * ux * uy;
-    pi[4] = sxz - rho * ux * uz;
-    pi[5] = syz - rho * uy * uz;
+    pi[0] = m[4] - d3 - jx * ux;
+    pi[1] = m[5] - d3 - jy * uy;
+    pi[2] = m[6] - d3 - jz * uz;
+    pi[3] = m[7] - jx * uy;
+    pi[4] = m[8] - jx * uz;
+    pi[5] = m[9] - jy * uz;
     const float qn = pi[0] * pi[0] + pi[1] * pi[1] + pi[2] * pi[2] +
                      2.f * (pi[3] * pi[3] + pi[4] * pi[4] + pi[5] * pi[5]);
     float cs2 = p.cs2;
     if (CL == CL_MLP) cs2 = mlp_cs2(p, pi, drho);
-    const float tau = 0.5f * (p.tau0 + sqrtf(p.tau0 * p.tau0 + 25.455844122715711f * cs2 * sqrtf(qn) / rho));
-    wp = 1.f / tau;
-    wm = 1.f / (p.lambda / (tau - 0.5f) + 0.5f);
+    const float tau = 0.5f * (p.tau0 + fast_sqrt(p.tau0 * p.tau0 + 25.455844122715711f * cs2 * fast_sqrt(qn) * inv));
+    wp = __fdividef(1.f, tau);
+    wm = __fdividef(1.f, __fdividef(p.lambda, tau - 0.5f) + 0.5f);
   }
-  const float usq = ux * ux + uy * uy + uz * uz;
-  const float uF = ux * p.F[0] + uy * p.F[1] + uz * p.F[2];
-  const float gp = 1.f - 0.5f * wp, gm = 1.f - 0.5f * wm;
+  CollCtx c;
+  c.rho = rho;
+  c.drho = drho;
+  c.ux = ux;
+  c.uy = uy;
+  c.uz = uz;
+  c.jx = jx;
+  c.jy = jy;
+  c.jz = jz;
+  c.usq = ux * ux + uy * uy + uz * uz;
+  c.Fx = p.F[0];
+  c.Fy = p.F[1];
+  c.Fz = p.F[2];
+  c.uF = ux * c.Fx + uy * c.Fy + uz * c.Fz;
+  c.wp = wp;
+  c.wm = wm;
+  c.gp = 1.f - 0.5f * wp;
+  c.gm = 1.f - 0.5f * wm;
   {
-    constexpr float w0 = wgt<Q>(0);
-    const float feq = w0 * (drho - 1.5f * rho * usq);
-    f[0] = f[0] - wp * (f[0] - feq) + gp * (w0 * (-3.f * uF));
+    constexpr float w0 = (float)wgt_d<Q>(0);
+    const float n0 = f[0] - w0 * (drho - 1.5f * rho * c.usq);
+    f[0] = f[0] + (-wp * n0 + c.gp * (w0 * (-3.f * c.uF)));
   }
-#pragma unroll
-  for (int i = 1; i < Q; i += 2) {
-    constexpr int dummy = 0;
-    (void)dummy;
-    const float w = wgt<Q>(i);
-    const float cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
-    const float cF = cx(i) * p.F[0] + cy(i) * p.F[1] + cz(i) * p.F[2];
-    const float es = w * (drho + rho * (4.5f * cu * cu - 1.5f * usq));
-    const float ea = w * rho * 3.f * cu;
-    const float fsym = 0.5f * (f[i] + f[i + 1]);
-    const float fasy = 0.5f * (f[i] - f[i + 1]);
-    const float so = fsym - wp * (fsym - es) + gp * (w * (9.f * cu * cF - 3.f * uF));
-    const float ao = fasy - wm * (fasy - ea) + gm * (w * 3.f * cF);
-    f[i] = so + ao;
-    f[i + 1] = so - ao;
-  }
+  trt_pairs<Q>(f, c, Pairs{});
   return rho;
 }
 
@@ -371,17 +460,16 @@ __device__ __forceinline__ float collide(const KParams& p, float (&f)[Q]) {
   const int cls = x < p.nx ? p.cls[cell] : CLS_SKIP;
 
 template <int Q, class S, int CL, int PAR>
-__global__ void __launch_bounds__(128) k_step(const __grid_constant__ KParams p) {
+__global__ void __launch_bounds__(128, CL == CL_MLP ? 4 : 8) k_step(const __grid_constant__ KParams p) {
   LBM_CELL_COORDS
-  S* F = static_cast<S*>(p.f);
   float f[Q];
   unsigned outmask;
-  load_state<Q, S, PAR>(p, F, x, y, z, cell, cls, f, outmask);
+  load_state<Q, S, PAR>(p, x, y, z, cell, cls, f, outmask);
   outflow_fix<Q>(p, x, f, outmask);
   if (cls == CLS_SKIP) return;
   const float rho = collide<Q, CL>(p, f);
   if (!(rho > 0.f && rho < 3.0e38f)) atomicOr(p.status, 1);
-  store_state<Q, S, PAR>(p, F, x, y, z, cell, cls, f);
+  store_state<Q, S, PAR>(p, x, y, z, cell, cls, f);
 }
 
 // Exports of the current state (read-only): populations, moments, FP64 sums, statistics.
@@ -403,10 +491,9 @@ __device__ __forceinline__ double warp_sum(double v) {
 template <int Q, class S, int PAR, int MODE>
 __global__ void __launch_bounds__(128) k_export(const __grid_constant__ KParams p, ExportArgs a) {
   LBM_CELL_COORDS
-  const S* F = static_cast<const S*>(p.f);
   float f[Q];
   unsigned outmask;
-  load_state<Q, S, PAR>(p, F, x, y, z, cell, cls, f, outmask);
+  load_state<Q, S, PAR>(p, x, y, z, cell, cls, f, outmask);
   outflow_fix<Q>(p, x, f, outmask);
   const bool fluid = cls != CLS_SKIP;
   const long long dense = ((long long)z * p.ny + y) * p.nx + x;
@@ -456,7 +543,6 @@ __global__ void __launch_bounds__(128) k_init_eq(const __grid_constant__ KParams
                                                  const float* u_in) {
   LBM_CELL_COORDS
   if (x >= p.nx) return;
-  S* F = static_cast<S*>(p.f);
   const long long dense = ((long long)z * p.ny + y) * p.nx + x;
   const long long N = (long long)p.nx * p.ny * p.nz;
   const bool fluid = cls != CLS_SKIP;
@@ -469,7 +555,7 @@ __global__ void __launch_bounds__(128) k_init_eq(const __grid_constant__ KParams
   for (int i = 0; i < Q; i++) {
     const float cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
     const float v = wgt<Q>(i) * (drho + rho * (3.f * cu + 4.5f * cu * cu - 1.5f * usq));
-    st<S>(F + (long long)i * p.plane + cell, fluid ? v : 0.f);
+    st<S>(plane_ptr<S>(p, i) + cell, fluid ? v : 0.f);
   }
 }
 
@@ -478,12 +564,11 @@ template <int Q, class S>
 __global__ void __launch_bounds__(128) k_set_pop(const __grid_constant__ KParams p, const float* df) {
   LBM_CELL_COORDS
   if (x >= p.nx) return;
-  S* F = static_cast<S*>(p.f);
   const long long dense = ((long long)z * p.ny + y) * p.nx + x;
   const long long N = (long long)p.nx * p.ny * p.nz;
   const bool fluid = cls != CLS_SKIP;
 #pragma unroll
-  for (int i = 0; i < Q; i++) st<S>(F + (long long)i * p.plane + cell, fluid ? df[i * N + dense] : 0.f);
+  for (int i = 0; i < Q; i++) st<S>(plane_ptr<S>(p, i) + cell, fluid ? df[i * N + dense] : 0.f);
 }
 
 }  // namespace lbm

@@ -148,7 +148,13 @@ def test_poiseuille_1000_steps_matches_oracle():
 
 @pytest.mark.parametrize("q", [19, 27])
 def test_poiseuille_steady_closed_form(q):
-    """Quasi-1D channel to steady state: the TRT bounce-back parabola with Lambda = 3/16."""
+    """Quasi-1D channel to steady state: the TRT bounce-back parabola with Lambda = 3/16.
+
+    Tolerance from the FP32 arithmetic: near steady state a population only moves when its
+    per-step change exceeds half an ulp, so the slowest mode (time constant
+    T = H^2 / (pi^2 nu)) can stall where its per-step drive falls below that granularity,
+    i.e. at a relative error of about T * 2^-23 (one ulp of 3 w u relative to u, times T);
+    twice that is allowed."""
     ny, tau, g = 18, 0.8, 1e-6
     nu = (tau - 0.5) / 3
     from paper_2305_09910_gb300 import lbm
@@ -161,7 +167,8 @@ def test_poiseuille_steady_closed_form(q):
     _, u = lat.moments()
     y = np.arange(ny) + 0.5
     ua = g / (2 * nu) * y * (ny - y)
-    assert np.abs(u[0, 0, :, 0] - ua).max() / ua.max() <= 2e-5
+    T = ny * ny / (np.pi ** 2 * nu)
+    assert np.abs(u[0, 0, :, 0] - ua).max() / ua.max() <= 2 * T * 2.0 ** -23
 
 
 @pytest.mark.parametrize("precision", ["f32", "f16", "bf16"])
@@ -181,13 +188,30 @@ def test_checkpoint_resume_bit_exact(precision, n):
     assert np.array_equal(a.get_populations(), b.get_populations())
 
 
+def _inflow_adjacent(case):
+    """Cells whose update may use a moving-wall (inflow) rule."""
+    nx, ny, nz = case["nx"], case["ny"], case["nz"]
+    flags = case.get("flags")
+    inflow = np.zeros((nz, ny, nx), bool) if flags is None else flags == 2
+    near = inflow.copy()
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                near |= np.roll(inflow, (dz, dy, dx), axis=(0, 1, 2))
+    if case.get("faces", ("periodic",) * 6)[0] == "inflow":
+        near[:, :, 0] = True
+    return near
+
+
 @pytest.mark.parametrize("precision,bound", [("f16", 2.0 ** -11), ("bf16", 2.0 ** -8)])
 @pytest.mark.parametrize("name", ["channel19", "tunnel27"])
 def test_half_storage_rounding_bound(precision, bound, name):
+    """One step from a state the half-precision store represents exactly: every population
+    is within one storage rounding of the oracle (two roundings, of the bounced value and of
+    the moving-wall sum, where an inflow rule applies)."""
     case = CASES[name]
     lat, ora = make_pair(precision=precision, **case)
     df = _start(lat, ora, case, seed=11)
-    # start both sides from the values the half-precision store represents
     import torch
 
     dt = torch.float16 if precision == "f16" else torch.bfloat16
@@ -199,9 +223,12 @@ def test_half_storage_rounding_bound(precision, bound, name):
     got = lat.get_populations().astype(np.float64)
     ref = ora.shifted()
     fluid = ora.flags == 0
-    err = np.abs(got - ref)[:, fluid]
-    allowed = bound * np.abs(ref)[:, fluid] + 2e-7
-    assert (err <= allowed).all(), float((err - allowed).max())
+    err = np.abs(got - ref)
+    allowed = bound * np.abs(ref) + 2e-7
+    near = _inflow_adjacent(case)
+    allowed[:, near] += bound * 0.03  # |6 w rho_w c.u_w| <= 0.03 for |u_w| <= 0.06
+    bad = (err > allowed)[:, fluid]
+    assert not bad.any(), float((err - allowed)[:, fluid].max())
 
 
 def test_full_size_channel_sampled_parity():
@@ -266,7 +293,18 @@ def test_full_size_bluff_body_sampled_parity():
                         u_w=uw, flags=flags)
     ref = ora.step_sampled(rho, u, cells) - ora.w[None, :]
     fl = flags.reshape(-1)[cells] == 0
-    assert np.abs(got - ref)[fl].max() <= 1e-6
+    err = np.abs(got - ref)
+    err[~fl] = 0.0
+    if err.max() > 1e-6:
+        k, i = np.unravel_index(np.argmax(err), err.shape)
+        cidx = int(cells[k])
+        x, y, z = cidx % nx, (cidx // nx) % ny, cidx // (nx * ny)
+        nb = flags[max(z - 1, 0):z + 2, max(y - 1, 0):y + 2, max(x - 1, 0):x + 2]
+        bad = np.argwhere(err > 1e-6)
+        worst = [(int(cells[a] % nx), int(cells[a] // nx % ny), int(cells[a] // (nx * ny)), int(b),
+                  float(err[a, b])) for a, b in bad[:12]]
+        raise AssertionError(f"max err {err.max():.3e} at cell ({x},{y},{z}) dir {i}: got {got[k, i]!r} "
+                             f"ref {ref[k, i]!r}; neighbour flags sum {int(nb.sum())}; bad {worst}")
 
 
 def test_errors_and_edge_cases():
