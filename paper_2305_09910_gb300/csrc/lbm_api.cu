@@ -107,6 +107,9 @@ static KParams kparams(const lbm_s* h) {
     const double cu = c[3 * i] * h->prm.u_inflow[0] + c[3 * i + 1] * h->prm.u_inflow[1] +
                       c[3 * i + 2] * h->prm.u_inflow[2];
     p.inflow_term[i] = (float)(6.0 * w[i] * h->prm.rho_inflow * cu);
+    const double cF = c[3 * i] * h->force[0] + c[3 * i + 1] * h->force[1] + c[3 * i + 2] * h->force[2];
+    p.F3w[i] = (float)(3.0 * w[i] * cF);
+    p.F9w[i] = (float)(9.0 * w[i] * cF);
   }
   p.mlp_scale[0] = h->mlp_scale[0];
   p.mlp_scale[1] = h->mlp_scale[1];

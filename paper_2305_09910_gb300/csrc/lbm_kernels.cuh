@@ -71,6 +71,8 @@ struct KParams {
   float tau0, lambda, cs2, omega_p, omega_m;
   float F[3];
   float inflow_term[27];  // 6 w_i rho_w (c_i . u_w)
+  float F3w[27];          // 3 w_i (c_i . F): antisymmetric Guo term
+  float F9w[27];          // 9 w_i (c_i . F): symmetric Guo term, times c_i . u
   float mlp_scale[2];
 };
 
@@ -331,7 +333,11 @@ __device__ __forceinline__ Mom<Q> moments(const KParams& p, const float (&f)[Q])
 }
 
 struct CollCtx {
-  float rho, drho, ux, uy, uz, jx, jy, jz, usq, uF, Fx, Fy, Fz, wp, wm, gp, gm;
+  float ux, uy, uz, jx, jy, jz;
+  float A, B;        // equilibrium symmetric part: w (A + B (c.u)^2), A = drho - 1.5 rho u^2, B = 4.5 rho
+  float hwp, hwm;    // omega+/2, omega-/2
+  float gp, gm;      // 1 - omega+/2, 1 - omega-/2
+  float gu3;         // (1 - omega+/2) 3 u.F
 };
 
 // Sums over the +/- pairs: s_P = f_i + f_opp(i), d_P = f_i - f_opp(i) (i = 2P+1).
@@ -365,28 +371,30 @@ __device__ __forceinline__ void all_pair_moments(const float (&f)[Q], float (&m)
 // from f first, where the operands nearly cancel.  This keeps the per-step momentum error
 // at the level of one rounding of f, which matters at the small velocities of laminar runs.
 template <int Q, int I>
-__device__ __forceinline__ void trt_pair(float (&f)[Q], const CollCtx& c) {
+__device__ __forceinline__ void trt_pair(const KParams& p, float (&f)[Q], const CollCtx& c) {
   constexpr int X = cx(I), Y = cy(I), Z = cz(I);
   constexpr float w = (float)wgt_d<Q>(I);
   constexpr float khi = (float)(3.0 * wgt_d<Q>(I));
   constexpr float klo = (float)(3.0 * wgt_d<Q>(I) - (double)khi);
   const float cu = X * c.ux + Y * c.uy + Z * c.uz;
   const float cj = X * c.jx + Y * c.jy + Z * c.jz;
-  const float cF = X * c.Fx + Y * c.Fy + Z * c.Fz;
   const float eh = cj * khi;
   const float el = fmaf(cj, klo, fmaf(cj, khi, -eh));
-  const float es = w * (c.drho + c.rho * (4.5f * cu * cu - 1.5f * c.usq));
+  const float es = w * fmaf(c.B, cu * cu, c.A);
   const float ni = ((f[I] - eh) - el) - es;
   const float nj = ((f[I + 1] + eh) + el) - es;
-  const float ds = -c.wp * (0.5f * (ni + nj)) + c.gp * (w * (9.f * cu * cF - 3.f * c.uF));
-  const float da = -c.wm * (0.5f * (ni - nj)) + c.gm * (w * 3.f * cF);
+  // Guo terms: symmetric w (9 (c.u)(c.F) - 3 u.F), antisymmetric 3 w (c.F)
+  const float fsym = fmaf(c.gp * p.F9w[I], cu, -w * c.gu3);
+  const float ds = fmaf(-c.hwp, ni + nj, fsym);
+  const float da = fmaf(-c.hwm, ni - nj, c.gm * p.F3w[I]);
   f[I] = f[I] + (ds + da);
   f[I + 1] = f[I + 1] + (ds - da);
 }
 
 template <int Q, int... P>
-__device__ __forceinline__ void trt_pairs(float (&f)[Q], const CollCtx& c, std::integer_sequence<int, P...>) {
-  (trt_pair<Q, 2 * P + 1>(f, c), ...);
+__device__ __forceinline__ void trt_pairs(const KParams& p, float (&f)[Q], const CollCtx& c,
+                                          std::integer_sequence<int, P...>) {
+  (trt_pair<Q, 2 * P + 1>(p, f, c), ...);
 }
 
 // sqrt of a non-negative value from the hardware reciprocal square root (x = 0 gives 0).
@@ -423,29 +431,27 @@ __device__ __forceinline__ float collide(const KParams& p, float (&f)[Q]) {
     wm = __fdividef(1.f, __fdividef(p.lambda, tau - 0.5f) + 0.5f);
   }
   CollCtx c;
-  c.rho = rho;
-  c.drho = drho;
   c.ux = ux;
   c.uy = uy;
   c.uz = uz;
   c.jx = jx;
   c.jy = jy;
   c.jz = jz;
-  c.usq = ux * ux + uy * uy + uz * uz;
-  c.Fx = p.F[0];
-  c.Fy = p.F[1];
-  c.Fz = p.F[2];
-  c.uF = ux * c.Fx + uy * c.Fy + uz * c.Fz;
-  c.wp = wp;
-  c.wm = wm;
-  c.gp = 1.f - 0.5f * wp;
-  c.gm = 1.f - 0.5f * wm;
+  const float usq = ux * ux + uy * uy + uz * uz;
+  const float uF = ux * p.F[0] + uy * p.F[1] + uz * p.F[2];
+  c.A = drho - 1.5f * rho * usq;
+  c.B = 4.5f * rho;
+  c.hwp = 0.5f * wp;
+  c.hwm = 0.5f * wm;
+  c.gp = 1.f - c.hwp;
+  c.gm = 1.f - c.hwm;
+  c.gu3 = c.gp * 3.f * uF;
   {
     constexpr float w0 = (float)wgt_d<Q>(0);
-    const float n0 = f[0] - w0 * (drho - 1.5f * rho * c.usq);
-    f[0] = f[0] + (-wp * n0 + c.gp * (w0 * (-3.f * c.uF)));
+    const float n0 = f[0] - w0 * c.A;
+    f[0] = f[0] + (-wp * n0 - w0 * c.gu3);
   }
-  trt_pairs<Q>(f, c, Pairs{});
+  trt_pairs<Q>(p, f, c, Pairs{});
   return rho;
 }
 
