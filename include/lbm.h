@@ -186,6 +186,30 @@ lbm_status lbm_set_closure(lbm_handle h, const uint16_t* bf16_params, int n, dou
  * bytes moved per lattice update of the stepping kernel (2 q s + 1 flag byte). */
 lbm_status lbm_info(lbm_handle h, int* nxp, int* bytes_per_pop, double* bytes_per_update);
 
+/* lbm_reduce_noalloc: the sums of lbm_reduce (out[0] = sum rho, out[1..3] = sum rho u over
+ * fluid cells, FP64) computed from populations the caller already holds, without allocating
+ * any host or device memory.  The paper has no counterpart: this exists for callers that may
+ * not allocate device memory where they need the sums (e.g. an analysis hook inside another
+ * application's time loop on a GPU whose free memory that application's allocator owns, or
+ * a process held to a fixed device-memory budget), since creating a handle allocates.
+ *   df      device pointer, shifted float32 populations [q][nz][ny][nx] (the layout
+ *           lbm_get_populations writes); caller-owned, read only.
+ *   flags   device pointer to nx*ny*nz uint8 cell flags, or NULL for all fluid.
+ *   force   body-force density (3 doubles, host) used for rho u = sum c f + F/2, or NULL.
+ *   out     4 doubles, host or device memory; written before the call returns.
+ *   stream  cudaStream_t the work is ordered on (NULL = legacy default stream); the call
+ *           synchronises it before returning.
+ * Scratch: a static device array of LBM_NOALLOC_MAX_PARTIALS * 4 + 4 doubles (512 KiB) that
+ * every GPU loading the library keeps until exit.  Lattices of more than
+ * LBM_NOALLOC_MAX_PARTIALS * 16384 cells (2^28) are rejected with LBM_EINVAL and a message in
+ * lbm_last_error(NULL).  The first call on a device (with that device current) looks up the
+ * array's device address; make that first call before any stream capture.  All calls share
+ * the array, so calls whose GPU work overlaps race with each other.  No cudaMalloc, cudaFree
+ * or allocating library call is made. */
+#define LBM_NOALLOC_MAX_PARTIALS 16384
+lbm_status lbm_reduce_noalloc(const float* df, const uint8_t* flags, int nx, int ny, int nz,
+                              int stencil, const double force[3], double out[4], void* stream);
+
 /* Message for the last failing call on h (or on creation when h is NULL). */
 const char* lbm_last_error(lbm_handle h);
 

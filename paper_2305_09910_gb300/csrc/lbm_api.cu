@@ -39,6 +39,8 @@ struct lbm_s {
 
 static std::string g_create_error;
 
+void lbm_internal_set_error(const char* msg) { g_create_error = msg; }
+
 static lbm_status fail(lbm_handle h, lbm_status s, const char* fmt, ...) {
   char buf[512];
   va_list ap;

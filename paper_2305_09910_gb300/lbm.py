@@ -91,6 +91,7 @@ def load():
             "lbm_set_closure": (I, [H, P, I, D, D]),
             "lbm_info": (I, [H, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]),
             "lbm_last_error": (ctypes.c_char_p, [H]),
+            "lbm_reduce_noalloc": (I, [P, P, I, I, I, I, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -258,6 +259,22 @@ def lbm_info(h):
     nxp, bpp, bpu = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
     _check(load().lbm_info(h, ctypes.byref(nxp), ctypes.byref(bpp), ctypes.byref(bpu)), h)
     return nxp.value, bpp.value, bpu.value
+
+
+def lbm_reduce_noalloc(df, flags, nx, ny, nz, stencil, force=(0.0, 0.0, 0.0), stream=None):
+    """FP64 sums of a caller-held population array without any allocation by the library
+    (out is a host array owned here).  df and flags must be CUDA tensors."""
+    pd, dd = _buf(df, np.float32)
+    pf, df_ = _buf(flags, np.uint8) if flags is not None else (None, 1)
+    if not dd or not df_:
+        raise ValueError("df and flags must be device buffers")
+    fv = np.ascontiguousarray(force, dtype=np.float64)
+    out = np.zeros(4, dtype=np.float64)
+    st = stream if stream is not None else _current_stream()
+    _check(load().lbm_reduce_noalloc(pd, pf, int(nx), int(ny), int(nz), int(stencil),
+                                     fv.ctypes.data_as(ctypes.c_void_p),
+                                     out.ctypes.data_as(ctypes.c_void_p), st), None)
+    return out
 
 
 def lbm_last_error(h=None) -> str:
