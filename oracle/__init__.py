@@ -87,6 +87,11 @@ def lib():
             L.ora_mlp_forward.restype = ctypes.c_double
             L.ora_mlp_backward.argtypes = [P, P, ctypes.c_double, P]
             L.ora_mlp_features.argtypes = [P, P, P]
+            L.ora_closure_samples.argtypes = [P, P, ctypes.c_double, ctypes.c_double, P, P, P, P, P]
+            L.ora_closure_loss.argtypes = [P, P, P, P, P, ctypes.c_int64, ctypes.c_double, P]
+            L.ora_closure_loss.restype = ctypes.c_double
+            L.ora_adam.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_double, ctypes.c_int64]
             _lib = L
     return _lib
 
@@ -128,6 +133,28 @@ def mlp_backward(params: np.ndarray, x: np.ndarray, dy: float) -> np.ndarray:
     g = np.zeros(MLP_NPARAM, dtype=np.float64)
     lib().ora_mlp_backward(_ptr(params), _ptr(x), float(dy), _ptr(g))
     return g
+
+
+def closure_loss(params, x, target, smag, weight, cs0):
+    """(L, dL/dparams) of the weighted eddy-viscosity MSE (FP64)."""
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    t = np.ascontiguousarray(target, dtype=np.float64)
+    sm = np.ascontiguousarray(smag, dtype=np.float64)
+    w = np.ascontiguousarray(weight, dtype=np.float64)
+    g = np.zeros(MLP_NPARAM, dtype=np.float64)
+    loss = lib().ora_closure_loss(_ptr(params), _ptr(x), _ptr(t), _ptr(sm), _ptr(w), t.size,
+                                  float(cs0), _ptr(g))
+    return loss, g
+
+
+def adam(p, g, m, v, lr, t, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step in place on float64 arrays p, m, v (t is 1-based)."""
+    for a in (p, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    lib().ora_adam(_ptr(p), _ptr(g), _ptr(m), _ptr(v), p.size, float(lr), float(beta1),
+                   float(beta2), float(eps), int(t))
 
 
 class Oracle:
@@ -236,6 +263,18 @@ class Oracle:
         x = np.zeros(7, dtype=np.float64)
         lib().ora_mlp_features(ctypes.byref(self.cfg), _ptr(f), _ptr(x))
         return x
+
+    def closure_samples(self, tau0_c, cs0, scale=(1.0, 1.0)):
+        """Box-filter-2 training samples for the coarse grid from the current state.
+
+        Returns x (nc, 7), target nu*, |S_c|, weight, with nc = (nx/2)(ny/2)(nz/2)."""
+        nc = (self.nx // 2) * (self.ny // 2) * (self.nz // 2)
+        x = np.zeros((nc, 7))
+        t, sm, w = np.zeros(nc), np.zeros(nc), np.zeros(nc)
+        sc = np.ascontiguousarray(scale, dtype=np.float64)
+        lib().ora_closure_samples(ctypes.byref(self.cfg), _ptr(self.f), float(tau0_c), float(cs0),
+                                  _ptr(sc), _ptr(x), _ptr(t), _ptr(sm), _ptr(w))
+        return x, t, sm, w
 
     def step_sampled(self, rho_in, u_in, cells):
         """One step from f = f^eq(rho_in, u_in) (float32 fields), at the listed linear cells.

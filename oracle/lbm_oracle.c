@@ -500,3 +500,103 @@ void ora_stats_sample(const ora_cfg* cfg, const double* f, double* acc) {
         a[9] += u[1] * u[2];
       }
 }
+
+/* ---- learned closure ------------------------------------------------------------------- */
+
+static double sigmoid(double y) { return 1.0 / (1.0 + exp(-y)); }
+
+void ora_closure_samples(const ora_cfg* fine, const double* f, double tau0_c, double cs0,
+                         const double* scale, double* x, double* target, double* smag,
+                         double* weight) {
+  const int q = fine->q;
+  const int ncx = fine->nx / 2, ncy = fine->ny / 2, ncz = fine->nz / 2;
+  const int64_t N = (int64_t)fine->nx * fine->ny * fine->nz;
+  static const int A[6] = {0, 1, 2, 0, 0, 1}, B[6] = {0, 1, 2, 1, 2, 2};
+  for (int Z = 0; Z < ncz; Z++)
+    for (int Y = 0; Y < ncy; Y++)
+      for (int X = 0; X < ncx; X++) {
+        const int64_t k = ((int64_t)Z * ncy + Y) * ncx + X;
+        double rho_s = 0.0, m_s[3] = {0, 0, 0}, ruu_s[6] = {0, 0, 0, 0, 0, 0};
+        double S_s[6] = {0, 0, 0, 0, 0, 0}, nS_s[6] = {0, 0, 0, 0, 0, 0};
+        for (int c = 0; c < 2; c++)
+          for (int b = 0; b < 2; b++)
+            for (int a = 0; a < 2; a++) {
+              const int fx = 2 * X + a, fy = 2 * Y + b, fz = 2 * Z + c;
+              const int64_t cell = ((int64_t)fz * fine->ny + fy) * fine->nx + fx;
+              double fl[27], rho, u[3], feq[27], pi[6];
+              for (int i = 0; i < q; i++) fl[i] = f[i * N + cell];
+              ora_moments_cell(fine, fl, &rho, u);
+              ora_equilibrium(q, rho, u, feq);
+              noneq_stress(q, fl, feq, pi);
+              double qn = pi[0] * pi[0] + pi[1] * pi[1] + pi[2] * pi[2] +
+                          2.0 * (pi[3] * pi[3] + pi[4] * pi[4] + pi[5] * pi[5]);
+              double tau = fine->closure == ORA_CLOSURE_SMAG
+                               ? ora_smag_tau(fine->tau, fine->cs * fine->cs, qn, rho)
+                               : fine->tau;
+              double nut = (tau - fine->tau) / 3.0;
+              rho_s += rho;
+              for (int d = 0; d < 3; d++) m_s[d] += rho * u[d];
+              for (int j = 0; j < 6; j++) {
+                const double S = -3.0 * pi[j] / (2.0 * rho * tau);
+                ruu_s[j] += rho * u[A[j]] * u[B[j]];
+                S_s[j] += S;
+                nS_s[j] += nut * S;
+              }
+            }
+        const double rb = rho_s / 8.0;
+        double ub[3], tsg[6], Sc[6];
+        for (int d = 0; d < 3; d++) ub[d] = m_s[d] / 8.0 / rb;
+        for (int j = 0; j < 6; j++) {
+          tsg[j] = ruu_s[j] / 8.0 / rb - ub[A[j]] * ub[B[j]] - 2.0 * nS_s[j] / 8.0;
+          Sc[j] = 2.0 * S_s[j] / 8.0;
+        }
+        const double tr = (tsg[0] + tsg[1] + tsg[2]) / 3.0;
+        double num = 0.0, den = 0.0;
+        for (int j = 0; j < 6; j++) {
+          const double mult = j < 3 ? 1.0 : 2.0;
+          const double td = j < 3 ? tsg[j] - tr : tsg[j];
+          num += mult * td * Sc[j];
+          den += mult * Sc[j] * Sc[j];
+        }
+        const double Smag = sqrt(2.0 * den);
+        /* no strain (below round-off level): the projection is undefined, take nu* = 0 */
+        double nu = Smag > 1e-10 ? -num / (2.0 * den) : 0.0;
+        if (nu < 0.0) nu = 0.0;
+        const double tauc = tau0_c + 3.0 * cs0 * cs0 * Smag;
+        for (int j = 0; j < 6; j++) x[k * 7 + j] = scale[0] * (-(2.0 * rb / 3.0) * tauc * Sc[j]);
+        x[k * 7 + 6] = scale[1] * (rb - 1.0);
+        target[k] = nu;
+        smag[k] = Smag;
+        weight[k] = Smag * Smag;
+      }
+}
+
+double ora_closure_loss(const double* p, const double* x, const double* target,
+                        const double* smag, const double* weight, int64_t n, double cs0,
+                        double* grad) {
+  const double k = cs0 * cs0 / log(2.0);
+  double wsum = 0.0, loss = 0.0;
+  for (int64_t s = 0; s < n; s++) wsum += weight[s];
+  for (int j = 0; j < ORA_MLP_NPARAM; j++) grad[j] = 0.0;
+  if (wsum <= 0.0) return 0.0;
+  for (int64_t s = 0; s < n; s++) {
+    const double y = ora_mlp_forward(p, x + s * 7, NULL, NULL, NULL, NULL);
+    const double nu = softplus(y) * k * smag[s];
+    const double r = nu - target[s];
+    loss += weight[s] * r * r;
+    const double dy = 2.0 * weight[s] * r * k * smag[s] * sigmoid(y) / wsum;
+    ora_mlp_backward(p, x + s * 7, dy, grad);
+  }
+  return loss / wsum;
+}
+
+void ora_adam(double* p, const double* g, double* m, double* v, int64_t n, double lr,
+              double beta1, double beta2, double eps, int64_t t) {
+  const double c1 = 1.0 - pow(beta1, (double)t), c2 = 1.0 - pow(beta2, (double)t);
+  for (int64_t j = 0; j < n; j++) {
+    m[j] = beta1 * m[j] + (1.0 - beta1) * g[j];
+    v[j] = beta2 * v[j] + (1.0 - beta2) * g[j] * g[j];
+    const double mh = m[j] / c1, vh = v[j] / c2;
+    p[j] -= lr * mh / (sqrt(vh) + eps);
+  }
+}

@@ -117,6 +117,35 @@ void ora_mlp_backward(const double* p, const double* x, double dy, double* grad)
 /* Closure features of one cell: scaled non-equilibrium stress and density deviation. */
 void ora_mlp_features(const ora_cfg* cfg, const double* f, double* x);
 
+/* ---- learned closure: training data, loss, optimiser ------------------------------------
+ * Samples for the coarse grid (half the fine resolution in each axis) from one fine state,
+ * by a box filter of width 2.  For each coarse cell (8 fine cells) the fine solver's local
+ * quantities are averaged: density, momentum, rho u u, strain rate estimated from the
+ * non-equilibrium stress S_f = -3 Pi_f / (2 rho tau_eff), and the fine Smagorinsky stress
+ * -2 nu_t,f S_f.  The unresolved stress on the coarse grid is
+ *   tau_sgs = <rho u u>/<rho> - u_bar u_bar - 2 <nu_t,f S_f>,
+ * the coarse strain rate is S_c = 2 <S_f> (one coarse step = two fine steps, acoustic
+ * scaling), and the target eddy viscosity is the least-squares projection of the
+ * deviatoric tau_sgs on S_c, nu* = -(tau_sgs^d : S_c) / (2 S_c : S_c), clipped at 0
+ * (and 0 where |S_c| <= 1e-10, below the round-off of the strain estimate).
+ * Features are what the coarse solver sees: Pi_c = -(2 rho_bar / 3) tau_c S_c with the
+ * coarse Smagorinsky relaxation time tau_c = tau0_c + 3 cs0^2 |S_c|, |S| = sqrt(2 S:S),
+ * scaled like ora_mlp_features.  Per sample: x[7], target nu*, |S_c|, weight |S_c|^2. */
+void ora_closure_samples(const ora_cfg* fine, const double* f, double tau0_c, double cs0,
+                         const double* scale, double* x /* nc*7 */, double* target,
+                         double* smag /* |S_c| */, double* weight);
+
+/* Weighted mean-square error of the predicted eddy viscosity and its gradient:
+ *   nu = softplus(y) cs0^2 / ln 2 * |S|,  L = sum w (nu - nu*)^2 / sum w.
+ * grad (ORA_MLP_NPARAM, overwritten) = dL/dparams.  Returns L. */
+double ora_closure_loss(const double* p, const double* x, const double* target,
+                        const double* smag, const double* weight, int64_t n, double cs0,
+                        double* grad);
+
+/* One Adam step (Kingma and Ba 2015) on n parameters; t is the 1-based step count. */
+void ora_adam(double* p, const double* g, double* m, double* v, int64_t n, double lr,
+              double beta1, double beta2, double eps, int64_t t);
+
 #ifdef __cplusplus
 }
 #endif
