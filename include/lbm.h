@@ -97,7 +97,7 @@ enum { LBM_CELL_FLUID = 0, LBM_CELL_SOLID = 1, LBM_CELL_INFLOW = 2 };
 
 /* MLP closure parameters: 7 -> 32 -> 32 -> 1, packed W1[32][7], b1[32], W2[32][32], b2[32],
  * W3[32], b3 (bfloat16 bit patterns).  Features: Pi^neq_{xx,yy,zz,xy,xz,yz} * scale_pi and
- * (rho - 1) * scale_rho.  C_s^2(x) = softplus(y) * cs_smag^2 / ln 2 (y = 0 gives cs_smag^2). */
+ * (rho - 1) * scale_rho, each clipped to [-8, 8].  C_s^2(x) = softplus(y) * cs_smag^2 / ln 2 (y = 0 gives cs_smag^2). */
 #define LBM_MLP_NPARAM 1345
 
 /* Number of doubles per y-plane in the turbulence statistics:
@@ -181,6 +181,57 @@ lbm_status lbm_stats_get(lbm_handle h, double* out, int64_t* nsamples);
  * scales.  Needed before stepping with closure LBM_CLOSURE_MLP. */
 lbm_status lbm_set_closure(lbm_handle h, const uint16_t* bf16_params, int n, double scale_pi,
                            double scale_rho);
+
+/* As lbm_set_closure, from float32 parameters (host or device), rounded to bfloat16 with
+ * round-to-nearest-even. */
+lbm_status lbm_set_closure_f32(lbm_handle h, const float* params, int on_device, double scale_pi,
+                               double scale_rho);
+
+/* Lower bound on the learned coefficient: C_s^2(x) = max(network value, cs_min^2) (default
+ * cs_min = 0, no bound).  A safeguard for coarse runs near tau = 1/2, where a learned eddy
+ * viscosity below the Smagorinsky one can leave too little dissipation. */
+lbm_status lbm_set_closure_floor(lbm_handle h, double cs_min);
+
+/* ---- learned-closure training (all array arguments are caller-owned DEVICE pointers) ----
+ * The closure's network is trained on pairs the solver generates: a fine lattice is
+ * box-filtered (width 2) onto the coarse grid.  Per coarse cell (8 fine cells) the fine
+ * solver's density, momentum, rho u u, strain rate S_f = -3 Pi^neq / (2 rho tau_eff) and
+ * Smagorinsky stress -2 nu_t S_f are averaged; the unresolved stress is
+ * tau_sgs = <rho u u>/<rho> - u_bar u_bar - 2 <nu_t S_f>; the coarse strain rate is
+ * S_c = 2 <S_f> (one coarse step spans two fine steps); the target eddy viscosity is
+ * nu* = max(0, -(tau_sgs^d : S_c) / (2 S_c : S_c)) (0 where |S_c| <= 1e-10), and the
+ * features are those the coarse solver sees: Pi_c = -(2 rho_bar/3) tau_c S_c with
+ * tau_c = tau0_c + 3 cs0^2 |S_c|, scaled by scale[0], and (rho_bar - 1) * scale[1].
+ * Outputs (nc = (nx/2)(ny/2)(nz/2) coarse cells, x fastest): x[nc][7], target[nc],
+ * smag[nc] = |S_c| = sqrt(2 S_c:S_c), weight[nc] = |S_c|^2 (0 where a fine cell is not
+ * fluid).  Needs even sizes and no outflow face (EUNSUPPORTED).  Asynchronous on the
+ * fine handle's stream. */
+lbm_status lbm_closure_samples(lbm_handle fine, double tau0_c, double cs0, const double scale[2],
+                               float* x, float* target, float* smag, float* weight);
+
+/* Box filter of width 2 of the fine state (device outputs, nc coarse cells as above):
+ * rho_bar = mean density of the 8 fine cells, u_bar = <rho u> / <rho> (Favre, [3][nc]).
+ * Needs even sizes and no outflow face.  Asynchronous on the fine handle's stream. */
+lbm_status lbm_filter2(lbm_handle fine, float* rho_bar, float* u_bar);
+
+/* Network output y for n samples x[n][7] (parameters: LBM_MLP_NPARAM floats). */
+lbm_status lbm_mlp_forward(const float* params, const float* x, int64_t n, float* y, void* stream);
+
+/* grad = sum_s dy[s] d y_s / d params (overwritten). */
+lbm_status lbm_mlp_backward(const float* params, const float* x, const float* dy, int64_t n,
+                            float* grad, void* stream);
+
+/* Weighted mean-square error of the predicted eddy viscosity over the batch of samples
+ * offset + s * stride (s < n):  nu = softplus(y) cs0^2/ln 2 * smag,
+ * L = sum w (nu - target)^2 / sum w.  grad (overwritten) = dL/dparams; *loss (host or
+ * device double) = L.  Synchronises the stream. */
+lbm_status lbm_closure_loss_grad(const float* params, const float* x, const float* target,
+                                 const float* smag, const float* weight, int64_t n, int64_t offset,
+                                 int64_t stride, double cs0, float* grad, double* loss, void* stream);
+
+/* One Adam step (Kingma and Ba) on n parameters; t is the 1-based step count. */
+lbm_status lbm_adam_step(float* params, const float* grad, float* m, float* v, int n, double lr,
+                         double beta1, double beta2, double eps, int64_t t, void* stream);
 
 /* Sizes of the handle: padded row length nxp, bytes of one stored population, algorithmic
  * bytes moved per lattice update of the stepping kernel (2 q s + 1 flag byte). */

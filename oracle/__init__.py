@@ -59,6 +59,7 @@ class _Cfg(ctypes.Structure):
         ("flags", ctypes.c_void_p),
         ("mlp", ctypes.c_void_p),
         ("mlp_scale", ctypes.c_double * 2),
+        ("mlp_cs_min", ctypes.c_double),
     ]
 
 
@@ -90,6 +91,7 @@ def lib():
             L.ora_closure_samples.argtypes = [P, P, ctypes.c_double, ctypes.c_double, P, P, P, P, P]
             L.ora_closure_loss.argtypes = [P, P, P, P, P, ctypes.c_int64, ctypes.c_double, P]
             L.ora_closure_loss.restype = ctypes.c_double
+            L.ora_filter2.argtypes = [P, P, P, P]
             L.ora_adam.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                                    ctypes.c_double, ctypes.c_double, ctypes.c_int64]
             _lib = L
@@ -162,7 +164,7 @@ class Oracle:
 
     def __init__(self, nx, ny, nz, q=19, tau=0.8, lam=3.0 / 16.0, closure="none", cs=0.0,
                  faces=("periodic",) * 6, u_w=(0.0, 0.0, 0.0), rho_w=1.0,
-                 force=(0.0, 0.0, 0.0), flags=None, mlp=None, mlp_scale=(1.0, 1.0)):
+                 force=(0.0, 0.0, 0.0), flags=None, mlp=None, mlp_scale=(1.0, 1.0), mlp_cs_min=0.0):
         self.nx, self.ny, self.nz, self.q = int(nx), int(ny), int(nz), int(q)
         self.N = self.nx * self.ny * self.nz
         self._flags = None
@@ -188,6 +190,7 @@ class Oracle:
         c.flags = None if self._flags is None else self._flags.ctypes.data
         c.mlp = None if self._mlp is None else self._mlp.ctypes.data
         c.mlp_scale[0], c.mlp_scale[1] = float(mlp_scale[0]), float(mlp_scale[1])
+        c.mlp_cs_min = float(mlp_cs_min)
         self.cfg = c
         rc = lib().ora_check(ctypes.byref(c))
         if rc != 0:
@@ -275,6 +278,14 @@ class Oracle:
         lib().ora_closure_samples(ctypes.byref(self.cfg), _ptr(self.f), float(tau0_c), float(cs0),
                                   _ptr(sc), _ptr(x), _ptr(t), _ptr(sm), _ptr(w))
         return x, t, sm, w
+
+    def filter2(self):
+        """Box-filter-2 density (nzc, nyc, nxc) and Favre velocity (3, nzc, nyc, nxc)."""
+        shp = (self.nz // 2, self.ny // 2, self.nx // 2)
+        rb = np.zeros(shp)
+        ub = np.zeros((3,) + shp)
+        lib().ora_filter2(ctypes.byref(self.cfg), _ptr(self.f), _ptr(rb), _ptr(ub))
+        return rb, ub
 
     def step_sampled(self, rho_in, u_in, cells):
         """One step from f = f^eq(rho_in, u_in) (float32 fields), at the listed linear cells.

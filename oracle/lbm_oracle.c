@@ -130,6 +130,9 @@ static double gelu_grad(double a) {
 
 static double softplus(double y) { return (y > 0.0 ? y : 0.0) + log1p(exp(-fabs(y))); }
 
+/* scaled closure features are clipped to [-8, 8] */
+static double xclamp(double v) { return v < -8.0 ? -8.0 : (v > 8.0 ? 8.0 : v); }
+
 double ora_mlp_forward(const double* p, const double* x, double* a1, double* h1, double* a2,
                        double* h2) {
   const double* W1 = p;
@@ -201,8 +204,8 @@ void ora_mlp_features(const ora_cfg* cfg, const double* f, double* x) {
   ora_moments_cell(cfg, f, &rho, u);
   ora_equilibrium(cfg->q, rho, u, feq);
   noneq_stress(cfg->q, f, feq, pi);
-  for (int k = 0; k < 6; k++) x[k] = cfg->mlp_scale[0] * pi[k];
-  x[6] = cfg->mlp_scale[1] * (rho - 1.0);
+  for (int k = 0; k < 6; k++) x[k] = xclamp(cfg->mlp_scale[0] * pi[k]);
+  x[6] = xclamp(cfg->mlp_scale[1] * (rho - 1.0));
 }
 
 void ora_collide(const ora_cfg* cfg, const double* f, double* fstar, double* tau_eff) {
@@ -222,10 +225,11 @@ void ora_collide(const ora_cfg* cfg, const double* f, double* fstar, double* tau
       cs2 = cfg->cs * cfg->cs;
     } else {
       double x[ORA_MLP_NIN];
-      for (int k = 0; k < 6; k++) x[k] = cfg->mlp_scale[0] * pi[k];
-      x[6] = cfg->mlp_scale[1] * (rho - 1.0);
+      for (int k = 0; k < 6; k++) x[k] = xclamp(cfg->mlp_scale[0] * pi[k]);
+      x[6] = xclamp(cfg->mlp_scale[1] * (rho - 1.0));
       double y = ora_mlp_forward(cfg->mlp, x, NULL, NULL, NULL, NULL);
       cs2 = softplus(y) * cfg->cs * cfg->cs / log(2.0);
+      if (cs2 < cfg->mlp_cs_min * cfg->mlp_cs_min) cs2 = cfg->mlp_cs_min * cfg->mlp_cs_min;
     }
     tau = ora_smag_tau(cfg->tau, cs2, qn, rho);
   }
@@ -563,8 +567,8 @@ void ora_closure_samples(const ora_cfg* fine, const double* f, double tau0_c, do
         double nu = Smag > 1e-10 ? -num / (2.0 * den) : 0.0;
         if (nu < 0.0) nu = 0.0;
         const double tauc = tau0_c + 3.0 * cs0 * cs0 * Smag;
-        for (int j = 0; j < 6; j++) x[k * 7 + j] = scale[0] * (-(2.0 * rb / 3.0) * tauc * Sc[j]);
-        x[k * 7 + 6] = scale[1] * (rb - 1.0);
+        for (int j = 0; j < 6; j++) x[k * 7 + j] = xclamp(scale[0] * (-(2.0 * rb / 3.0) * tauc * Sc[j]));
+        x[k * 7 + 6] = xclamp(scale[1] * (rb - 1.0));
         target[k] = nu;
         smag[k] = Smag;
         weight[k] = Smag * Smag;
@@ -599,4 +603,28 @@ void ora_adam(double* p, const double* g, double* m, double* v, int64_t n, doubl
     const double mh = m[j] / c1, vh = v[j] / c2;
     p[j] -= lr * mh / (sqrt(vh) + eps);
   }
+}
+
+void ora_filter2(const ora_cfg* fine, const double* f, double* rho_bar, double* u_bar) {
+  const int q = fine->q;
+  const int ncx = fine->nx / 2, ncy = fine->ny / 2, ncz = fine->nz / 2;
+  const int64_t N = (int64_t)fine->nx * fine->ny * fine->nz, nc = (int64_t)ncx * ncy * ncz;
+  for (int Z = 0; Z < ncz; Z++)
+    for (int Y = 0; Y < ncy; Y++)
+      for (int X = 0; X < ncx; X++) {
+        const int64_t k = ((int64_t)Z * ncy + Y) * ncx + X;
+        double rs = 0.0, ms[3] = {0.0, 0.0, 0.0};
+        for (int c = 0; c < 8; c++) {
+          const int64_t cell = ((int64_t)(2 * Z + (c >> 2)) * fine->ny + 2 * Y + ((c >> 1) & 1)) * fine->nx +
+                               2 * X + (c & 1);
+          if (fine->flags && fine->flags[cell] != ORA_CELL_FLUID) continue;
+          double fl[27], rho, u[3];
+          for (int i = 0; i < q; i++) fl[i] = f[i * N + cell];
+          ora_moments_cell(fine, fl, &rho, u);
+          rs += rho;
+          for (int d = 0; d < 3; d++) ms[d] += rho * u[d];
+        }
+        rho_bar[k] = rs / 8.0;
+        for (int d = 0; d < 3; d++) u_bar[d * nc + k] = rs > 0.0 ? ms[d] / rs : 0.0;
+      }
 }

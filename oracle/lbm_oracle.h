@@ -59,6 +59,7 @@ typedef struct {
   const uint8_t* flags; /* nx*ny*nz cell flags, NULL = all fluid */
   const double* mlp;    /* ORA_MLP_NPARAM parameters (closure MLP) */
   double mlp_scale[2];  /* feature scales: stress components, density deviation */
+  double mlp_cs_min;    /* lower bound on the learned C_s (0: none) */
 } ora_cfg;
 
 /* Direction table in the published order; returns q or 0 on a bad q. */
@@ -114,7 +115,8 @@ double ora_mlp_forward(const double* p, const double* x, double* a1, double* h1,
                        double* h2);
 /* Gradient of y with respect to all parameters (added into grad), times dy. */
 void ora_mlp_backward(const double* p, const double* x, double dy, double* grad);
-/* Closure features of one cell: scaled non-equilibrium stress and density deviation. */
+/* Closure features of one cell: scaled non-equilibrium stress and density deviation, each
+ * clipped to [-8, 8]. */
 void ora_mlp_features(const ora_cfg* cfg, const double* f, double* x);
 
 /* ---- learned closure: training data, loss, optimiser ------------------------------------
@@ -130,10 +132,14 @@ void ora_mlp_features(const ora_cfg* cfg, const double* f, double* x);
  * (and 0 where |S_c| <= 1e-10, below the round-off of the strain estimate).
  * Features are what the coarse solver sees: Pi_c = -(2 rho_bar / 3) tau_c S_c with the
  * coarse Smagorinsky relaxation time tau_c = tau0_c + 3 cs0^2 |S_c|, |S| = sqrt(2 S:S),
- * scaled like ora_mlp_features.  Per sample: x[7], target nu*, |S_c|, weight |S_c|^2. */
+ * scaled like ora_mlp_features (and, like them, clipped to [-8, 8]).  Per sample: x[7], target nu*, |S_c|, weight |S_c|^2. */
 void ora_closure_samples(const ora_cfg* fine, const double* f, double tau0_c, double cs0,
                          const double* scale, double* x /* nc*7 */, double* target,
                          double* smag /* |S_c| */, double* weight);
+
+/* Box filter of width 2: per coarse cell the mean density and the Favre-averaged velocity
+ * <rho u> / <rho> of its 8 fine cells (u including +F/2).  rho_bar nc, u_bar 3*nc (SoA). */
+void ora_filter2(const ora_cfg* fine, const double* f, double* rho_bar, double* u_bar);
 
 /* Weighted mean-square error of the predicted eddy viscosity and its gradient:
  *   nu = softplus(y) cs0^2 / ln 2 * |S|,  L = sum w (nu - nu*)^2 / sum w.

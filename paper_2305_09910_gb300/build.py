@@ -60,7 +60,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
     jobs = [(os.path.join(CSRC, "lbm_api.cu"), os.path.join(BUILD, "lbm_api.o"), []),
-            (os.path.join(CSRC, "lbm_noalloc.cu"), os.path.join(BUILD, "lbm_noalloc.o"), [])]
+            (os.path.join(CSRC, "lbm_noalloc.cu"), os.path.join(BUILD, "lbm_noalloc.o"), []),
+            (os.path.join(CSRC, "lbm_closure.cu"), os.path.join(BUILD, "lbm_closure.o"), [])]
     for q, s in INSTANCES:
         tag = s.strip("_").replace("nv_", "")
         jobs.append((os.path.join(CSRC, "kern_inst.cu"), os.path.join(BUILD, f"kern_q{q}_{tag}.o"),

@@ -29,6 +29,7 @@ struct lbm_s {
   double* stats = nullptr;    // ny * LBM_STATS_K doubles
   float* mlp = nullptr;       // MLP parameters widened to float
   float mlp_scale[2] = {0.f, 0.f};
+  double cs_min = 0.0;        // lower bound on the learned Smagorinsky constant
   bool mlp_set = false;
   int64_t nsamples = 0;
   double force[3] = {0.0, 0.0, 0.0};
@@ -115,6 +116,7 @@ static KParams kparams(const lbm_s* h) {
   }
   p.mlp_scale[0] = h->mlp_scale[0];
   p.mlp_scale[1] = h->mlp_scale[1];
+  p.cs2_min = (float)(h->cs_min * h->cs_min);
   return p;
 }
 
@@ -201,6 +203,24 @@ __global__ void k_classify(const __grid_constant__ KParams p, uint8_t* cls, int 
   }
   cls[cell] = (uint8_t)c;
 }
+
+// ---- accessors used by the other translation units (closure training) -------------------------
+KParams lbm_internal_kparams(lbm_handle h) { return kparams(h); }
+
+int lbm_internal_info(lbm_handle h, int* q, int* precision, int* parity, int* closure, int* nx, int* ny,
+                      int* nz, void** stream) {
+  *q = h->q;
+  *precision = h->prm.precision;
+  *parity = h->parity;
+  *closure = h->prm.closure;
+  *nx = h->nx;
+  *ny = h->ny;
+  *nz = h->nz;
+  *stream = (void*)h->stream;
+  return 0;
+}
+
+lbm_status lbm_internal_fail(lbm_handle h, lbm_status s, const char* msg) { return fail(h, s, "%s", msg); }
 
 // ---- C ABI ----------------------------------------------------------------------------------
 
@@ -585,6 +605,35 @@ lbm_status lbm_set_closure(lbm_handle h, const uint16_t* bf16_params, int n, dou
   h->mlp_scale[0] = (float)scale_pi;
   h->mlp_scale[1] = (float)scale_rho;
   h->mlp_set = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_closure_f32(lbm_handle h, const float* params, int on_device, double scale_pi,
+                               double scale_rho) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (!params) return fail(h, LBM_EINVAL, "params is NULL");
+  float host[LBM_MLP_NPARAM];
+  if (on_device) {
+    CUDA_TRY(h, cudaMemcpyAsync(host, params, sizeof host, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  } else {
+    std::memcpy(host, params, sizeof host);
+  }
+  uint16_t bf[LBM_MLP_NPARAM];
+  for (int k = 0; k < LBM_MLP_NPARAM; k++) {
+    if (!std::isfinite(host[k])) return fail(h, LBM_EINVAL, "non-finite MLP parameter %d", k);
+    uint32_t bits;
+    std::memcpy(&bits, &host[k], sizeof bits);
+    bits += 0x7FFFu + ((bits >> 16) & 1u);  // round to nearest even on the upper 16 bits
+    bf[k] = (uint16_t)(bits >> 16);
+  }
+  return lbm_set_closure(h, bf, LBM_MLP_NPARAM, scale_pi, scale_rho);
+}
+
+lbm_status lbm_set_closure_floor(lbm_handle h, double cs_min) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (!(cs_min >= 0.0) || !std::isfinite(cs_min)) return fail(h, LBM_EINVAL, "cs_min must be >= 0");
+  h->cs_min = cs_min;
   return LBM_OK;
 }
 

@@ -55,6 +55,9 @@ enum : int { K_STREAM = 0, K_BB = 1, K_INFLOW = 2, K_OUTCOPY = 3 };
 
 constexpr int MLP_NIN = 7, MLP_NH = 32;
 constexpr int MLP_NPARAM = MLP_NH * MLP_NIN + MLP_NH + MLP_NH * MLP_NH + MLP_NH + MLP_NH + 1;
+// scaled features are clipped to [-8, 8] (training data are standardised, so this only keeps
+// rare outliers, e.g. acoustic density transients, from extrapolating the network)
+constexpr float MLP_XCLAMP = 8.f;
 
 struct KParams {
   void* f;               // population array, q planes of `plane` elements
@@ -74,6 +77,7 @@ struct KParams {
   float F3w[27];          // 3 w_i (c_i . F): antisymmetric Guo term
   float F9w[27];          // 9 w_i (c_i . F): symmetric Guo term, times c_i . u
   float mlp_scale[2];
+  float cs2_min;          // lower bound on the learned C_s^2 (0: none)
 };
 
 __device__ __forceinline__ int cidx(const KParams& p, int x, int y, int z) {
@@ -273,8 +277,8 @@ __device__ __forceinline__ float mlp_cs2(const KParams& p, const float (&pi)[6],
   const float* b3 = W3 + MLP_NH;
   float xin[MLP_NIN];
 #pragma unroll
-  for (int k = 0; k < 6; k++) xin[k] = p.mlp_scale[0] * pi[k];
-  xin[6] = p.mlp_scale[1] * drho;
+  for (int k = 0; k < 6; k++) xin[k] = fminf(fmaxf(p.mlp_scale[0] * pi[k], -MLP_XCLAMP), MLP_XCLAMP);
+  xin[6] = fminf(fmaxf(p.mlp_scale[1] * drho, -MLP_XCLAMP), MLP_XCLAMP);
   float h1[MLP_NH];
 #pragma unroll
   for (int j = 0; j < MLP_NH; j++) {
@@ -425,7 +429,7 @@ __device__ __forceinline__ float collide(const KParams& p, float (&f)[Q]) {
     const float qn = pi[0] * pi[0] + pi[1] * pi[1] + pi[2] * pi[2] +
                      2.f * (pi[3] * pi[3] + pi[4] * pi[4] + pi[5] * pi[5]);
     float cs2 = p.cs2;
-    if (CL == CL_MLP) cs2 = mlp_cs2(p, pi, drho);
+    if (CL == CL_MLP) cs2 = fmaxf(mlp_cs2(p, pi, drho), p.cs2_min);
     const float tau = 0.5f * (p.tau0 + fast_sqrt(p.tau0 * p.tau0 + 25.455844122715711f * cs2 * fast_sqrt(qn) * inv));
     wp = __fdividef(1.f, tau);
     wm = __fdividef(1.f, __fdividef(p.lambda, tau - 0.5f) + 0.5f);

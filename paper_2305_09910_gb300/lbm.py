@@ -92,6 +92,15 @@ def load():
             "lbm_info": (I, [H, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]),
             "lbm_last_error": (ctypes.c_char_p, [H]),
             "lbm_reduce_noalloc": (I, [P, P, I, I, I, I, P, P, P]),
+            "lbm_set_closure_f32": (I, [H, P, I, D, D]),
+            "lbm_set_closure_floor": (I, [H, D]),
+            "lbm_closure_samples": (I, [H, D, D, P, P, P, P, P]),
+            "lbm_mlp_forward": (I, [P, P, ctypes.c_int64, P, P]),
+            "lbm_filter2": (I, [H, P, P]),
+            "lbm_mlp_backward": (I, [P, P, P, ctypes.c_int64, P, P]),
+            "lbm_closure_loss_grad": (I, [P, P, P, P, P, ctypes.c_int64, ctypes.c_int64,
+                                          ctypes.c_int64, D, P, P, P]),
+            "lbm_adam_step": (I, [P, P, P, P, I, D, D, D, D, ctypes.c_int64, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -275,6 +284,58 @@ def lbm_reduce_noalloc(df, flags, nx, ny, nz, stencil, force=(0.0, 0.0, 0.0), st
                                      fv.ctypes.data_as(ctypes.c_void_p),
                                      out.ctypes.data_as(ctypes.c_void_p), st), None)
     return out
+
+
+def _dev(a, dtype=np.float32):
+    p, dev = _buf(a, dtype)
+    if not dev:
+        raise ValueError("expected a CUDA tensor")
+    return p
+
+
+def lbm_set_closure_f32(h, params, scale_pi: float, scale_rho: float):
+    p, dev = _buf(params, np.float32)
+    _check(load().lbm_set_closure_f32(h, p, dev, float(scale_pi), float(scale_rho)), h)
+
+
+def lbm_set_closure_floor(h, cs_min: float):
+    _check(load().lbm_set_closure_floor(h, float(cs_min)), h)
+
+
+def lbm_closure_samples(h, tau0_c, cs0, scale, x, target, smag, weight):
+    sc = np.ascontiguousarray(scale, dtype=np.float64)
+    _check(load().lbm_closure_samples(h, float(tau0_c), float(cs0), sc.ctypes.data_as(ctypes.c_void_p),
+                                      _dev(x), _dev(target), _dev(smag), _dev(weight)), h)
+
+
+def lbm_filter2(h, rho_bar, u_bar):
+    _check(load().lbm_filter2(h, _dev(rho_bar), _dev(u_bar)), h)
+
+
+def lbm_mlp_forward(params, x, n, y, stream=None):
+    st = stream if stream is not None else _current_stream()
+    _check(load().lbm_mlp_forward(_dev(params), _dev(x), int(n), _dev(y), st), None)
+
+
+def lbm_mlp_backward(params, x, dy, n, grad, stream=None):
+    st = stream if stream is not None else _current_stream()
+    _check(load().lbm_mlp_backward(_dev(params), _dev(x), _dev(dy), int(n), _dev(grad), st), None)
+
+
+def lbm_closure_loss_grad(params, x, target, smag, weight, n, offset, stride, cs0, grad, stream=None):
+    st = stream if stream is not None else _current_stream()
+    loss = ctypes.c_double(0.0)
+    _check(load().lbm_closure_loss_grad(_dev(params), _dev(x), _dev(target), _dev(smag), _dev(weight),
+                                        int(n), int(offset), int(stride), float(cs0), _dev(grad),
+                                        ctypes.byref(loss), st), None)
+    return loss.value
+
+
+def lbm_adam_step(params, grad, m, v, lr, t, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    st = stream if stream is not None else _current_stream()
+    n = params.numel() if hasattr(params, "numel") else params.size
+    _check(load().lbm_adam_step(_dev(params), _dev(grad), _dev(m), _dev(v), int(n), float(lr),
+                                float(beta1), float(beta2), float(eps), int(t), st), None)
 
 
 def lbm_last_error(h=None) -> str:

@@ -1,0 +1,185 @@
+"""Parity of the learned-closure kernels with the FP64 oracle.
+
+* training samples (box filter of width 2) from identical fine states, at both AA parities;
+* network forward, backward (gradients for given dy), the eddy-viscosity loss gradient and
+  the Adam step;
+* the closure fused into the collide kernel: single steps with BF16 weights match the
+  oracle (which gets the same BF16 values in FP64) within 1e-6 per population, and a zero
+  output layer reproduces Smagorinsky.
+"""
+import numpy as np
+import pytest
+
+from tests.cases import FACES_CHANNEL, developed_state, make_pair, max_abs_pop_error
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    import torch
+
+    from paper_2305_09910_gb300 import build
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+
+
+def _bf16_round(a):
+    import torch
+
+    return torch.from_numpy(np.asarray(a, np.float32)).to(torch.bfloat16).to(torch.float32).numpy()
+
+
+def _params(seed, scale=0.3):
+    rng = np.random.default_rng(seed)
+    p = rng.normal(0, scale, 1345).astype(np.float32)
+    p[-1] = 0.2
+    return p
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_closure_samples_match_oracle(q):
+    import torch
+
+    from paper_2305_09910_gb300 import inputs, lbm
+
+    nx, ny, nz = 34, 18, 10
+    lat, ora = make_pair(nx, ny, nz, q=q, tau=0.54, closure="smag", cs=0.1, faces=FACES_CHANNEL,
+                         force=(2e-5, 0, 0))
+    rho, u = inputs.channel_init(nx, ny, nz, u_bulk=0.05, seed=8)
+    df = developed_state(ora, rho, u, 8, noise_seed=8, noise=0.05)
+    ora.set_shifted(df)
+    lat.set_populations(df)
+    nc = (nx // 2) * (ny // 2) * (nz // 2)
+    scale = (300.0, 50.0)
+    for steps in (0, 1):  # natural and swapped AA layouts
+        lat.step(steps)
+        ora.step(steps)
+        out = [torch.zeros((nc, 7), device="cuda")] + [torch.zeros(nc, device="cuda") for _ in range(3)]
+        lbm.lbm_closure_samples(lat.h, 0.52, 0.1, scale, *out)
+        torch.cuda.synchronize()
+        x, t, sm, w = (o.cpu().numpy().astype(np.float64) for o in out)
+        xr, tr, smr, wr = ora.closure_samples(0.52, 0.1, scale)
+        assert np.abs(x - xr).max() <= 1e-5 * np.abs(xr).max()
+        assert np.abs(sm - smr).max() <= 1e-5 * smr.max()
+        assert np.abs(w - wr).max() <= 1e-4 * wr.max()
+        assert tr.max() > 0
+        assert np.abs(t - tr).max() <= 1e-3 * tr.max()
+
+
+def test_mlp_forward_backward_match_oracle():
+    import torch
+
+    import oracle
+    from paper_2305_09910_gb300 import lbm
+
+    rng = np.random.default_rng(41)
+    p = _params(41)
+    n = 300
+    x = rng.normal(0, 1, (n, 7)).astype(np.float32)
+    dy = rng.normal(0, 1, n).astype(np.float32)
+    pd, xd, dyd = (torch.from_numpy(a).cuda() for a in (p, x, dy))
+    y = torch.zeros(n, device="cuda")
+    lbm.lbm_mlp_forward(pd, xd, n, y)
+    g = torch.zeros(1345, device="cuda")
+    lbm.lbm_mlp_backward(pd, xd, dyd, n, g)
+    torch.cuda.synchronize()
+    yr = np.array([oracle.mlp_forward(p.astype(np.float64), x[s].astype(np.float64)) for s in range(n)])
+    assert np.abs(y.cpu().numpy() - yr).max() <= 1e-5 * max(1.0, np.abs(yr).max())
+    gr = sum(oracle.mlp_backward(p.astype(np.float64), x[s].astype(np.float64), float(dy[s])) for s in range(n))
+    gg = g.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(gg - gr) <= 1e-5 * np.linalg.norm(gr)
+
+
+def test_closure_loss_gradient_and_adam_match_oracle():
+    import torch
+
+    import oracle
+    from paper_2305_09910_gb300 import lbm
+
+    rng = np.random.default_rng(42)
+    p = _params(42)
+    n_all = 1000
+    x = rng.normal(0, 1, (n_all, 7)).astype(np.float32)
+    t = np.abs(rng.normal(0, 2e-5, n_all)).astype(np.float32)
+    sm = (np.abs(rng.normal(0, 3e-3, n_all)) + 1e-4).astype(np.float32)
+    w = (sm * sm).astype(np.float32)
+    dev = [torch.from_numpy(a).cuda() for a in (p, x, t, sm, w)]
+    g = torch.zeros(1345, device="cuda")
+    off, stride, n = 3, 4, 240
+    loss = lbm.lbm_closure_loss_grad(*dev, n, off, stride, 0.1, g)
+    idx = off + stride * np.arange(n)
+    lr, gr = oracle.closure_loss(p.astype(np.float64), x[idx], t[idx], sm[idx], w[idx], 0.1)
+    assert abs(loss - lr) <= 1e-5 * lr
+    gg = g.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(gg - gr) <= 1e-5 * np.linalg.norm(gr)
+    # Adam on the GPU vs the FP64 oracle, three steps with this gradient
+    pm = torch.from_numpy(p.copy()).cuda()
+    m = torch.zeros(1345, device="cuda")
+    v = torch.zeros(1345, device="cuda")
+    po, mo, vo = p.astype(np.float64), np.zeros(1345), np.zeros(1345)
+    for step in (1, 2, 3):
+        lbm.lbm_adam_step(pm, g, m, v, 1e-3, step)
+        oracle.adam(po, gg, mo, vo, 1e-3, step)
+    torch.cuda.synchronize()
+    assert np.abs(pm.cpu().numpy() - po).max() <= 1e-6
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_fused_mlp_closure_single_steps_match_oracle(q):
+    from paper_2305_09910_gb300 import inputs, lbm
+
+    p = _bf16_round(_params(43, 0.4))
+    scale = (400.0, 30.0)
+    nx, ny, nz = 37, 14, 9
+    lat, ora = make_pair(nx, ny, nz, q=q, tau=0.52, closure="mlp", cs=0.1, faces=FACES_CHANNEL,
+                         force=(1e-5, 0, 0), mlp=p.astype(np.float64), mlp_scale=scale)
+    lbm.lbm_set_closure_f32(lat.h, p, *scale)
+    rho, u = inputs.channel_init(nx, ny, nz, u_bulk=0.05, seed=9)
+    df = developed_state(ora, rho, u, 4, noise_seed=9, noise=0.05)
+    ora.set_shifted(df)
+    lat.set_populations(df)
+    for steps in (1, 2):
+        lat.step(steps)
+        ora.step(steps)
+        lat.sync()
+        assert max_abs_pop_error(lat, ora) <= 1e-6
+
+
+def test_zero_output_layer_is_smagorinsky_on_gpu():
+    from paper_2305_09910_gb300 import inputs, lbm
+
+    p = _bf16_round(_params(44))
+    p[224 + 32 + 1024 + 32:] = 0.0
+    nx, ny, nz = 40, 12, 8
+    a = lbm.Lattice(nx, ny, nz, tau=0.52, closure="mlp", cs_smag=0.1, faces=FACES_CHANNEL)
+    b = lbm.Lattice(nx, ny, nz, tau=0.52, closure="smag", cs_smag=0.1, faces=FACES_CHANNEL)
+    lbm.lbm_set_closure_f32(a.h, p, 100.0, 10.0)
+    rho, u = inputs.channel_init(nx, ny, nz, u_bulk=0.05, seed=10)
+    for lat in (a, b):
+        lat.init_equilibrium(rho, u)
+        lat.step(20)
+    assert np.abs(a.get_populations() - b.get_populations()).max() <= 1e-7
+
+
+def test_filter2_matches_oracle():
+    import torch
+
+    from paper_2305_09910_gb300 import inputs, lbm
+
+    nx, ny, nz = 34, 18, 10
+    lat, ora = make_pair(nx, ny, nz, q=19, tau=0.6, closure="smag", faces=FACES_CHANNEL, force=(1e-5, 0, 0))
+    rho, u = inputs.channel_init(nx, ny, nz, u_bulk=0.05, seed=12)
+    df = developed_state(ora, rho, u, 3, noise_seed=12, noise=0.05)
+    ora.set_shifted(df)
+    lat.set_populations(df)
+    for steps in (0, 1):
+        lat.step(steps)
+        ora.step(steps)
+        rb = torch.zeros((nz // 2, ny // 2, nx // 2), device="cuda")
+        ub = torch.zeros((3, nz // 2, ny // 2, nx // 2), device="cuda")
+        lbm.lbm_filter2(lat.h, rb, ub)
+        rr, ur = ora.filter2()
+        assert np.abs(rb.cpu().numpy() - rr).max() <= 1e-6
+        assert np.abs(ub.cpu().numpy() - ur).max() <= 1e-6
