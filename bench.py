@@ -218,6 +218,63 @@ def _roofline(ncell, bytes_per_update, per_launch_ms, peak, peak_kind, traffic):
             "bytes_per_update": bytes_per_update, "avg_launch_ms": round(avg_s * 1e3, 4)}
 
 
+def _form_line(lat, nsteps, warmup, peak, peak_kind):
+    ms, per = _time_steps(lat, nsteps, warmup, None)
+    return {"MLUPS": round(lat.ncell * nsteps / (ms * 1e-3) / 1e6, 1), "cells": lat.ncell,
+            "roofline": _roofline(lat.ncell, lat.bytes_per_update, per, peak, peak_kind, None)}
+
+
+def _extra_forms(nsteps, warmup, peak, peak_kind):
+    """The other benchmark shapes, timed the same way (state values do not change the cost
+    of a step; these start from rest or from uniform flow):
+      * precision form: channel 1024x512x512 (268M cells), FP32 and FP16-shifted storage;
+      * bluff body: 768x384x384 D3Q27 TRT+Smagorinsky tunnel (inflow 0.05, outflow, free-slip)
+        with the landing-gear flags, FP32 and FP16-shifted storage;
+      * learned closure: channel 256x128x128, fused MLP closure vs Smagorinsky (network
+        weights from a fixed seed: the cost of the fused inference does not depend on them)."""
+    import numpy as np
+    import torch
+
+    from paper_2305_09910_gb300 import closure, inputs, lbm
+
+    out = {}
+    par = inputs.channel_parameters(512)
+    for prec in ("f32", "f16"):
+        lat = lbm.Lattice(1024, 512, 512, stencil=19, tau=par["tau"], precision=prec, closure="smag",
+                          cs_smag=0.1, faces=FACES_CHANNEL)
+        lat.set_force(par["force"])
+        lat.init_equilibrium()
+        out[f"channel1024_{prec}"] = _form_line(lat, max(20, nsteps // 4), warmup, peak, peak_kind)
+        lat.close()
+        torch.cuda.empty_cache()
+    flags = torch.from_numpy(inputs.landing_gear_flags(768, 384, 384)).cuda()
+    tau = 0.5 + 3 * 0.05 * 80 / 1e4
+    for prec in ("f32", "f16"):
+        lat = lbm.Lattice(768, 384, 384, stencil=27, tau=tau, precision=prec, closure="smag", cs_smag=0.1,
+                          faces=("inflow", "outflow", "freeslip", "freeslip", "freeslip", "freeslip"),
+                          u_inflow=(0.05, 0.0, 0.0))
+        lat.set_flags(flags)
+        u = torch.zeros((3, 384, 384, 768), dtype=torch.float32, device="cuda")
+        u[0] = 0.05
+        lat.init_equilibrium(None, u)
+        del u
+        out[f"bluffbody768_q27_{prec}"] = _form_line(lat, max(20, nsteps // 4), warmup, peak, peak_kind)
+        lat.close()
+        torch.cuda.empty_cache()
+    params = closure.init_params(7)
+    params[closure.OUT_LAYER] = np.random.default_rng(7).normal(0, 0.1, 33).astype(np.float32)
+    for name in ("smag", "mlp"):
+        lat = closure.channel(256, 128, 128, closure=name)
+        if name == "mlp":
+            lbm.lbm_set_closure_f32(lat.h, params, 600.0, 3000.0)
+            lbm.lbm_set_closure_floor(lat.h, 0.1)
+        line = _form_line(lat, nsteps, warmup, peak, peak_kind)
+        line["roofline"]["bound"] = "hbm" if name == "smag" else "alu (fused 7-32-32-1 network per cell)"
+        out[f"channel256_{name}"] = line
+        lat.close()
+    return out
+
+
 def _cpu_baseline(target_s=12.0):
     """The FP64 oracle on this host's cores, on a 128x64x64 sub-lattice of the channel."""
     import numpy as np
@@ -361,14 +418,12 @@ def main():
 
     forms = {}
     if not args.no_forms:
+        nsteps = max(50, args.steps // 4)
         for prec in ("f16", "bf16"):
             fl, _ = _channel_lattice(nx, ny, nz, prec)
-            ms, per_f = _time_steps(fl, max(50, args.steps // 4), args.warmup, None)
-            n = max(50, args.steps // 4)
-            forms[f"{prec}_shifted"] = {
-                "MLUPS": round(ncell * n / (ms * 1e-3) / 1e6, 1),
-                "roofline": _roofline(ncell, fl.bytes_per_update, per_f, peak, peak_kind, None)}
+            forms[f"channel512_{prec}_shifted"] = _form_line(fl, nsteps, args.warmup, peak, peak_kind)
             fl.close()
+        forms.update(_extra_forms(nsteps, args.warmup, peak, peak_kind))
 
     workload = WORKLOAD if (nx, ny, nz, args.form) == (512, 256, 256, "f32") else \
         f"turbulent channel {nx}x{ny}x{nz} D3Q19 TRT+Smagorinsky {args.form} (AA in place)"

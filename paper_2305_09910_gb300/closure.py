@@ -25,7 +25,7 @@ OUT_LAYER = slice(32 * 7 + 32 + 32 * 32 + 32, NP)
 
 
 def channel(nx, ny, nz, closure="smag", cs0=0.1, precision="f32", re_tau=180.0, u_bulk=0.05,
-            seed=inputs.DEFAULT_SEED, tau=None, force=None):
+            seed=inputs.DEFAULT_SEED, tau=None, force=None, amp=0.1):
     """A channel lattice (walls at the y faces) initialised from the perturbed parabola."""
     import torch
 
@@ -35,8 +35,15 @@ def channel(nx, ny, nz, closure="smag", cs0=0.1, precision="f32", re_tau=180.0, 
     lat = lbm.Lattice(nx, ny, nz, stencil=19, tau=tau, precision=precision, closure=closure,
                       cs_smag=cs0, faces=FACES_CHANNEL)
     lat.set_force(force)
-    rho, u = inputs.channel_init(nx, ny, nz, u_bulk=u_bulk, seed=seed)
-    lat.init_equilibrium(torch.from_numpy(rho).cuda(), torch.from_numpy(u).cuda())
+    rho = torch.empty((nz, ny, nx), dtype=torch.float32, device="cuda")
+    u = torch.empty((3, nz, ny, nx), dtype=torch.float32, device="cuda")
+    step = max(1, nz // 8)
+    for z0 in range(0, nz, step):  # slab by slab to bound host memory
+        z1 = min(nz, z0 + step)
+        r, v = inputs.channel_init(nx, ny, nz, u_bulk=u_bulk, seed=seed, z_range=(z0, z1), amp=amp)
+        rho[z0:z1].copy_(torch.from_numpy(r))
+        u[:, z0:z1].copy_(torch.from_numpy(v))
+    lat.init_equilibrium(rho, u)
     lat.tau, lat.force = tau, force
     return lat
 
@@ -212,7 +219,7 @@ def split(samples, frac):
 
 
 def experiment(nx, ny, nz, re_tau=180.0, u_bulk=0.05, spin=60000, nsnap=20, every=500, epochs=6,
-               coarse_steps=20000, cs0=0.1, cs_min=0.1, seed=0, log=None):
+               coarse_steps=20000, cs0=0.1, cs_min=0.1, seed=0, log=None, amp=0.1):
     """The learned-closure experiment on a fine channel of nx x ny x nz cells.
 
     1. spin the fine Smagorinsky channel up; 2. collect nsnap box-filtered sample sets;
@@ -226,9 +233,14 @@ def experiment(nx, ny, nz, re_tau=180.0, u_bulk=0.05, spin=60000, nsnap=20, ever
     rep = {"fine": [nx, ny, nz], "coarse": [nx // 2, ny // 2, nz // 2], "re_tau": re_tau,
            "u_bulk": u_bulk, "spin_steps": spin, "snapshots": nsnap, "every": every,
            "epochs": epochs, "coarse_steps": coarse_steps, "cs0": cs0, "cs_min": cs_min}
-    fine = channel(nx, ny, nz, closure="smag", cs0=cs0, re_tau=re_tau, u_bulk=u_bulk)
+    fine = channel(nx, ny, nz, closure="smag", cs0=cs0, re_tau=re_tau, u_bulk=u_bulk, amp=amp)
     fine.step(spin)
     fine.sync()
+    lbm.lbm_stats_reset(fine.h)
+    lbm.lbm_stats_sample(fine.h)
+    st, _ = lbm.lbm_stats_get(fine.h, ny)
+    rep["fine_rms_max_after_spin"] = profiles(st, 1)[1].max(axis=0).tolist()
+    rep["amp"] = amp
     tau_c = 1.5 * (fine.tau - 0.5) / 3.0 + 0.5
     rep["tau_fine"], rep["tau_coarse"] = fine.tau, tau_c
     scale = feature_scales(fine, tau_c, cs0)
@@ -264,11 +276,12 @@ if __name__ == "__main__":
     ap.add_argument("--epochs", type=int, default=6)
     ap.add_argument("--coarse-steps", type=int, default=20000)
     ap.add_argument("--cs-min", type=float, default=0.1)
+    ap.add_argument("--amp", type=float, default=0.1, help="sinusoid amplitude / u_bulk")
     ap.add_argument("--out", default=None, help="JSON report path")
     a = ap.parse_args()
     nx, ny, nz = (int(v) for v in a.size.split("x"))
     rep = experiment(nx, ny, nz, a.re_tau, a.u_bulk, a.spin, a.snapshots, a.every, a.epochs,
-                     a.coarse_steps, cs_min=a.cs_min, log=lambda s: print(s, flush=True))
+                     a.coarse_steps, cs_min=a.cs_min, log=lambda s: print(s, flush=True), amp=a.amp)
     short = {k: v for k, v in rep.items() if k != "params"}
     print(json.dumps(short))
     if a.out:

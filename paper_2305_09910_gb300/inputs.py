@@ -71,13 +71,14 @@ def channel_parameters(ny: int, re_tau: float = 180.0, u_bulk: float = 0.05):
 
 
 def channel_init(nx: int, ny: int, nz: int, u_bulk: float = 0.05, seed: int = DEFAULT_SEED,
-                 z_range=None, dtype=np.float32):
+                 z_range=None, dtype=np.float32, amp: float = 0.1):
     """(rho, u) of the perturbed laminar channel, shapes (nz', ny, nx) and (3, nz', ny, nx).
 
     Walls are at the -y and +y faces (y = -1/2 and y = ny - 1/2).  u_x is the parabola of
-    bulk velocity u_bulk; u_y and u_z carry a sinusoid of amplitude 0.1 u_bulk with seeded
-    phases (4 periods in x, 2 in z, vanishing at the walls); every component gets uniform
-    noise in [-0.05, 0.05] u_bulk.  z_range = (z0, z1) generates a slab of the full field."""
+    bulk velocity u_bulk; u_y and u_z carry a sinusoid of amplitude amp * u_bulk (0.1 by
+    default) with seeded phases (4 periods in x, 2 in z, vanishing at the walls); every
+    component gets uniform noise in [-0.05, 0.05] u_bulk.  z_range = (z0, z1) generates a
+    slab of the full field."""
     z0, z1 = (0, nz) if z_range is None else z_range
     ph = 2 * math.pi * uniform01(seed, 1, np.arange(4, dtype=np.uint64))
     x = np.arange(nx, dtype=np.float64)[None, None, :]
@@ -86,7 +87,7 @@ def channel_init(nx: int, ny: int, nz: int, u_bulk: float = 0.05, seed: int = DE
     shape = (z1 - z0, ny, nx)
     u = np.zeros((3,) + shape, dtype=np.float64)
     u[0] = 6.0 * u_bulk * yc * (1.0 - yc)
-    amp = 0.1 * u_bulk
+    amp = amp * u_bulk
     env = np.sin(math.pi * yc)
     u[1] = amp * np.sin(2 * math.pi * 4 * x / nx + ph[0]) * env * np.cos(2 * math.pi * 2 * z / nz + ph[1])
     u[2] = amp * np.cos(2 * math.pi * 4 * x / nx + ph[2]) * env * np.sin(2 * math.pi * 2 * z / nz + ph[3])
