@@ -176,8 +176,10 @@ def _channel_lattice(nx, ny, nz, precision, closure="smag"):
     return lat, par
 
 
-def _time_steps(lat, steps, warmup, dist):
-    """Device time of `steps` single-launch steps (CUDA events on the handle's stream)."""
+def _time_steps(lat, steps, warmup, dist, stats_every=0):
+    """Device time of `steps` single-launch steps (CUDA events on the handle's stream); with
+    stats_every > 0 the FP64 profile statistics are sampled every that many steps inside the
+    timed region (the turbulent-channel job accumulates mean and RMS profiles)."""
     import torch
 
     from paper_2305_09910_gb300 import lbm
@@ -193,11 +195,15 @@ def _time_steps(lat, steps, warmup, dist):
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
+    if stats_every:
+        lbm.lbm_stats_reset(lat.h)
     t0.record(stream)
     for k in range(steps):
         starts[k].record(stream)
         lbm.lbm_step(lat.h, 1)
         ends[k].record(stream)
+        if stats_every and (k + 1) % stats_every == 0:
+            lbm.lbm_stats_sample(lat.h)
     t1.record(stream)
     torch.cuda.synchronize()
     if dist is not None:
@@ -378,7 +384,7 @@ def main():
         lbm.lbm_step(lat.h, 1)
     torch.cuda.synchronize()
     clocks.start()
-    total_ms, per = _time_steps(lat, args.steps, 3, dist)
+    total_ms, per = _time_steps(lat, args.steps, 3, dist, stats_every=10)
     clocks.stop()
     total_ms = _barrier_max(dist, total_ms)
     value = world * ncell * args.steps / (total_ms * 1e-3) / 1e6
@@ -434,8 +440,9 @@ def main():
            "config": {"workload": workload, "storage": args.form, "nx": nx, "ny": ny, "nz": nz, "stencil": 19,
                       "tau": round(par["tau"], 6), "force": par["force"], "cs_smag": 0.1,
                       "global_batch": world * ncell, "parallelism": f"replicas x{world}",
+                      "stats": "FP64 mean/RMS profile sample every 10 steps, inside the timed region",
                       "l2": f"inputs larger than L2 ({lat_bytes / 1e9:.2f} GB population array vs 129 MB L2)"},
-           "roofline": roof, "e2e": e2e, "gpu_launches": args.steps,
+           "roofline": roof, "e2e": e2e, "gpu_launches": args.steps + args.steps // 10,
            "clocks": clocks.summary(), "mass_after": mass, "forms": forms}
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = _cpu_baseline()

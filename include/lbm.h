@@ -80,7 +80,8 @@ typedef enum {
 
 /* storage precision of the populations (arithmetic is float32 in every case) */
 enum { LBM_F32 = 0, LBM_F16_SHIFTED = 1, LBM_BF16_SHIFTED = 2 };
-/* streaming pattern: AA in place (one population array) or two-grid pull */
+/* streaming pattern: AA in place (one population array) or two-grid pull (two arrays; each
+ * step gathers the neighbours' post-collision values from one and writes the other) */
 enum { LBM_AA = 0, LBM_PULL = 1 };
 /* relaxation-time closure */
 enum { LBM_CLOSURE_NONE = 0, LBM_CLOSURE_SMAG = 1, LBM_CLOSURE_MLP = 2 };
@@ -115,7 +116,16 @@ typedef struct {
   double u_inflow[3];   /* velocity of INFLOW faces and cells, default 0 */
   double rho_inflow;    /* density used by moving-wall bounce-back, default 1 */
   void* stream;         /* cudaStream_t for all work, default NULL */
+  int32_t pipeline;     /* load pipeline of the AA step kernels (LBM_PIPE_*), default DIRECT */
 } lbm_params;
+
+/* load pipeline of the AA step kernels (two-grid pull always loads directly):
+ * DIRECT (default) = every thread loads its cell from global memory;
+ * TMA = loads staged in shared memory by 1-D bulk copies in a 3-stage mbarrier pipeline of
+ *   persistent CTAs; PREFETCH = direct loads double-buffered in registers along z.
+ * All three compute bit-identical updates; on GB300 DIRECT is the fastest (the step is
+ * issue-bound, not latency-bound), so the others are kept as measured alternatives. */
+enum { LBM_PIPE_TMA = 0, LBM_PIPE_DIRECT = 1, LBM_PIPE_PREFETCH = 2 };
 
 /* Fills p with the defaults listed above. */
 void lbm_params_default(lbm_params* p);
@@ -153,7 +163,8 @@ lbm_status lbm_init_equilibrium(lbm_handle h, const float* rho, const float* u, 
 lbm_status lbm_step(lbm_handle h, int64_t n);
 
 /* Waits for the handle's stream.  LBM_EUNSTABLE if any step since the last state reset saw a
- * non-finite or non-positive density. */
+ * non-finite or non-positive density; LBM_ECUDA if a pipelined step gave up waiting for its
+ * staged loads (a bounded wait that should never expire). */
 lbm_status lbm_sync(lbm_handle h);
 
 /* Moments of the current state: rho (N floats) and u (3*N floats, includes +F/(2 rho)).

@@ -1,5 +1,7 @@
 // kern_inst.cu -- instantiates the kernels and launchers for one (stencil, precision) pair.
 // Compiled once per pair with -DLBM_Q=19|27 and -DLBM_S=float|__half|__nv_bfloat16.
+#include <algorithm>
+
 #include "lbm_launch.cuh"
 
 #ifndef LBM_Q
@@ -11,34 +13,91 @@
 
 namespace lbm {
 
+template <int Q, class S, int LOAD, int STORE>
+static void step_mode(const KParams& p, int closure, const Launch& L) {
+  if (closure == CL_NONE) k_step<Q, S, CL_NONE, LOAD, STORE><<<L.grid, L.block, 0, L.stream>>>(p);
+  else if (closure == CL_SMAG) k_step<Q, S, CL_SMAG, LOAD, STORE><<<L.grid, L.block, 0, L.stream>>>(p);
+  else k_step<Q, S, CL_MLP, LOAD, STORE><<<L.grid, L.block, 0, L.stream>>>(p);
+}
+
+// mode: 0 AA even, 1 AA odd, 2 first pull step after an import, 3 pull step
 template <int Q, class S>
-cudaError_t launch_step(const KParams& p, int closure, int parity, const Launch& L) {
-  if (parity == 0) {
-    if (closure == CL_NONE) k_step<Q, S, CL_NONE, 0><<<L.grid, L.block, 0, L.stream>>>(p);
-    else if (closure == CL_SMAG) k_step<Q, S, CL_SMAG, 0><<<L.grid, L.block, 0, L.stream>>>(p);
-    else k_step<Q, S, CL_MLP, 0><<<L.grid, L.block, 0, L.stream>>>(p);
-  } else {
-    if (closure == CL_NONE) k_step<Q, S, CL_NONE, 1><<<L.grid, L.block, 0, L.stream>>>(p);
-    else if (closure == CL_SMAG) k_step<Q, S, CL_SMAG, 1><<<L.grid, L.block, 0, L.stream>>>(p);
-    else k_step<Q, S, CL_MLP, 1><<<L.grid, L.block, 0, L.stream>>>(p);
+cudaError_t launch_step(const KParams& p, int closure, int mode, const Launch& L) {
+  switch (mode) {
+    case 0: step_mode<Q, S, 0, 0>(p, closure, L); break;
+    case 1: step_mode<Q, S, 1, 1>(p, closure, L); break;
+    case 2: step_mode<Q, S, 0, 2>(p, closure, L); break;
+    default: step_mode<Q, S, 2, 2>(p, closure, L); break;
   }
   return cudaGetLastError();
 }
 
+template <int Q, class S>
+cudaError_t launch_step_zp(const KParams& p, int closure, int parity, const Launch& L0) {
+  constexpr int ZC = 4;
+  Launch L = L0;
+  L.grid.z = (p.nz + ZC - 1) / ZC;
+  if (parity == 0) {
+    if (closure == CL_NONE) k_step_zp<Q, S, CL_NONE, 0, ZC><<<L.grid, L.block, 0, L.stream>>>(p);
+    else if (closure == CL_SMAG) k_step_zp<Q, S, CL_SMAG, 0, ZC><<<L.grid, L.block, 0, L.stream>>>(p);
+    else k_step_zp<Q, S, CL_MLP, 0, ZC><<<L.grid, L.block, 0, L.stream>>>(p);
+  } else {
+    if (closure == CL_NONE) k_step_zp<Q, S, CL_NONE, 1, ZC><<<L.grid, L.block, 0, L.stream>>>(p);
+    else if (closure == CL_SMAG) k_step_zp<Q, S, CL_SMAG, 1, ZC><<<L.grid, L.block, 0, L.stream>>>(p);
+    else k_step_zp<Q, S, CL_MLP, 1, ZC><<<L.grid, L.block, 0, L.stream>>>(p);
+  }
+  return cudaGetLastError();
+}
+
+template <int Q, class S, int CL, int PAR>
+static cudaError_t tma_one(const KParams& p, cudaStream_t stream, int nsm) {
+  constexpr int smem = TmaGeom<S>::template smem_bytes<Q, PAR>();
+  auto kern = k_step_tma<Q, S, CL, PAR>;
+  static int blocks_per_sm = 0;  // per instantiation, found once
+  if (blocks_per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, TMA_TX, smem);
+    if (e != cudaSuccess) return e;
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+  }
+  const int nseg = (p.nxp + TMA_TX - 1) / TMA_TX;
+  const long long ntiles = (long long)nseg * p.ny * p.nz;
+  const long long grid = std::min<long long>(ntiles, (long long)nsm * blocks_per_sm);
+  kern<<<(unsigned)grid, TMA_TX, smem, stream>>>(p, ntiles);
+  return cudaGetLastError();
+}
+
+template <int Q, class S>
+cudaError_t launch_step_tma(const KParams& p, int closure, int parity, cudaStream_t stream, int nsm) {
+  if (parity == 0) {
+    if (closure == CL_NONE) return tma_one<Q, S, CL_NONE, 0>(p, stream, nsm);
+    if (closure == CL_SMAG) return tma_one<Q, S, CL_SMAG, 0>(p, stream, nsm);
+    return tma_one<Q, S, CL_MLP, 0>(p, stream, nsm);
+  }
+  if (closure == CL_NONE) return tma_one<Q, S, CL_NONE, 1>(p, stream, nsm);
+  if (closure == CL_SMAG) return tma_one<Q, S, CL_SMAG, 1>(p, stream, nsm);
+  return tma_one<Q, S, CL_MLP, 1>(p, stream, nsm);
+}
+
 template <int Q, class S, int PAR>
 static void export_par(const KParams& p, int mode, const ExportArgs& a, const Launch& L) {
+  // plane sums: a grid of (ny, z chunks) blocks, about four per multiprocessor
+  const int zchunk = std::max(1, (int)((long long)p.nz * p.ny / 608 + 1));
+  const dim3 sgrid((unsigned)p.ny, (unsigned)((p.nz + zchunk - 1) / zchunk));
   switch (mode) {
     case EX_POP: k_export<Q, S, PAR, EX_POP><<<L.grid, L.block, 0, L.stream>>>(p, a); break;
     case EX_MOM: k_export<Q, S, PAR, EX_MOM><<<L.grid, L.block, 0, L.stream>>>(p, a); break;
-    case EX_SUM: k_export<Q, S, PAR, EX_SUM><<<L.grid, L.block, 0, L.stream>>>(p, a); break;
-    default: k_export<Q, S, PAR, EX_STATS><<<L.grid, L.block, 0, L.stream>>>(p, a); break;
+    case EX_SUM: k_plane_sums<Q, S, PAR, EX_SUM><<<sgrid, 128, 0, L.stream>>>(p, a.sums, zchunk); break;
+    default: k_plane_sums<Q, S, PAR, EX_STATS><<<sgrid, 128, 0, L.stream>>>(p, a.sums, zchunk); break;
   }
 }
 
 template <int Q, class S>
 cudaError_t launch_export(const KParams& p, int parity, int mode, const ExportArgs& a, const Launch& L) {
   if (parity == 0) export_par<Q, S, 0>(p, mode, a, L);
-  else export_par<Q, S, 1>(p, mode, a, L);
+  else if (parity == 1) export_par<Q, S, 1>(p, mode, a, L);
+  else export_par<Q, S, 2>(p, mode, a, L);
   return cudaGetLastError();
 }
 
@@ -55,6 +114,8 @@ cudaError_t launch_set_pop(const KParams& p, const float* df, const Launch& L) {
 }
 
 template cudaError_t launch_step<LBM_Q, LBM_S>(const KParams&, int, int, const Launch&);
+template cudaError_t launch_step_tma<LBM_Q, LBM_S>(const KParams&, int, int, cudaStream_t, int);
+template cudaError_t launch_step_zp<LBM_Q, LBM_S>(const KParams&, int, int, const Launch&);
 template cudaError_t launch_export<LBM_Q, LBM_S>(const KParams&, int, int, const ExportArgs&, const Launch&);
 template cudaError_t launch_init_eq<LBM_Q, LBM_S>(const KParams&, const float*, const float*, const Launch&);
 template cudaError_t launch_set_pop<LBM_Q, LBM_S>(const KParams&, const float*, const Launch&);

@@ -1,5 +1,6 @@
 // lbm_api.cu -- the C ABI declared in include/lbm.h: handle lifetime, validation, state
-// bookkeeping (AA parity), and dispatch to the (stencil, precision) kernel instances.
+// bookkeeping (AA parity, two-grid buffers), and dispatch to the (stencil, precision)
+// kernel instances.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -21,6 +22,8 @@ struct lbm_s {
   lbm_params prm{};
   cudaStream_t stream = nullptr;
   void* f = nullptr;          // populations, q * plane elements of the storage type
+  void* f2 = nullptr;         // second population array (two-grid pull only)
+  int cur = 0;                // pull: which array holds the state (0: f, 1: f2)
   uint8_t* flags = nullptr;   // raw flags, padded layout
   uint8_t* cls = nullptr;     // cell classes, padded layout
   int* status = nullptr;      // device status word
@@ -33,8 +36,11 @@ struct lbm_s {
   bool mlp_set = false;
   int64_t nsamples = 0;
   double force[3] = {0.0, 0.0, 0.0};
-  int parity = 0;             // 0: natural layout, 1: swapped (after an odd number of steps)
+  // layout of the state: 0 natural pre-collision (AA after an even number of steps, or any
+  // import), 1 AA swapped post-collision (odd number of steps), 2 pull post-collision
+  int parity = 0;
   int nat_valid = 1;          // natural layout came from an import (outflow slots hold values)
+  int nsm = 0;                // multiprocessors of the device (persistent grid size)
   std::string err;
 };
 
@@ -78,11 +84,15 @@ static Launch launch_cfg(const lbm_s* h) {
 static KParams kparams(const lbm_s* h) {
   KParams p;
   std::memset(&p, 0, sizeof p);
-  p.f = h->f;
   {
+    void* a = h->cur ? h->f2 : h->f;  // the state
+    void* b = h->cur ? h->f : h->f2;  // pull destination (null for AA)
+    p.f = a;
     const size_t sb = store_bytes(h->prm.precision);
-    for (int i = 0; i < 27; i++)
-      p.fp[i] = i < h->q ? (void*)((char*)h->f + (size_t)i * (size_t)plane_of(h) * sb) : nullptr;
+    for (int i = 0; i < 27; i++) {
+      p.fp[i] = i < h->q ? (void*)((char*)a + (size_t)i * (size_t)plane_of(h) * sb) : nullptr;
+      p.fq[i] = (i < h->q && b) ? (void*)((char*)b + (size_t)i * (size_t)plane_of(h) * sb) : nullptr;
+    }
   }
   p.nat_valid = h->nat_valid;
   p.flags = h->flags;
@@ -123,6 +133,28 @@ static KParams kparams(const lbm_s* h) {
 template <int Q>
 static cudaError_t dispatch_step(const lbm_s* h, const KParams& p, int closure, int parity) {
   const Launch L = launch_cfg(h);
+  if (h->prm.streaming == LBM_PULL) {  // direct loads only
+    const int mode = parity == 0 ? 2 : 3;
+    switch (h->prm.precision) {
+      case LBM_F32: return launch_step<Q, float>(p, closure, mode, L);
+      case LBM_F16_SHIFTED: return launch_step<Q, __half>(p, closure, mode, L);
+      default: return launch_step<Q, __nv_bfloat16>(p, closure, mode, L);
+    }
+  }
+  if (h->prm.pipeline == LBM_PIPE_PREFETCH) {
+    switch (h->prm.precision) {
+      case LBM_F32: return launch_step_zp<Q, float>(p, closure, parity, L);
+      case LBM_F16_SHIFTED: return launch_step_zp<Q, __half>(p, closure, parity, L);
+      default: return launch_step_zp<Q, __nv_bfloat16>(p, closure, parity, L);
+    }
+  }
+  if (h->prm.pipeline == LBM_PIPE_TMA) {
+    switch (h->prm.precision) {
+      case LBM_F32: return launch_step_tma<Q, float>(p, closure, parity, h->stream, h->nsm);
+      case LBM_F16_SHIFTED: return launch_step_tma<Q, __half>(p, closure, parity, h->stream, h->nsm);
+      default: return launch_step_tma<Q, __nv_bfloat16>(p, closure, parity, h->stream, h->nsm);
+    }
+  }
   switch (h->prm.precision) {
     case LBM_F32: return launch_step<Q, float>(p, closure, parity, L);
     case LBM_F16_SHIFTED: return launch_step<Q, __half>(p, closure, parity, L);
@@ -238,6 +270,7 @@ void lbm_params_default(lbm_params* p) {
   for (int k = 0; k < 6; k++) p->face_bc[k] = LBM_FACE_PERIODIC;
   p->rho_inflow = 1.0;
   p->stream = nullptr;
+  p->pipeline = LBM_PIPE_DIRECT;
 }
 
 int lbm_stencil(int q, int* c, double* w) {
@@ -270,6 +303,7 @@ static lbm_status launch_classify(lbm_handle h) {
 lbm_status lbm_destroy(lbm_handle h) {
   if (!h) return LBM_OK;
   if (h->f) cudaFreeAsync(h->f, h->stream);
+  if (h->f2) cudaFreeAsync(h->f2, h->stream);
   if (h->flags) cudaFreeAsync(h->flags, h->stream);
   if (h->cls) cudaFreeAsync(h->cls, h->stream);
   if (h->status) cudaFreeAsync(h->status, h->stream);
@@ -303,9 +337,10 @@ lbm_status lbm_create(int nx, int ny, int nz, int stencil, double tau, const lbm
     return fail(nullptr, LBM_EINVAL, "unknown precision %d", p.precision);
   if (p.closure < LBM_CLOSURE_NONE || p.closure > LBM_CLOSURE_MLP)
     return fail(nullptr, LBM_EINVAL, "unknown closure %d", p.closure);
-  if (p.streaming == LBM_PULL)
-    return fail(nullptr, LBM_EUNSUPPORTED, "two-grid pull streaming is not built in this library");
-  if (p.streaming != LBM_AA) return fail(nullptr, LBM_EINVAL, "unknown streaming %d", p.streaming);
+  if (p.streaming != LBM_AA && p.streaming != LBM_PULL)
+    return fail(nullptr, LBM_EINVAL, "unknown streaming %d", p.streaming);
+  if (p.pipeline != LBM_PIPE_TMA && p.pipeline != LBM_PIPE_DIRECT && p.pipeline != LBM_PIPE_PREFETCH)
+    return fail(nullptr, LBM_EINVAL, "unknown pipeline %d", p.pipeline);
   if (!(p.cs_smag >= 0.0)) return fail(nullptr, LBM_EINVAL, "cs_smag must be >= 0");
   for (int k = 0; k < 6; k++)
     if (p.face_bc[k] < LBM_FACE_PERIODIC || p.face_bc[k] > LBM_FACE_OUTFLOW)
@@ -333,10 +368,18 @@ lbm_status lbm_create(int nx, int ny, int nz, int stencil, double tau, const lbm
   h->tau = tau;
   h->prm = p;
   h->stream = (cudaStream_t)p.stream;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+      cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (h->nsm < 1) h->nsm = 1;
+  }
   const long long plane = plane_of(h);
   const size_t fbytes = (size_t)plane * stencil * store_bytes(p.precision);
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMallocAsync(&h->f, fbytes, h->stream);
+  if (e == cudaSuccess && p.streaming == LBM_PULL) e = cudaMallocAsync(&h->f2, fbytes, h->stream);
+  if (e == cudaSuccess && h->f2) e = cudaMemsetAsync(h->f2, 0, fbytes, h->stream);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->flags, (size_t)plane, h->stream);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->cls, (size_t)plane, h->stream);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->status, sizeof(int), h->stream);
@@ -473,8 +516,14 @@ lbm_status lbm_step(lbm_handle h, int64_t n) {
     cudaError_t e = h->q == 19 ? dispatch_step<19>(h, p, h->prm.closure, h->parity)
                                : dispatch_step<27>(h, p, h->prm.closure, h->parity);
     CUDA_TRY(h, e);
-    if (h->parity == 1) h->nat_valid = 0;  // an odd step leaves the outflow slots unwritten
-    h->parity ^= 1;
+    if (h->prm.streaming == LBM_PULL) {  // the destination array holds the new state
+      h->cur ^= 1;
+      h->parity = 2;
+      p = kparams(h);
+    } else {
+      if (h->parity == 1) h->nat_valid = 0;  // an odd step leaves the outflow slots unwritten
+      h->parity ^= 1;
+    }
   }
   return LBM_OK;
 }
@@ -483,6 +532,8 @@ lbm_status lbm_sync(lbm_handle h) {
   if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
   CUDA_TRY(h, cudaMemcpyAsync(h->status_host, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  if (*h->status_host & 2)
+    return fail(h, LBM_ECUDA, "a pipelined step timed out waiting for its staged loads");
   if (*h->status_host & 1)
     return fail(h, LBM_EUNSTABLE, "a step produced a non-finite or non-positive density");
   return LBM_OK;

@@ -369,7 +369,8 @@ template <int Q, class S>
 static void launch_samples(const KParams& p, int parity, const SampleArgs& a, long long nc, cudaStream_t st) {
   const unsigned blocks = (unsigned)((nc + 127) / 128);
   if (parity == 0) k_closure_samples<Q, S, 0><<<blocks, 128, 0, st>>>(p, a);
-  else k_closure_samples<Q, S, 1><<<blocks, 128, 0, st>>>(p, a);
+  else if (parity == 1) k_closure_samples<Q, S, 1><<<blocks, 128, 0, st>>>(p, a);
+  else k_closure_samples<Q, S, 2><<<blocks, 128, 0, st>>>(p, a);
 }
 
 template <int Q, class S>
@@ -378,7 +379,8 @@ static void launch_filter(const KParams& p, int parity, int ncx, int ncy, int nc
   const long long nc = (long long)ncx * ncy * ncz;
   const unsigned blocks = (unsigned)((nc + 127) / 128);
   if (parity == 0) k_filter2<Q, S, 0><<<blocks, 128, 0, st>>>(p, ncx, ncy, ncz, rb, ub);
-  else k_filter2<Q, S, 1><<<blocks, 128, 0, st>>>(p, ncx, ncy, ncz, rb, ub);
+  else if (parity == 1) k_filter2<Q, S, 1><<<blocks, 128, 0, st>>>(p, ncx, ncy, ncz, rb, ub);
+  else k_filter2<Q, S, 2><<<blocks, 128, 0, st>>>(p, ncx, ncy, ncz, rb, ub);
 }
 
 extern "C" {

@@ -13,6 +13,9 @@
 //     it read f_i from, which is where f_opp(i) of the receiving cell lives at t+1.
 //   Every slot is read and written by exactly one thread per launch, so both kernels are
 //   race-free in place (the boundary rules are involutions on (cell, direction) pairs).
+// Two-grid pull streaming keeps the post-collision f*_i(x) in slot (x, i) of one array and
+// writes the next step's into the other: its gather is the odd AA gather with every plane
+// index replaced by its opposite, and its store is a plain own-cell store.
 // Zero-gradient outflow (+x face) copies what the upstream cell x-1 receives; both cells
 // sit in the same warp (nx % 32 != 1), which passes the value with a warp shuffle before
 // any thread writes.
@@ -62,6 +65,7 @@ constexpr float MLP_XCLAMP = 8.f;
 struct KParams {
   void* f;               // population array, q planes of `plane` elements
   void* fp[27];          // fp[i] = start of plane i (per-direction base pointers)
+  void* fq[27];          // two-grid pull: planes of the destination array
   const uint8_t* flags;  // raw cell flags, padded layout
   const uint8_t* cls;    // cell classes, padded layout
   const float* mlp;      // MLP parameters (bf16 values widened to float), device
@@ -180,6 +184,8 @@ struct Nbr {
 };
 
 // ---- loading the pre-collision populations of one cell ---------------------------------
+// PAR 0: natural layout (own slots); 1: AA swapped layout (gather); 2: post-collision values
+// in natural layout (two-grid pull, gather).
 template <int Q, class S, int PAR>
 __device__ __forceinline__ void load_state(const KParams& p, int x, int y, int z, int cell, int cls,
                                            float (&f)[Q], unsigned& outmask) {
@@ -204,7 +210,7 @@ __device__ __forceinline__ void load_state(const KParams& p, int x, int y, int z
     Nbr nb;
     nb.init(p, x, y, z);
 #pragma unroll
-    for (int i = 0; i < Q; i++) f[i] = ld<S>(plane_ptr<S>(p, opp(i)) + nb.src(p, i));
+    for (int i = 0; i < Q; i++) f[i] = ld<S>(plane_ptr<S>(p, PAR == 2 ? i : opp(i)) + nb.src(p, i));
   } else {
 #pragma unroll
     for (int i = 0; i < Q; i++) {
@@ -213,7 +219,7 @@ __device__ __forceinline__ void load_state(const KParams& p, int x, int y, int z
       if (k == K_OUTCOPY) {
         outmask |= 1u << i;
       } else {
-        float v = ld<S>(plane_ptr<S>(p, pl) + ce);
+        float v = ld<S>(plane_ptr<S>(p, PAR == 2 ? opp(pl) : pl) + ce);
         // moving-wall value rounded like the natural-layout slot that holds it
         if (k == K_INFLOW) v = rnd<S>(v + p.inflow_term[i]);
         f[i] = v;
@@ -239,10 +245,15 @@ __device__ __forceinline__ void outflow_fix(const KParams& p, int x, float (&f)[
 }
 
 // ---- storing the post-collision populations -------------------------------------------
+// PAR 0: own cell, swapped slots (AA even); 1: back into the gathered slots (AA odd);
+// 2: own cell, natural slots of the destination array (two-grid pull).
 template <int Q, class S, int PAR>
 __device__ __forceinline__ void store_state(const KParams& p, int x, int y, int z, int cell, int cls,
                                             const float (&fs)[Q]) {
-  if (PAR == 0) {
+  if (PAR == 2) {
+#pragma unroll
+    for (int i = 0; i < Q; i++) st<S>(static_cast<S*>(p.fq[i]) + cell, fs[i]);
+  } else if (PAR == 0) {
 #pragma unroll
     for (int i = 0; i < Q; i++) st<S>(plane_ptr<S>(p, opp(i)) + cell, fs[i]);
   } else if (cls == CLS_INTERIOR) {
@@ -469,17 +480,58 @@ __device__ __forceinline__ float collide(const KParams& p, float (&f)[Q]) {
   const int cell = cidx(p, x, y, z);                      \
   const int cls = x < p.nx ? p.cls[cell] : CLS_SKIP;
 
-template <int Q, class S, int CL, int PAR>
+// LOAD / STORE modes as in load_state / store_state: AA even (0, 0), AA odd (1, 1), first
+// pull step after an import (0, 2), pull step (2, 2).
+template <int Q, class S, int CL, int LOAD, int STORE>
 __global__ void __launch_bounds__(128, CL == CL_MLP ? 4 : 8) k_step(const __grid_constant__ KParams p) {
   LBM_CELL_COORDS
   float f[Q];
   unsigned outmask;
-  load_state<Q, S, PAR>(p, x, y, z, cell, cls, f, outmask);
+  load_state<Q, S, LOAD>(p, x, y, z, cell, cls, f, outmask);
   outflow_fix<Q>(p, x, f, outmask);
   if (cls == CLS_SKIP) return;
   const float rho = collide<Q, CL>(p, f);
   if (!(rho > 0.f && rho < 3.0e38f)) atomicOr(p.status, 1);
-  store_state<Q, S, PAR>(p, x, y, z, cell, cls, f);
+  store_state<Q, S, STORE>(p, x, y, z, cell, cls, f);
+}
+
+// The same step with register double-buffering along z: each thread updates ZC cells
+// (x, y, z0 .. z0+ZC-1) and loads the next cell's populations before colliding the current
+// one, so a warp keeps one cell's loads in flight through its arithmetic.  Consecutive
+// cells of a thread own disjoint slots in both AA launches, so the early load is safe.
+template <int Q, class S, int CL, int PAR, int ZC>
+__global__ void __launch_bounds__(128, CL == CL_MLP ? 4 : 5) k_step_zp(const __grid_constant__ KParams p) {
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z0 = blockIdx.z * ZC;
+  if (y >= p.ny) return;  // whole warp
+  const int zend = min(p.nz, z0 + ZC);
+  float f[Q], g[Q];
+  unsigned outmask, outmask_g = 0;
+  int cell = cidx(p, x, y, z0);
+  int cls = x < p.nx ? p.cls[cell] : CLS_SKIP;
+  load_state<Q, S, PAR>(p, x, y, z0, cell, cls, f, outmask);
+#pragma unroll 1
+  for (int z = z0; z < zend; z++) {
+    const int zn = z + 1;
+    int celln = 0, clsn = CLS_SKIP;
+    if (zn < zend) {
+      celln = cidx(p, x, y, zn);
+      clsn = x < p.nx ? p.cls[celln] : CLS_SKIP;
+      load_state<Q, S, PAR>(p, x, y, zn, celln, clsn, g, outmask_g);
+    }
+    outflow_fix<Q>(p, x, f, outmask);
+    if (cls != CLS_SKIP) {
+      const float rho = collide<Q, CL>(p, f);
+      if (!(rho > 0.f && rho < 3.0e38f)) atomicOr(p.status, 1);
+      store_state<Q, S, PAR>(p, x, y, z, cell, cls, f);
+    }
+#pragma unroll
+    for (int i = 0; i < Q; i++) f[i] = g[i];
+    outmask = outmask_g;
+    cell = celln;
+    cls = clsn;
+  }
 }
 
 // Exports of the current state (read-only): populations, moments, FP64 sums, statistics.
@@ -544,6 +596,58 @@ __global__ void __launch_bounds__(128) k_export(const __grid_constant__ KParams 
       const double s = warp_sum(v[k]);
       if ((threadIdx.x & 31) == 0) atomicAdd(a.sums + (long long)y * 10 + k, s);
     }
+  }
+}
+
+// FP64 sums over fluid cells: MODE EX_SUM -> sums[0..3] = (rho, rho u); MODE EX_STATS ->
+// per y plane, sums[y*10 + k] = (count, u, u^2 components, u_x u_y, u_x u_z, u_y u_z).
+// Grid (ny, z chunks) of 128-thread blocks; each block walks whole rows of one y plane (a warp
+// covers 32 aligned x, as the outflow shuffle needs), reduces in the block and adds once.
+template <int Q, class S, int PAR, int MODE>
+__global__ void __launch_bounds__(128) k_plane_sums(const __grid_constant__ KParams p, double* sums, int zchunk) {
+  constexpr int K = MODE == EX_SUM ? 4 : 10;
+  const int y = blockIdx.x;
+  const int z0 = blockIdx.y * zchunk, z1 = min(p.nz, z0 + zchunk);
+  double acc[K];
+#pragma unroll
+  for (int k = 0; k < K; k++) acc[k] = 0.0;
+  for (int z = z0; z < z1; z++) {
+    for (int xb = 0; xb < p.nxp; xb += 128) {
+      const int x = xb + threadIdx.x;
+      const bool in = x < p.nxp;
+      const int cell = in ? cidx(p, x, y, z) : 0;
+      const int cls = (in && x < p.nx) ? p.cls[cell] : CLS_SKIP;
+      float f[Q];
+      unsigned outmask;
+      load_state<Q, S, PAR>(p, x, y, z, cell, cls, f, outmask);
+      outflow_fix<Q>(p, x, f, outmask);
+      if (cls == CLS_SKIP) continue;
+      const Mom<Q> m = moments<Q>(p, f);
+      if (MODE == EX_SUM) {
+        const double r = m.rho;
+        acc[0] += r;
+        acc[1] += r * m.ux;
+        acc[2] += r * m.uy;
+        acc[3] += r * m.uz;
+      } else {
+        const double ux = m.ux, uy = m.uy, uz = m.uz;
+        const double v[10] = {1.0, ux, uy, uz, ux * ux, uy * uy, uz * uz, ux * uy, ux * uz, uy * uz};
+#pragma unroll
+        for (int k = 0; k < K; k++) acc[k] += v[k];
+      }
+    }
+  }
+  __shared__ double red[K][4];
+#pragma unroll
+  for (int k = 0; k < K; k++) {
+    const double v = warp_sum(acc[k]);
+    if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+    const double v = red[threadIdx.x][0] + red[threadIdx.x][1] + red[threadIdx.x][2] + red[threadIdx.x][3];
+    if (MODE == EX_SUM) atomicAdd(sums + threadIdx.x, v);
+    else atomicAdd(sums + (long long)y * 10 + threadIdx.x, v);
   }
 }
 

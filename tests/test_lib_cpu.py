@@ -54,6 +54,7 @@ def test_params_default(lib):
     assert p.struct_size == ctypes.sizeof(lbm.lbm_params)
     assert p.magic_lambda == 3.0 / 16.0 and p.cs_smag == 0.1 and p.rho_inflow == 1.0
     assert list(p.face_bc) == [0] * 6 and p.precision == 0 and p.streaming == 0
+    assert p.pipeline == 1  # direct loads
 
 
 def test_create_rejects_bad_arguments_before_touching_the_device(lib):
