@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -92,6 +93,14 @@ static KParams kparams(const lbm_s* h) {
     for (int i = 0; i < 27; i++) {
       p.fp[i] = i < h->q ? (void*)((char*)a + (size_t)i * (size_t)plane_of(h) * sb) : nullptr;
       p.fq[i] = (i < h->q && b) ? (void*)((char*)b + (size_t)i * (size_t)plane_of(h) * sb) : nullptr;
+    }
+    int c[81];
+    lbm_stencil(27, c, nullptr);
+    for (int i = 0; i < h->q; i++) {
+      const long long off = c[3 * i] + (long long)c[3 * i + 1] * h->nxp + (long long)c[3 * i + 2] * h->nxp * h->ny;
+      const int o = i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1);
+      p.ga[i] = (void*)((uintptr_t)p.fp[o] - (uintptr_t)(off * (long long)sb));
+      p.gb[i] = (void*)((uintptr_t)p.fp[i] - (uintptr_t)(off * (long long)sb));
     }
   }
   p.nat_valid = h->nat_valid;
@@ -221,6 +230,7 @@ __global__ void k_classify(const __grid_constant__ KParams p, uint8_t* cls, int 
   const int xc[3] = {x, y, z};
   const int n[3] = {p.nx, p.ny, p.nz};
   int c = CLS_INTERIOR;
+  bool wrap_yz = false;
   for (int i = 1; i < q && c == CLS_INTERIOR; i++) {
     const int d[3] = {cx(i), cy(i), cz(i)};
     int s[3];
@@ -228,11 +238,13 @@ __global__ void k_classify(const __grid_constant__ KParams p, uint8_t* cls, int 
       s[a] = xc[a] - d[a];
       if (s[a] < 0 || s[a] >= n[a]) {
         if (p.face[2 * a] != FACE_PERIODIC) c = CLS_BOUNDARY;
+        else if (a > 0) wrap_yz = true;
         s[a] = s[a] < 0 ? s[a] + n[a] : s[a] - n[a];
       }
     }
     if (c == CLS_INTERIOR && p.flags[cidx(p, s[0], s[1], s[2])] != CELL_FLUID) c = CLS_BOUNDARY;
   }
+  if (c == CLS_INTERIOR && wrap_yz) c = CLS_WRAP;
   cls[cell] = (uint8_t)c;
 }
 

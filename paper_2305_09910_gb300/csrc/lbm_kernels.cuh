@@ -50,9 +50,10 @@ __host__ __device__ constexpr float wgt(int i) {
 // ---- flags, faces, cell classes ------------------------------------------------------
 enum : int { CELL_FLUID = 0, CELL_SOLID = 1, CELL_INFLOW = 2 };
 enum : int { FACE_PERIODIC = 0, FACE_WALL = 1, FACE_FREESLIP = 2, FACE_INFLOW = 3, FACE_OUTFLOW = 4 };
-// cls: interior fluid (every source is a fluid cell reached by plain or periodic streaming),
-// boundary fluid (some source needs a rule), and everything that is not updated.
-enum : int { CLS_INTERIOR = 0, CLS_BOUNDARY = 1, CLS_SKIP = 2 };
+// cls: interior fluid (every source is a fluid cell reached by plain streaming, or by a
+// periodic wrap in x), wrap fluid (as interior, but a source wraps across a periodic y or z
+// face), boundary fluid (some source needs a rule), and everything that is not updated.
+enum : int { CLS_INTERIOR = 0, CLS_BOUNDARY = 1, CLS_SKIP = 2, CLS_WRAP = 3 };
 enum : int { CL_NONE = 0, CL_SMAG = 1, CL_MLP = 2 };
 enum : int { K_STREAM = 0, K_BB = 1, K_INFLOW = 2, K_OUTCOPY = 3 };
 
@@ -66,6 +67,11 @@ struct KParams {
   void* f;               // population array, q planes of `plane` elements
   void* fp[27];          // fp[i] = start of plane i (per-direction base pointers)
   void* fq[27];          // two-grid pull: planes of the destination array
+  // gather bases of interior cells: the slot holding f_i(x) is ga[i] + cell (AA swapped
+  // layout) or gb[i] + cell (post-collision natural layout), i.e. the plane pointer moved by
+  // -(c_x + c_y nxp + c_z nxp ny) elements; x wraps are applied to `cell` before use
+  void* ga[27];
+  void* gb[27];
   const uint8_t* flags;  // raw cell flags, padded layout
   const uint8_t* cls;    // cell classes, padded layout
   const float* mlp;      // MLP parameters (bf16 values widened to float), device
@@ -207,6 +213,15 @@ __device__ __forceinline__ void load_state(const KParams& p, int x, int y, int z
       }
     }
   } else if (cls == CLS_INTERIOR) {
+    // periodic x wrap of the row ends, applied to the cell index once per sign of c_x
+    const int cp = cell + (x == 0 ? p.nx : 0);       // sources x - 1
+    const int cm = cell - (x == p.nx - 1 ? p.nx : 0);  // sources x + 1
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+      const S* base = static_cast<const S*>(PAR == 2 ? p.gb[i] : p.ga[i]);
+      f[i] = ld<S>(base + (cx(i) > 0 ? cp : cx(i) < 0 ? cm : cell));
+    }
+  } else if (cls == CLS_WRAP) {
     Nbr nb;
     nb.init(p, x, y, z);
 #pragma unroll
@@ -257,6 +272,12 @@ __device__ __forceinline__ void store_state(const KParams& p, int x, int y, int 
 #pragma unroll
     for (int i = 0; i < Q; i++) st<S>(plane_ptr<S>(p, opp(i)) + cell, fs[i]);
   } else if (cls == CLS_INTERIOR) {
+    const int cp = cell + (x == 0 ? p.nx : 0);
+    const int cm = cell - (x == p.nx - 1 ? p.nx : 0);
+#pragma unroll
+    for (int i = 0; i < Q; i++)
+      st<S>(static_cast<S*>(p.ga[i]) + (cx(i) > 0 ? cp : cx(i) < 0 ? cm : cell), fs[opp(i)]);
+  } else if (cls == CLS_WRAP) {
     Nbr nb;
     nb.init(p, x, y, z);
 #pragma unroll

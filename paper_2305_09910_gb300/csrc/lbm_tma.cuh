@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(TMA_TX, CL == CL_MLP ? 4 : 5) k_step_tma(const
     // cells on the periodic x seam pull across the row end: their sources are not in this
     // tile's rows, so they take the direct path like boundary cells
     const bool seam = PAR && (x == 0 || x >= p.nx - 1);
-    if (cls == CLS_INTERIOR && !seam) {
+    if ((cls == CLS_INTERIOR || cls == CLS_WRAP) && !seam) {
       if (PAR == 0) {
 #pragma unroll
         for (int i = 0; i < Q; i++) f[i] = ld<S>(rows + i * RL + t);
