@@ -119,13 +119,14 @@ typedef struct {
   int32_t pipeline;     /* load pipeline of the AA step kernels (LBM_PIPE_*), default DIRECT */
 } lbm_params;
 
-/* load pipeline of the AA step kernels (two-grid pull always loads directly):
+/* load pipeline of the step kernels:
  * DIRECT (default) = every thread loads its cell from global memory;
- * TMA = loads staged in shared memory by 1-D bulk copies in a 3-stage mbarrier pipeline of
- *   persistent CTAs; PREFETCH = direct loads double-buffered in registers along z.
- * All three compute bit-identical updates; on GB300 DIRECT is the fastest (the step is
- * issue-bound, not latency-bound), so the others are kept as measured alternatives. */
-enum { LBM_PIPE_TMA = 0, LBM_PIPE_DIRECT = 1, LBM_PIPE_PREFETCH = 2 };
+ * TMA = AA loads staged in shared memory by 1-D bulk copies in a 3-stage mbarrier pipeline
+ *   of persistent CTAs; PREFETCH = AA loads double-buffered in registers along z;
+ * ASYNC = loads staged in shared memory by per-lane asynchronous copies (cp.async) a few
+ *   cells ahead along z (FP32 storage; AA and two-grid pull; half storage loads directly).
+ * All compute bit-identical updates. */
+enum { LBM_PIPE_TMA = 0, LBM_PIPE_DIRECT = 1, LBM_PIPE_PREFETCH = 2, LBM_PIPE_ASYNC = 3 };
 
 /* Fills p with the defaults listed above. */
 void lbm_params_default(lbm_params* p);

@@ -1,6 +1,7 @@
 // kern_inst.cu -- instantiates the kernels and launchers for one (stencil, precision) pair.
 // Compiled once per pair with -DLBM_Q=19|27 and -DLBM_S=float|__half|__nv_bfloat16.
 #include <algorithm>
+#include <type_traits>
 
 #include "lbm_launch.cuh"
 
@@ -15,8 +16,26 @@ namespace lbm {
 
 template <int Q, class S, int LOAD, int STORE>
 static void step_mode(const KParams& p, int closure, const Launch& L) {
+  if constexpr (sizeof(S) == 2 && Q == 19) {  // half storage: x-pairs, 64 x per warp (D3Q19)
+    if (closure != CL_MLP) {
+      dim3 g = L.grid;
+      g.x = (p.nxp + 63) / 64;
+      if (closure == CL_NONE) k_step_h2<Q, S, CL_NONE, LOAD, STORE><<<g, L.block, 0, L.stream>>>(p);
+      else k_step_h2<Q, S, CL_SMAG, LOAD, STORE><<<g, L.block, 0, L.stream>>>(p);
+      return;
+    }
+  }
+#ifndef LBM_PAIR
   if (closure == CL_NONE) k_step<Q, S, CL_NONE, LOAD, STORE><<<L.grid, L.block, 0, L.stream>>>(p);
   else if (closure == CL_SMAG) k_step<Q, S, CL_SMAG, LOAD, STORE><<<L.grid, L.block, 0, L.stream>>>(p);
+  else k_step<Q, S, CL_MLP, LOAD, STORE><<<L.grid, L.block, 0, L.stream>>>(p);
+  return;
+#endif
+  // two cells (y, y + 1) per thread without the learned closure: half the grid rows
+  dim3 g2 = L.grid;
+  g2.y = (p.ny + 2 * L.block.y - 1) / (2 * L.block.y);
+  if (closure == CL_NONE) k_step2<Q, S, CL_NONE, LOAD, STORE><<<g2, L.block, 0, L.stream>>>(p);
+  else if (closure == CL_SMAG) k_step2<Q, S, CL_SMAG, LOAD, STORE><<<g2, L.block, 0, L.stream>>>(p);
   else k_step<Q, S, CL_MLP, LOAD, STORE><<<L.grid, L.block, 0, L.stream>>>(p);
 }
 
@@ -30,6 +49,46 @@ cudaError_t launch_step(const KParams& p, int closure, int mode, const Launch& L
     default: step_mode<Q, S, 2, 2>(p, closure, L); break;
   }
   return cudaGetLastError();
+}
+
+#ifndef LBM_ASYNC_ZC
+#define LBM_ASYNC_ZC 8
+#endif
+#ifndef LBM_ASYNC_NST
+#define LBM_ASYNC_NST 2
+#endif
+
+template <int Q, int CL, int LOAD, int STORE>
+static cudaError_t async_one(const KParams& p, const Launch& L0) {
+  constexpr int ZC = LBM_ASYNC_ZC, NST = LBM_ASYNC_NST;
+  constexpr int smem = NST * Q * 128 * (int)sizeof(float);
+  static_assert(smem <= 48 * 1024, "stage buffers above the default dynamic shared memory limit");
+  Launch L = L0;
+  L.grid.z = (p.nz + ZC - 1) / ZC;
+  k_step_async<Q, CL, LOAD, STORE, ZC, NST><<<L.grid, L.block, smem, L.stream>>>(p);
+  return cudaGetLastError();
+}
+
+template <int Q, int LOAD, int STORE>
+static cudaError_t async_mode(const KParams& p, int closure, const Launch& L) {
+  if (closure == CL_NONE) return async_one<Q, CL_NONE, LOAD, STORE>(p, L);
+  if (closure == CL_SMAG) return async_one<Q, CL_SMAG, LOAD, STORE>(p, L);
+  return async_one<Q, CL_MLP, LOAD, STORE>(p, L);
+}
+
+// Staged (cp.async) step; FP32 storage only, the half forms take the direct kernels.
+template <int Q, class S>
+cudaError_t launch_step_async(const KParams& p, int closure, int mode, const Launch& L) {
+  if constexpr (!std::is_same<S, float>::value) {
+    return launch_step<Q, S>(p, closure, mode, L);
+  } else {
+    switch (mode) {
+      case 0: return async_mode<Q, 0, 0>(p, closure, L);
+      case 1: return async_mode<Q, 1, 1>(p, closure, L);
+      case 2: return async_mode<Q, 0, 2>(p, closure, L);
+      default: return async_mode<Q, 2, 2>(p, closure, L);
+    }
+  }
 }
 
 template <int Q, class S>
@@ -116,6 +175,7 @@ cudaError_t launch_set_pop(const KParams& p, const float* df, const Launch& L) {
 template cudaError_t launch_step<LBM_Q, LBM_S>(const KParams&, int, int, const Launch&);
 template cudaError_t launch_step_tma<LBM_Q, LBM_S>(const KParams&, int, int, cudaStream_t, int);
 template cudaError_t launch_step_zp<LBM_Q, LBM_S>(const KParams&, int, int, const Launch&);
+template cudaError_t launch_step_async<LBM_Q, LBM_S>(const KParams&, int, int, const Launch&);
 template cudaError_t launch_export<LBM_Q, LBM_S>(const KParams&, int, int, const ExportArgs&, const Launch&);
 template cudaError_t launch_init_eq<LBM_Q, LBM_S>(const KParams&, const float*, const float*, const Launch&);
 template cudaError_t launch_set_pop<LBM_Q, LBM_S>(const KParams&, const float*, const Launch&);

@@ -27,6 +27,7 @@ struct lbm_s {
   int cur = 0;                // pull: which array holds the state (0: f, 1: f2)
   uint8_t* flags = nullptr;   // raw flags, padded layout
   uint8_t* cls = nullptr;     // cell classes, padded layout
+  unsigned long long* rules = nullptr;  // per-direction rules of boundary cells, padded layout
   int* status = nullptr;      // device status word
   int* status_host = nullptr; // pinned copy
   double* sums = nullptr;     // 4 doubles (lbm_reduce)
@@ -106,6 +107,7 @@ static KParams kparams(const lbm_s* h) {
   p.nat_valid = h->nat_valid;
   p.flags = h->flags;
   p.cls = h->cls;
+  p.rules = h->rules;
   p.mlp = h->mlp;
   p.status = h->status;
   p.plane = plane_of(h);
@@ -142,12 +144,26 @@ static KParams kparams(const lbm_s* h) {
 template <int Q>
 static cudaError_t dispatch_step(const lbm_s* h, const KParams& p, int closure, int parity) {
   const Launch L = launch_cfg(h);
-  if (h->prm.streaming == LBM_PULL) {  // direct loads only
+  if (h->prm.streaming == LBM_PULL) {  // direct or staged loads
     const int mode = parity == 0 ? 2 : 3;
+    if (h->prm.pipeline == LBM_PIPE_ASYNC) {
+      switch (h->prm.precision) {
+        case LBM_F32: return launch_step_async<Q, float>(p, closure, mode, L);
+        case LBM_F16_SHIFTED: return launch_step_async<Q, __half>(p, closure, mode, L);
+        default: return launch_step_async<Q, __nv_bfloat16>(p, closure, mode, L);
+      }
+    }
     switch (h->prm.precision) {
       case LBM_F32: return launch_step<Q, float>(p, closure, mode, L);
       case LBM_F16_SHIFTED: return launch_step<Q, __half>(p, closure, mode, L);
       default: return launch_step<Q, __nv_bfloat16>(p, closure, mode, L);
+    }
+  }
+  if (h->prm.pipeline == LBM_PIPE_ASYNC) {
+    switch (h->prm.precision) {
+      case LBM_F32: return launch_step_async<Q, float>(p, closure, parity, L);
+      case LBM_F16_SHIFTED: return launch_step_async<Q, __half>(p, closure, parity, L);
+      default: return launch_step_async<Q, __nv_bfloat16>(p, closure, parity, L);
     }
   }
   if (h->prm.pipeline == LBM_PIPE_PREFETCH) {
@@ -217,7 +233,7 @@ __global__ void k_flags_in(const uint8_t* in, uint8_t* out, int nx, int ny, int 
 }
 
 // Cell classes: skip (non-fluid or padding), boundary (a source needs a rule), interior.
-__global__ void k_classify(const __grid_constant__ KParams p, uint8_t* cls, int q) {
+__global__ void k_classify(const __grid_constant__ KParams p, uint8_t* cls, unsigned long long* rules, int q) {
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
@@ -246,6 +262,11 @@ __global__ void k_classify(const __grid_constant__ KParams p, uint8_t* cls, int 
   }
   if (c == CLS_INTERIOR && wrap_yz) c = CLS_WRAP;
   cls[cell] = (uint8_t)c;
+  if (c == CLS_BOUNDARY) {
+    unsigned long long r = 0;
+    for (int i = 1; i < q; i++) r |= (unsigned long long)rule_of(p, x, y, z, i) << (2 * i);
+    rules[cell] = r;
+  }
 }
 
 // ---- accessors used by the other translation units (closure training) -------------------------
@@ -307,7 +328,7 @@ const char* lbm_last_error(lbm_handle h) { return h ? h->err.c_str() : g_create_
 static lbm_status launch_classify(lbm_handle h) {
   KParams p = kparams(h);
   Launch L = launch_cfg(h);
-  k_classify<<<L.grid, L.block, 0, h->stream>>>(p, h->cls, h->q);
+  k_classify<<<L.grid, L.block, 0, h->stream>>>(p, h->cls, h->rules, h->q);
   CUDA_TRY(h, cudaGetLastError());
   return LBM_OK;
 }
@@ -318,6 +339,7 @@ lbm_status lbm_destroy(lbm_handle h) {
   if (h->f2) cudaFreeAsync(h->f2, h->stream);
   if (h->flags) cudaFreeAsync(h->flags, h->stream);
   if (h->cls) cudaFreeAsync(h->cls, h->stream);
+  if (h->rules) cudaFreeAsync(h->rules, h->stream);
   if (h->status) cudaFreeAsync(h->status, h->stream);
   if (h->sums) cudaFreeAsync(h->sums, h->stream);
   if (h->stats) cudaFreeAsync(h->stats, h->stream);
@@ -351,7 +373,7 @@ lbm_status lbm_create(int nx, int ny, int nz, int stencil, double tau, const lbm
     return fail(nullptr, LBM_EINVAL, "unknown closure %d", p.closure);
   if (p.streaming != LBM_AA && p.streaming != LBM_PULL)
     return fail(nullptr, LBM_EINVAL, "unknown streaming %d", p.streaming);
-  if (p.pipeline != LBM_PIPE_TMA && p.pipeline != LBM_PIPE_DIRECT && p.pipeline != LBM_PIPE_PREFETCH)
+  if (p.pipeline < LBM_PIPE_TMA || p.pipeline > LBM_PIPE_ASYNC)
     return fail(nullptr, LBM_EINVAL, "unknown pipeline %d", p.pipeline);
   if (!(p.cs_smag >= 0.0)) return fail(nullptr, LBM_EINVAL, "cs_smag must be >= 0");
   for (int k = 0; k < 6; k++)
@@ -394,6 +416,7 @@ lbm_status lbm_create(int nx, int ny, int nz, int stencil, double tau, const lbm
   if (e == cudaSuccess && h->f2) e = cudaMemsetAsync(h->f2, 0, fbytes, h->stream);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->flags, (size_t)plane, h->stream);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->cls, (size_t)plane, h->stream);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->rules, (size_t)plane * 8, h->stream);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->status, sizeof(int), h->stream);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->sums, 4 * sizeof(double), h->stream);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->stats, (size_t)ny * LBM_STATS_K * sizeof(double), h->stream);

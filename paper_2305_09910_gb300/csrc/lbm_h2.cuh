@@ -1,0 +1,166 @@
+// lbm_h2.cuh -- the step for half-precision storage with two x-adjacent cells per thread.
+//
+// A lane owns cells (x, x+1), x even, so every slot the pair owns in a direction with
+// c_x = 0 (and every own-cell slot) is one aligned 32-bit word holding both cells' 16-bit
+// values: one load and one store move two populations.  Slots shifted in x by the odd AA
+// gather (c_x != 0) straddle two words and move as two 16-bit accesses.  The loaded words
+// stay packed (one register per direction for both cells); cell x is unpacked and collided
+// first, then cell x+1, and the two results are rounded and packed into one word each.
+// This halves the memory instructions and address arithmetic per cell and doubles the
+// bytes a thread keeps in flight, at the register cost of the one-cell kernel.
+//
+// Warps with any non-interior cell (boundary rules, periodic y/z wrap, skipped cells) take
+// the one-cell code for each of their two cells instead; the zero-gradient outflow passes
+// what cell x-1 receives from the lane that owns it (nx % 32 != 1 keeps x = nx-1 off lane 0).
+// Block (32, 4) covers 64 x 4 cells of one z plane; grid (ceil(nxp/64), ceil(ny/4), nz).
+#pragma once
+
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+template <class S> __device__ __forceinline__ float lo_of(uint32_t v);
+template <class S> __device__ __forceinline__ float hi_of(uint32_t v);
+template <> __device__ __forceinline__ float lo_of<__half>(uint32_t v) {
+  return __half2float(__ushort_as_half((unsigned short)(v & 0xffffu)));
+}
+template <> __device__ __forceinline__ float hi_of<__half>(uint32_t v) {
+  return __half2float(__ushort_as_half((unsigned short)(v >> 16)));
+}
+template <> __device__ __forceinline__ float lo_of<__nv_bfloat16>(uint32_t v) { return __uint_as_float(v << 16); }
+template <> __device__ __forceinline__ float hi_of<__nv_bfloat16>(uint32_t v) {
+  return __uint_as_float(v & 0xffff0000u);
+}
+
+// 16-bit pattern of v rounded to the storage precision (round to nearest even)
+template <class S> __device__ __forceinline__ uint32_t bits16(float v);
+template <> __device__ __forceinline__ uint32_t bits16<__half>(float v) { return __half_as_ushort(__float2half_rn(v)); }
+template <> __device__ __forceinline__ uint32_t bits16<__nv_bfloat16>(float v) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+
+// Zero-gradient outflow for x-pairs: cell x-1 of lane t's first cell is lane t-1's second.
+template <int Q>
+__device__ __forceinline__ void outflow_fix2(const KParams& p, int x0, float (&fa)[Q], float (&fb)[Q],
+                                             unsigned oa, unsigned ob) {
+  if (!p.outflow) return;
+  if (!(x0 <= p.nx - 1 && p.nx - 1 < x0 + 64)) return;  // warp-uniform
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    if (cx(i) != -1) continue;
+    const float v = __shfl_up_sync(0xffffffffu, fb[i], 1);
+    if (ob & (1u << i)) fb[i] = fa[i];  // x-1 is this lane's first cell (never itself an outflow cell)
+    if (oa & (1u << i)) fa[i] = v;
+  }
+}
+
+// Slot offsets of the two cells' sources in a direction with c_x != 0 (periodic x wrap).
+__device__ __forceinline__ void xsrc(int c, const KParams& p, int x, int cell, int& ca, int& cb) {
+  if (c > 0) {  // sources x-1, x
+    ca = cell + (x == 0 ? p.nx : 0);
+    cb = cell + 1;
+  } else {       // sources x+1, x+2
+    ca = cell;
+    cb = cell + 1 - (x + 1 == p.nx - 1 ? p.nx : 0);
+  }
+}
+
+// One-cell code for both cells of a lane (warps with a non-interior cell).  Kept out of
+// line so that the rare path does not take registers from the fast one.
+template <int Q, class S, int CL, int LOAD, int STORE>
+__device__ __noinline__ void pair_fallback(const KParams& p, int x, int y, int z, int cell, int clsA, int clsB) {
+  float fa[Q], fb[Q];
+  unsigned oa, ob;
+  load_state<Q, S, LOAD>(p, x, y, z, cell, clsA, fa, oa);
+  load_state<Q, S, LOAD>(p, x + 1, y, z, cell + 1, clsB, fb, ob);
+  outflow_fix2<Q>(p, 64 * blockIdx.x, fa, fb, oa, ob);
+  if (clsA != CLS_SKIP) {
+    const float r = collide<Q, CL, float, false>(p, fa);
+    if (!(r > 0.f && r < 3.0e38f)) atomicOr(p.status, 1);
+    store_state<Q, S, STORE>(p, x, y, z, cell, clsA, fa);
+  }
+  if (clsB != CLS_SKIP) {
+    const float r = collide<Q, CL, float, false>(p, fb);
+    if (!(r > 0.f && r < 3.0e38f)) atomicOr(p.status, 1);
+    store_state<Q, S, STORE>(p, x + 1, y, z, cell + 1, clsB, fb);
+  }
+}
+
+#ifndef LBM_H2_MINB
+#define LBM_H2_MINB 8
+#endif
+template <int Q, class S, int CL, int LOAD, int STORE>
+__global__ void __launch_bounds__(128, LBM_H2_MINB) k_step_h2(const __grid_constant__ KParams p) {
+  static_assert(sizeof(S) == 2, "two 16-bit populations per word");
+  const int x = 2 * (blockIdx.x * 32 + threadIdx.x);
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (y >= p.ny) return;  // whole warp
+  const int cell = cidx(p, x, y, z);
+  int ca_ = CLS_SKIP, cb_ = CLS_SKIP;
+  if (x < p.nx) {
+    const unsigned c2 = *reinterpret_cast<const unsigned short*>(p.cls + cell);
+    ca_ = c2 & 0xff;
+    cb_ = x + 1 < p.nx ? (int)(c2 >> 8) : CLS_SKIP;
+  }
+  const int clsA = ca_, clsB = cb_;
+  const bool fast = LOAD == 0 ? ((clsA == CLS_INTERIOR || clsA == CLS_WRAP) && (clsB == CLS_INTERIOR || clsB == CLS_WRAP))
+                              : (clsA == CLS_INTERIOR && clsB == CLS_INTERIOR);
+  if (__all_sync(0xffffffffu, fast)) {
+    uint32_t h[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+      if (LOAD == 0) {
+        h[i] = *reinterpret_cast<const uint32_t*>(plane_ptr<S>(p, i) + cell);
+      } else {
+        const S* base = static_cast<const S*>(LOAD == 2 ? p.gb[i] : p.ga[i]);
+        if (cx(i) == 0) {
+          h[i] = *reinterpret_cast<const uint32_t*>(base + cell);
+        } else {
+          int a, b;
+          xsrc(cx(i), p, x, cell, a, b);
+          const uint32_t lo = *reinterpret_cast<const unsigned short*>(base + a);
+          const uint32_t hi = *reinterpret_cast<const unsigned short*>(base + b);
+          h[i] = lo | (hi << 16);
+        }
+      }
+    }
+    // first cell: unpack, collide, round back into the low halves
+    float f[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) f[i] = lo_of<S>(h[i]);
+    const float ra = collide<Q, CL, float, false>(p, f);
+#pragma unroll
+    for (int i = 0; i < Q; i++) h[i] = __byte_perm(h[i], bits16<S>(f[i]), 0x3254);
+    // second cell: the high halves
+#pragma unroll
+    for (int i = 0; i < Q; i++) f[i] = hi_of<S>(h[i]);
+    const float rb = collide<Q, CL, float, false>(p, f);
+#pragma unroll
+    for (int i = 0; i < Q; i++) h[i] = __byte_perm(h[i], bits16<S>(f[i]), 0x5410);
+    if (!(ra > 0.f && ra < 3.0e38f) || !(rb > 0.f && rb < 3.0e38f)) atomicOr(p.status, 1);
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+      if (STORE == 0) {
+        *reinterpret_cast<uint32_t*>(plane_ptr<S>(p, opp(i)) + cell) = h[i];
+      } else if (STORE == 2) {
+        *reinterpret_cast<uint32_t*>(static_cast<S*>(p.fq[i]) + cell) = h[i];
+      } else {  // back into the slots the gather of direction i read: f*_opp(i)
+        S* base = static_cast<S*>(p.ga[i]);
+        const uint32_t v = h[opp(i)];
+        if (cx(i) == 0) {
+          *reinterpret_cast<uint32_t*>(base + cell) = v;
+        } else {
+          int a, b;
+          xsrc(cx(i), p, x, cell, a, b);
+          *reinterpret_cast<unsigned short*>(base + a) = (unsigned short)(v & 0xffffu);
+          *reinterpret_cast<unsigned short*>(base + b) = (unsigned short)(v >> 16);
+        }
+      }
+    }
+    return;
+  }
+  pair_fallback<Q, S, CL, LOAD, STORE>(p, x, y, z, cell, clsA, clsB);
+}
+
+}  // namespace lbm

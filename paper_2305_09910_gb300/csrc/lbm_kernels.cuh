@@ -29,6 +29,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
 #include <utility>
 
 namespace lbm {
@@ -56,6 +57,7 @@ enum : int { FACE_PERIODIC = 0, FACE_WALL = 1, FACE_FREESLIP = 2, FACE_INFLOW = 
 enum : int { CLS_INTERIOR = 0, CLS_BOUNDARY = 1, CLS_SKIP = 2, CLS_WRAP = 3 };
 enum : int { CL_NONE = 0, CL_SMAG = 1, CL_MLP = 2 };
 enum : int { K_STREAM = 0, K_BB = 1, K_INFLOW = 2, K_OUTCOPY = 3 };
+enum : int { R_STREAM = 0, R_BB = 1, R_INFLOW = 2, R_SPECIAL = 3 };
 
 constexpr int MLP_NIN = 7, MLP_NH = 32;
 constexpr int MLP_NPARAM = MLP_NH * MLP_NIN + MLP_NH + MLP_NH * MLP_NH + MLP_NH + MLP_NH + 1;
@@ -74,6 +76,11 @@ struct KParams {
   void* gb[27];
   const uint8_t* flags;  // raw cell flags, padded layout
   const uint8_t* cls;    // cell classes, padded layout
+  // boundary cells: 2 bits per direction i (bits 2i, 2i+1) naming the rule of the incoming
+  // population: R_STREAM (periodic-wrapped neighbour x - c_i), R_BB (bounce-back from the
+  // own cell), R_INFLOW (moving-wall bounce-back), R_SPECIAL (free-slip reflection or
+  // zero-gradient outflow copy, resolved from the geometry alone)
+  const unsigned long long* rules;
   const float* mlp;      // MLP parameters (bf16 values widened to float), device
   int* status;           // bit 0: non-finite or non-positive density seen
   long long plane;       // nxp * ny * nz
@@ -167,6 +174,43 @@ static __device__ __noinline__ int classify(const KParams& p, int x, int y, int 
   return K_STREAM;
 }
 
+// The 2-bit rule of (cell, direction) from classify's answer: plain streaming from the
+// periodic-wrapped neighbour, bounce-back, moving-wall bounce-back, or special.
+__device__ __forceinline__ int rule_of(const KParams& p, int x, int y, int z, int i) {
+  int pl, ce;
+  const int k = classify(p, x, y, z, i, pl, ce);
+  if (k == K_BB) return R_BB;
+  if (k == K_INFLOW) return R_INFLOW;
+  if (k == K_OUTCOPY) return R_SPECIAL;
+  return pl == opp(i) ? R_STREAM : R_SPECIAL;  // a free-slip reflection changes the plane
+}
+
+// classify() for a direction whose rule is R_SPECIAL, without reading flags: the outflow copy
+// at x = nx-1 (c_x = -1), otherwise the free-slip reflection (with periodic wraps on other axes).
+static __device__ __noinline__ int resolve_special(const KParams& p, int x, int y, int z, int i,
+                                                   int& plane, int& cell) {
+  if (p.outflow && x == p.nx - 1 && cx(i) == -1) return K_OUTCOPY;
+  const int c[3] = {cx(i), cy(i), cz(i)};
+  const int xc[3] = {x, y, z};
+  const int n[3] = {p.nx, p.ny, p.nz};
+  int s[3], d[3];
+  for (int a = 0; a < 3; a++) {
+    s[a] = xc[a] - c[a];
+    d[a] = c[a];
+    if (s[a] < 0 || s[a] >= n[a]) {
+      if (p.face[s[a] < 0 ? 2 * a : 2 * a + 1] == FACE_PERIODIC) {
+        s[a] = s[a] < 0 ? s[a] + n[a] : s[a] - n[a];
+      } else {
+        s[a] = xc[a];
+        d[a] = -d[a];
+      }
+    }
+  }
+  plane = opp(dir_index(d[0], d[1], d[2]));
+  cell = cidx(p, s[0], s[1], s[2]);
+  return K_STREAM;
+}
+
 template <class S>
 __device__ __forceinline__ S* plane_ptr(const KParams& p, int i) {
   return static_cast<S*>(p.fp[i]);
@@ -205,12 +249,10 @@ __device__ __forceinline__ void load_state(const KParams& p, int x, int y, int z
     // after a streaming step the outflow slots of x = nx-1 were not written (they are
     // copies of the upstream cell); after an import they hold the imported values
     if (cls == CLS_BOUNDARY && p.outflow && !p.nat_valid && x == p.nx - 1) {
+      const unsigned long long r = p.rules[cell];
 #pragma unroll
-      for (int i = 0; i < Q; i++) {
-        if (cx(i) != -1) continue;
-        int pl, ce;
-        if (classify(p, x, y, z, i, pl, ce) == K_OUTCOPY) outmask |= 1u << i;
-      }
+      for (int i = 0; i < Q; i++)
+        if (cx(i) == -1 && ((r >> (2 * i)) & 3) == R_SPECIAL) outmask |= 1u << i;
     }
   } else if (cls == CLS_INTERIOR) {
     // periodic x wrap of the row ends, applied to the cell index once per sign of c_x
@@ -227,17 +269,32 @@ __device__ __forceinline__ void load_state(const KParams& p, int x, int y, int z
 #pragma unroll
     for (int i = 0; i < Q; i++) f[i] = ld<S>(plane_ptr<S>(p, PAR == 2 ? i : opp(i)) + nb.src(p, i));
   } else {
+    // boundary cell: the precomputed rules make every load independent of the others
+    const unsigned long long r = p.rules[cell];
+    Nbr nb;
+    nb.init(p, x, y, z);
+    unsigned special = 0;
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-      int pl, ce;
-      const int k = classify(p, x, y, z, i, pl, ce);
-      if (k == K_OUTCOPY) {
-        outmask |= 1u << i;
-      } else {
-        float v = ld<S>(plane_ptr<S>(p, PAR == 2 ? opp(pl) : pl) + ce);
-        // moving-wall value rounded like the natural-layout slot that holds it
-        if (k == K_INFLOW) v = rnd<S>(v + p.inflow_term[i]);
-        f[i] = v;
+      const int k = (int)((r >> (2 * i)) & 3);
+      if (k == R_SPECIAL) {
+        special |= 1u << i;
+        continue;
+      }
+      const S* a = k == R_STREAM ? plane_ptr<S>(p, PAR == 2 ? i : opp(i)) + nb.src(p, i)
+                                 : plane_ptr<S>(p, PAR == 2 ? opp(i) : i) + cell;
+      float v = ld<S>(a);
+      // moving-wall value rounded like the natural-layout slot that holds it
+      if (k == R_INFLOW) v = rnd<S>(v + p.inflow_term[i]);
+      f[i] = v;
+    }
+    if (special) {
+#pragma unroll
+      for (int i = 0; i < Q; i++) {
+        if (!(special & (1u << i))) continue;
+        int pl, ce;
+        if (resolve_special(p, x, y, z, i, pl, ce) == K_OUTCOPY) outmask |= 1u << i;
+        else f[i] = ld<S>(plane_ptr<S>(p, PAR == 2 ? opp(pl) : pl) + ce);
       }
     }
   }
@@ -283,13 +340,21 @@ __device__ __forceinline__ void store_state(const KParams& p, int x, int y, int 
 #pragma unroll
     for (int i = 0; i < Q; i++) st<S>(plane_ptr<S>(p, opp(i)) + nb.src(p, i), fs[opp(i)]);
   } else {
+    const unsigned long long r = p.rules[cell];
+    Nbr nb;
+    nb.init(p, x, y, z);
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-      int pl, ce;
-      const int k = classify(p, x, y, z, i, pl, ce);
-      if (k == K_OUTCOPY) continue;
+      const int k = (int)((r >> (2 * i)) & 3);
+      int pl = opp(i), ce = nb.src(p, i);
+      if (k == R_BB || k == R_INFLOW) {
+        pl = i;
+        ce = cell;
+      } else if (k == R_SPECIAL) {
+        if (resolve_special(p, x, y, z, i, pl, ce) == K_OUTCOPY) continue;
+      }
       float v = fs[opp(i)];
-      if (k == K_INFLOW) v = rnd<S>(v) + p.inflow_term[i];  // same rounding as the swapped path
+      if (k == R_INFLOW) v = rnd<S>(v) + p.inflow_term[i];  // same rounding as the swapped path
       st<S>(plane_ptr<S>(p, pl) + ce, v);
     }
   }
@@ -368,126 +433,262 @@ __device__ __forceinline__ Mom<Q> moments(const KParams& p, const float (&f)[Q])
   return m;
 }
 
-struct CollCtx {
-  float ux, uy, uz, jx, jy, jz;
-  float A, B;        // equilibrium symmetric part: w (A + B (c.u)^2), A = drho - 1.5 rho u^2, B = 4.5 rho
-  float hwp, hwm;    // omega+/2, omega-/2
-  float gp, gm;      // 1 - omega+/2, 1 - omega-/2
-  float gu3;         // (1 - omega+/2) 3 u.F
+// ---- arithmetic on one cell (float) or two cells (float2, the packed FP32x2 pipe) ---------
+// Every operation rounds once to nearest even and none is contracted by the compiler, so
+// a thread that updates two cells gives each the bits a one-cell thread gives it.
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b as b * (-1) + a: the product is exact, so this is the correctly rounded difference
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+template <class V> __device__ __forceinline__ V vset(float a);
+template <> __device__ __forceinline__ float vset<float>(float a) { return a; }
+template <> __device__ __forceinline__ float2 vset<float2>(float a) { return make_float2(a, a); }
+
+template <class V> struct Lanes;
+template <> struct Lanes<float> {
+  static constexpr int n = 1;
+  __device__ __forceinline__ static float get(float v, int) { return v; }
+  __device__ __forceinline__ static void put(float& v, int, float a) { v = a; }
+};
+template <> struct Lanes<float2> {
+  static constexpr int n = 2;
+  __device__ __forceinline__ static float get(float2 v, int k) { return k ? v.y : v.x; }
+  __device__ __forceinline__ static void put(float2& v, int k, float a) { (k ? v.y : v.x) = a; }
 };
 
-// Sums over the +/- pairs: s_P = f_i + f_opp(i), d_P = f_i - f_opp(i) (i = 2P+1).
-template <int Q, int I>
-__device__ __forceinline__ void pair_moments(const float (&f)[Q], float (&m)[10]) {
-  constexpr int X = cx(I), Y = cy(I), Z = cz(I);
-  const float s = f[I] + f[I + 1];
-  const float d = f[I] - f[I + 1];
-  m[0] += s;
-  if (X) m[1] += X > 0 ? d : -d;
-  if (Y) m[2] += Y > 0 ? d : -d;
-  if (Z) m[3] += Z > 0 ? d : -d;
-  if (X) m[4] += s;
-  if (Y) m[5] += s;
-  if (Z) m[6] += s;
-  if (X * Y) m[7] += X * Y > 0 ? s : -s;
-  if (X * Z) m[8] += X * Z > 0 ? s : -s;
-  if (Y * Z) m[9] += Y * Z > 0 ? s : -s;
+// Orientation of the +/- pair (I, I+1), I odd: the member whose first non-zero velocity
+// component is positive is the primary one, so that c.u is a plain sum with a leading +.
+__host__ __device__ constexpr int lead(int i) { return cx(i) ? cx(i) : cy(i) ? cy(i) : cz(i); }
+__host__ __device__ constexpr int prim(int I) { return lead(I) > 0 ? I : I + 1; }
+
+// c . v for a velocity with entries in {-1, 0, 1} and a positive leading entry
+template <int X, int Y, int Z, class V>
+__device__ __forceinline__ V cdot(V vx, V vy, V vz) {
+  static_assert(X > 0 || (X == 0 && (Y > 0 || (Y == 0 && Z > 0))), "leading component must be positive");
+  V r;
+  if (X) r = vx;
+  if (Y) r = X ? (Y > 0 ? vadd(r, vy) : vsub(r, vy)) : vy;
+  if (Z) r = (X || Y) ? (Z > 0 ? vadd(r, vz) : vsub(r, vz)) : vz;
+  return r;
 }
 
-template <int Q, int... P>
-__device__ __forceinline__ void all_pair_moments(const float (&f)[Q], float (&m)[10],
-                                                 std::integer_sequence<int, P...>) {
-  (pair_moments<Q, 2 * P + 1>(f, m), ...);
+// Moment accumulators m[k]: k = 0 sum df, 1..3 j (without F/2), 4..6 sum c_a^2 df,
+// 7..9 sum c_x c_y df, c_x c_z df, c_y c_z df.  coef(k, i) is the factor of df_i in m[k].
+__host__ __device__ constexpr int mcoef(int k, int i) {
+  return k == 0 ? 1 : k == 1 ? cx(i) : k == 2 ? cy(i) : k == 3 ? cz(i) : k == 4 ? cx(i) * cx(i)
+       : k == 5 ? cy(i) * cy(i) : k == 6 ? cz(i) * cz(i) : k == 7 ? cx(i) * cy(i) : k == 8 ? cx(i) * cz(i)
+       : cy(i) * cz(i);
+}
+// first pair (odd I) that contributes to m[k]; the rest population opens m[0]
+__host__ __device__ constexpr int mfirst(int k) {
+  if (k == 0) return 0;
+  for (int I = 1; I < 27; I += 2)
+    if (mcoef(k, I) != 0) return I;
+  return -1;
 }
 
-// One +/- pair (I, I+1) of the TRT collision, written as f* = f + delta so that the only
-// rounding at the magnitude of f is the final addition.  The antisymmetric equilibrium
-// 3 w (c.j) is carried as an unevaluated sum hi + lo (the FMA recovers the product's
-// rounding error exactly), and the non-equilibrium parts are formed by subtracting it
-// from f first, where the operands nearly cancel.  This keeps the per-step momentum error
-// at the level of one rounding of f, which matters at the small velocities of laminar runs.
-template <int Q, int I>
-__device__ __forceinline__ void trt_pair(const KParams& p, float (&f)[Q], const CollCtx& c) {
-  constexpr int X = cx(I), Y = cy(I), Z = cz(I);
-  constexpr float w = (float)wgt_d<Q>(I);
-  constexpr float khi = (float)(3.0 * wgt_d<Q>(I));
-  constexpr float klo = (float)(3.0 * wgt_d<Q>(I) - (double)khi);
-  const float cu = X * c.ux + Y * c.uy + Z * c.uz;
-  const float cj = X * c.jx + Y * c.jy + Z * c.jz;
-  const float eh = cj * khi;
-  const float el = fmaf(cj, klo, fmaf(cj, khi, -eh));
-  const float es = w * fmaf(c.B, cu * cu, c.A);
-  const float ni = ((f[I] - eh) - el) - es;
-  const float nj = ((f[I + 1] + eh) + el) - es;
+template <int K, int I, class V>
+__device__ __forceinline__ void macc(V (&m)[10], V v, int sign) {
+  if (mfirst(K) == I) m[K] = sign > 0 ? v : vsub(vset<V>(0.f), v);
+  else m[K] = sign > 0 ? vadd(m[K], v) : vsub(m[K], v);
+}
+
+// Sums over the pair (I, I+1): s = f_I + f_I+1, d = f_P - f_R (P primary, R its opposite).
+template <int Q, int I, class V>
+__device__ __forceinline__ void pair_moments(const V (&f)[Q], V (&m)[10]) {
+  constexpr int P = prim(I), R = P == I ? I + 1 : I;
+  const V s = vadd(f[I], f[I + 1]);
+  const V d = vsub(f[P], f[R]);
+  macc<0, I>(m, s, 1);
+#pragma unroll
+  for (int k = 1; k <= 3; k++) {
+    if (mcoef(k, P) == 0) continue;
+    if (k == 1) macc<1, I>(m, d, mcoef(1, P));
+    if (k == 2) macc<2, I>(m, d, mcoef(2, P));
+    if (k == 3) macc<3, I>(m, d, mcoef(3, P));
+  }
+  if (mcoef(4, P)) macc<4, I>(m, s, 1);
+  if (mcoef(5, P)) macc<5, I>(m, s, 1);
+  if (mcoef(6, P)) macc<6, I>(m, s, 1);
+  if (mcoef(7, P)) macc<7, I>(m, s, mcoef(7, P));
+  if (mcoef(8, P)) macc<8, I>(m, s, mcoef(8, P));
+  if (mcoef(9, P)) macc<9, I>(m, s, mcoef(9, P));
+}
+
+template <int Q, class V, int... P>
+__device__ __forceinline__ void all_pair_moments(const V (&f)[Q], V (&m)[10], std::integer_sequence<int, P...>) {
+  (pair_moments<Q, 2 * P + 1, V>(f, m), ...);
+}
+
+template <class V>
+struct CollCtx {
+  V ux, uy, uz, jx, jy, jz;
+  V A, B;          // symmetric equilibrium w (A + B (c.u)^2): A = drho - 1.5 rho u^2, B = 4.5 rho
+  V nhwp, nhwm;    // -omega+/2, -omega-/2
+  V gp, gm;        // 1 - omega+/2, 1 - omega-/2
+  V gu3;           // (1 - omega+/2) 3 u.F
+};
+
+// One +/- pair of the TRT collision, written as f* = f + delta so that the only rounding at
+// the magnitude of f is the final addition.  The antisymmetric equilibrium 3 w (c.j) is
+// carried as an unevaluated sum eh + el (the FMA recovers the product's rounding error
+// exactly; eln = -el), and the non-equilibrium parts are formed by subtracting it from f
+// first, where the operands nearly cancel.  This keeps the per-step momentum error at the
+// level of one rounding of f, which matters at the small velocities of laminar runs.
+// The same pair update for half-precision storage, where the rounding of the stored value
+// (2^-11 or 2^-8 relative) dominates: the non-equilibrium parts are formed from the pair sum
+// and difference, and the antisymmetric equilibrium as 3 w rho (c.u) in one rounding.
+// kw: per-weight-class factors 2 w A, 2 w B, 6 w rho, -w gu3, indexed by |c|^2 - 1.
+template <int Q, int I, class V>
+__device__ __forceinline__ void trt_pair_lean(const KParams& p, V (&f)[Q], const CollCtx<V>& c,
+                                              const V (&kw)[3][4]) {
+  constexpr int P = prim(I), R = P == I ? I + 1 : I;
+  constexpr int X = cx(P), Y = cy(P), Z = cz(P), K = csq(P) - 1;
+  const V cu = cdot<X, Y, Z>(c.ux, c.uy, c.uz);
+  const V s = vadd(f[P], f[R]);
+  const V d = vsub(f[P], f[R]);
+  const V t1 = vsub(s, vfma(kw[K][1], vmul(cu, cu), kw[K][0]));
+  const V t2 = vsub(d, vmul(cu, kw[K][2]));
+  const V fsym = vfma(vmul(c.gp, vset<V>(p.F9w[P])), cu, kw[K][3]);
+  const V ds = vfma(c.nhwp, t1, fsym);
+  const V da = vfma(c.nhwm, t2, vmul(c.gm, vset<V>(p.F3w[P])));
+  f[P] = vadd(f[P], vadd(ds, da));
+  f[R] = vadd(f[R], vsub(ds, da));
+}
+
+template <int Q, class V, int... P>
+__device__ __forceinline__ void trt_pairs_lean(const KParams& p, V (&f)[Q], const CollCtx<V>& c,
+                                               const V (&kw)[3][4], std::integer_sequence<int, P...>) {
+  (trt_pair_lean<Q, 2 * P + 1, V>(p, f, c, kw), ...);
+}
+
+template <int Q, int I, class V>
+__device__ __forceinline__ void trt_pair(const KParams& p, V (&f)[Q], const CollCtx<V>& c) {
+  constexpr int P = prim(I), R = P == I ? I + 1 : I;
+  constexpr int X = cx(P), Y = cy(P), Z = cz(P);
+  constexpr float w = (float)wgt_d<Q>(P);
+  constexpr float khi = (float)(3.0 * wgt_d<Q>(P));
+  constexpr float klo = (float)(3.0 * wgt_d<Q>(P) - (double)khi);
+  const V cu = cdot<X, Y, Z>(c.ux, c.uy, c.uz);
+  const V cj = cdot<X, Y, Z>(c.jx, c.jy, c.jz);
+  const V eh = vmul(cj, vset<V>(khi));
+  const V eln = vfma(cj, vset<V>(-klo), vfma(cj, vset<V>(-khi), eh));
+  const V es = vmul(vset<V>(w), vfma(c.B, vmul(cu, cu), c.A));
+  const V ni = vsub(vadd(vsub(f[P], eh), eln), es);
+  const V nj = vsub(vsub(vadd(f[R], eh), eln), es);
   // Guo terms: symmetric w (9 (c.u)(c.F) - 3 u.F), antisymmetric 3 w (c.F)
-  const float fsym = fmaf(c.gp * p.F9w[I], cu, -w * c.gu3);
-  const float ds = fmaf(-c.hwp, ni + nj, fsym);
-  const float da = fmaf(-c.hwm, ni - nj, c.gm * p.F3w[I]);
-  f[I] = f[I] + (ds + da);
-  f[I + 1] = f[I + 1] + (ds - da);
+  const V fsym = vfma(vmul(c.gp, vset<V>(p.F9w[P])), cu, vmul(c.gu3, vset<V>(-w)));
+  const V ds = vfma(c.nhwp, vadd(ni, nj), fsym);
+  const V da = vfma(c.nhwm, vsub(ni, nj), vmul(c.gm, vset<V>(p.F3w[P])));
+  f[P] = vadd(f[P], vadd(ds, da));
+  f[R] = vadd(f[R], vsub(ds, da));
 }
 
-template <int Q, int... P>
-__device__ __forceinline__ void trt_pairs(const KParams& p, float (&f)[Q], const CollCtx& c,
+template <int Q, class V, int... P>
+__device__ __forceinline__ void trt_pairs(const KParams& p, V (&f)[Q], const CollCtx<V>& c,
                                           std::integer_sequence<int, P...>) {
-  (trt_pair<Q, 2 * P + 1>(p, f, c), ...);
+  (trt_pair<Q, 2 * P + 1, V>(p, f, c), ...);
 }
 
 // sqrt of a non-negative value from the hardware reciprocal square root (x = 0 gives 0).
-__device__ __forceinline__ float fast_sqrt(float x) { return x * rsqrtf(fmaxf(x, 1e-37f)); }
+__device__ __forceinline__ float fast_sqrt(float x) { return __fmul_rn(x, rsqrtf(fmaxf(x, 1e-37f))); }
 
-template <int Q, int CL>
-__device__ __forceinline__ float collide(const KParams& p, float (&f)[Q]) {
+// Relaxation rates of one cell from its stress invariant Q = Pi:Pi: tau_eff solves
+// tau = tau0 + 3 C_s^2 |S|(tau) in closed form, omega- keeps the magic parameter Lambda.
+__device__ __forceinline__ void les_rates(const KParams& p, float qn, float inv, float cs2, float& wp, float& wm) {
+  const float t = __fmul_rn(__fmul_rn(25.455844122715711f, cs2), __fmul_rn(fast_sqrt(qn), inv));
+  const float tau = __fmul_rn(0.5f, __fadd_rn(p.tau0, fast_sqrt(__fmaf_rn(p.tau0, p.tau0, t))));
+  wp = __fdividef(1.f, tau);
+  wm = __fdividef(1.f, __fadd_rn(__fdividef(p.lambda, __fsub_rn(tau, 0.5f)), 0.5f));
+}
+
+// ACC: the accurate pair update (float32 storage) or the lean one (half storage).
+template <class S>
+constexpr bool acc_form = std::is_same<S, float>::value;
+
+template <int Q, int CL, class V, bool ACC = true>
+__device__ __forceinline__ V collide(const KParams& p, V (&f)[Q]) {
   using Pairs = std::make_integer_sequence<int, (Q - 1) / 2>;
-  // m: sum s, j_x, j_y, j_z (without F/2), sum c_x^2 f, c_y^2 f, c_z^2 f, c_xc_y f, c_xc_z f, c_yc_z f
-  float m[10] = {f[0], 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  all_pair_moments<Q>(f, m, Pairs{});
-  const float drho = m[0];
-  const float rho = 1.f + drho;
-  const float jx = m[1] + 0.5f * p.F[0], jy = m[2] + 0.5f * p.F[1], jz = m[3] + 0.5f * p.F[2];
-  const float inv = __fdividef(1.f, rho);
-  const float ux = jx * inv, uy = jy * inv, uz = jz * inv;
-  float wp = p.omega_p, wm = p.omega_m;
+  using L = Lanes<V>;
+  V m[10];
+  m[0] = f[0];
+  all_pair_moments<Q, V>(f, m, Pairs{});
+  const V drho = m[0];
+  const V rho = vadd(drho, vset<V>(1.f));
+  const V jx = vadd(m[1], vset<V>(0.5f * p.F[0]));
+  const V jy = vadd(m[2], vset<V>(0.5f * p.F[1]));
+  const V jz = vadd(m[3], vset<V>(0.5f * p.F[2]));
+  V inv;
+#pragma unroll
+  for (int k = 0; k < L::n; k++) L::put(inv, k, __fdividef(1.f, L::get(rho, k)));
+  const V ux = vmul(jx, inv), uy = vmul(jy, inv), uz = vmul(jz, inv);
+  V wp = vset<V>(p.omega_p), wm = vset<V>(p.omega_m);
   if (CL != CL_NONE) {
     // Pi^neq = sum_i c c df_i - (drho/3) I - j u   (shifted form of sum c c (f - feq))
-    const float d3 = drho * (1.f / 3.f);
-    float pi[6];
-    pi[0] = m[4] - d3 - jx * ux;
-    pi[1] = m[5] - d3 - jy * uy;
-    pi[2] = m[6] - d3 - jz * uz;
-    pi[3] = m[7] - jx * uy;
-    pi[4] = m[8] - jx * uz;
-    pi[5] = m[9] - jy * uz;
-    const float qn = pi[0] * pi[0] + pi[1] * pi[1] + pi[2] * pi[2] +
-                     2.f * (pi[3] * pi[3] + pi[4] * pi[4] + pi[5] * pi[5]);
-    float cs2 = p.cs2;
-    if (CL == CL_MLP) cs2 = fmaxf(mlp_cs2(p, pi, drho), p.cs2_min);
-    const float tau = 0.5f * (p.tau0 + fast_sqrt(p.tau0 * p.tau0 + 25.455844122715711f * cs2 * fast_sqrt(qn) * inv));
-    wp = __fdividef(1.f, tau);
-    wm = __fdividef(1.f, __fdividef(p.lambda, tau - 0.5f) + 0.5f);
+    const V d3 = vmul(drho, vset<V>(1.f / 3.f));
+    V pi[6];
+    pi[0] = vsub(vsub(m[4], d3), vmul(jx, ux));
+    pi[1] = vsub(vsub(m[5], d3), vmul(jy, uy));
+    pi[2] = vsub(vsub(m[6], d3), vmul(jz, uz));
+    pi[3] = vsub(m[7], vmul(jx, uy));
+    pi[4] = vsub(m[8], vmul(jx, uz));
+    pi[5] = vsub(m[9], vmul(jy, uz));
+    V qn = vfma(pi[5], pi[5], vfma(pi[4], pi[4], vmul(pi[3], pi[3])));
+    qn = vfma(pi[2], pi[2], vfma(pi[1], pi[1], vfma(pi[0], pi[0], vadd(qn, qn))));
+#pragma unroll
+    for (int k = 0; k < L::n; k++) {
+      float cs2 = p.cs2;
+      if constexpr (CL == CL_MLP) {
+        static_assert(L::n == 1, "the learned closure runs one cell per thread");
+        cs2 = fmaxf(mlp_cs2(p, pi, drho), p.cs2_min);
+      }
+      float a, b;
+      les_rates(p, L::get(qn, k), L::get(inv, k), cs2, a, b);
+      L::put(wp, k, a);
+      L::put(wm, k, b);
+    }
   }
-  CollCtx c;
+  CollCtx<V> c;
   c.ux = ux;
   c.uy = uy;
   c.uz = uz;
   c.jx = jx;
   c.jy = jy;
   c.jz = jz;
-  const float usq = ux * ux + uy * uy + uz * uz;
-  const float uF = ux * p.F[0] + uy * p.F[1] + uz * p.F[2];
-  c.A = drho - 1.5f * rho * usq;
-  c.B = 4.5f * rho;
-  c.hwp = 0.5f * wp;
-  c.hwm = 0.5f * wm;
-  c.gp = 1.f - c.hwp;
-  c.gm = 1.f - c.hwm;
-  c.gu3 = c.gp * 3.f * uF;
+  const V usq = vfma(uz, uz, vfma(uy, uy, vmul(ux, ux)));
+  const V uF = vfma(uz, vset<V>(p.F[2]), vfma(uy, vset<V>(p.F[1]), vmul(ux, vset<V>(p.F[0]))));
+  c.A = vfma(vmul(rho, vset<V>(-1.5f)), usq, drho);
+  c.B = vmul(rho, vset<V>(4.5f));
+  c.nhwp = vmul(wp, vset<V>(-0.5f));
+  c.nhwm = vmul(wm, vset<V>(-0.5f));
+  c.gp = vadd(c.nhwp, vset<V>(1.f));
+  c.gm = vadd(c.nhwm, vset<V>(1.f));
+  c.gu3 = vmul(c.gp, vmul(uF, vset<V>(3.f)));
   {
     constexpr float w0 = (float)wgt_d<Q>(0);
-    const float n0 = f[0] - w0 * c.A;
-    f[0] = f[0] + (-wp * n0 - w0 * c.gu3);
+    const V n0 = vfma(c.A, vset<V>(-w0), f[0]);
+    f[0] = vadd(f[0], vfma(vadd(c.nhwp, c.nhwp), n0, vmul(c.gu3, vset<V>(-w0))));
   }
-  trt_pairs<Q>(p, f, c, Pairs{});
+  if constexpr (ACC) {
+    trt_pairs<Q, V>(p, f, c, Pairs{});
+  } else {
+    V kw[3][4];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      const float w = (float)(k == 0 ? wgt_d<Q>(1) : k == 1 ? wgt_d<Q>(7) : wgt_d<Q>(19 % Q));
+      kw[k][0] = vmul(c.A, vset<V>(2.f * w));
+      kw[k][1] = vmul(c.B, vset<V>(2.f * w));
+      kw[k][2] = vmul(rho, vset<V>(6.f * w));
+      kw[k][3] = vmul(c.gu3, vset<V>(-w));
+    }
+    trt_pairs_lean<Q, V>(p, f, c, kw, Pairs{});
+  }
   return rho;
 }
 
@@ -511,9 +712,51 @@ __global__ void __launch_bounds__(128, CL == CL_MLP ? 4 : 8) k_step(const __grid
   load_state<Q, S, LOAD>(p, x, y, z, cell, cls, f, outmask);
   outflow_fix<Q>(p, x, f, outmask);
   if (cls == CLS_SKIP) return;
-  const float rho = collide<Q, CL>(p, f);
+  const float rho = collide<Q, CL, float, acc_form<S>>(p, f);
   if (!(rho > 0.f && rho < 3.0e38f)) atomicOr(p.status, 1);
   store_state<Q, S, STORE>(p, x, y, z, cell, cls, f);
+}
+
+// The step for two cells per thread, (x, y) and (x, y + 1): their loads and stores are the
+// one-cell kernel's, and the collision runs on float2 pairs in the packed FP32x2 pipe
+// (half the arithmetic instructions of two one-cell threads, twice the loads in flight per
+// thread).  Block (32, 4) covers 32 x 8 cells; grid (nxp/32, ceil(ny/8), nz).  The learned
+// closure keeps the one-cell kernel.
+#ifndef LBM_PAIR_MINB
+#define LBM_PAIR_MINB 4
+#endif
+template <int Q, class S, int CL, int LOAD, int STORE>
+__global__ void __launch_bounds__(128, LBM_PAIR_MINB) k_step2(const __grid_constant__ KParams p) {
+  static_assert(CL != CL_MLP, "the learned closure runs one cell per thread");
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = (blockIdx.y * blockDim.y + threadIdx.y) * 2;
+  const int z = blockIdx.z;
+  if (y >= p.ny) return;  // whole warp
+  const int cell0 = cidx(p, x, y, z);
+  const int cell1 = cell0 + p.nxp;
+  const int cls0 = x < p.nx ? p.cls[cell0] : CLS_SKIP;
+  const int cls1 = (x < p.nx && y + 1 < p.ny) ? p.cls[cell1] : CLS_SKIP;
+  float fa[Q], fb[Q];
+  unsigned oa, ob;
+  load_state<Q, S, LOAD>(p, x, y, z, cell0, cls0, fa, oa);
+  load_state<Q, S, LOAD>(p, x, y + 1, z, cell1, cls1, fb, ob);
+  outflow_fix<Q>(p, x, fa, oa);
+  outflow_fix<Q>(p, x, fb, ob);
+  if (cls0 == CLS_SKIP && cls1 == CLS_SKIP) return;
+  float2 f[Q];
+#pragma unroll
+  for (int i = 0; i < Q; i++) f[i] = make_float2(fa[i], fb[i]);
+  const float2 rho = collide<Q, CL, float2, acc_form<S>>(p, f);
+  const bool bad0 = cls0 != CLS_SKIP && !(rho.x > 0.f && rho.x < 3.0e38f);
+  const bool bad1 = cls1 != CLS_SKIP && !(rho.y > 0.f && rho.y < 3.0e38f);
+  if (bad0 || bad1) atomicOr(p.status, 1);
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    fa[i] = f[i].x;
+    fb[i] = f[i].y;
+  }
+  if (cls0 != CLS_SKIP) store_state<Q, S, STORE>(p, x, y, z, cell0, cls0, fa);
+  if (cls1 != CLS_SKIP) store_state<Q, S, STORE>(p, x, y + 1, z, cell1, cls1, fb);
 }
 
 // The same step with register double-buffering along z: each thread updates ZC cells
@@ -543,7 +786,7 @@ __global__ void __launch_bounds__(128, CL == CL_MLP ? 4 : 5) k_step_zp(const __g
     }
     outflow_fix<Q>(p, x, f, outmask);
     if (cls != CLS_SKIP) {
-      const float rho = collide<Q, CL>(p, f);
+      const float rho = collide<Q, CL, float, acc_form<S>>(p, f);
       if (!(rho > 0.f && rho < 3.0e38f)) atomicOr(p.status, 1);
       store_state<Q, S, PAR>(p, x, y, z, cell, cls, f);
     }

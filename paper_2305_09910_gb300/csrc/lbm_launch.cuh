@@ -4,6 +4,8 @@
 
 #include "lbm_kernels.cuh"
 #include "lbm_tma.cuh"
+#include "lbm_async.cuh"
+#include "lbm_h2.cuh"
 
 namespace lbm {
 
@@ -17,6 +19,8 @@ cudaError_t launch_step(const KParams& p, int closure, int parity, const Launch&
 template <int Q, class S>
 cudaError_t launch_step_tma(const KParams& p, int closure, int parity, cudaStream_t stream, int nsm);
 template <int Q, class S>
+cudaError_t launch_step_async(const KParams& p, int closure, int mode, const Launch& L);
+template <int Q, class S>
 cudaError_t launch_step_zp(const KParams& p, int closure, int parity, const Launch& L);
 template <int Q, class S>
 cudaError_t launch_export(const KParams& p, int parity, int mode, const ExportArgs& a, const Launch& L);
@@ -29,6 +33,7 @@ cudaError_t launch_set_pop(const KParams& p, const float* df, const Launch& L);
   extern template cudaError_t launch_step<Q, S>(const KParams&, int, int, const Launch&);          \
   extern template cudaError_t launch_step_tma<Q, S>(const KParams&, int, int, cudaStream_t, int);  \
   extern template cudaError_t launch_step_zp<Q, S>(const KParams&, int, int, const Launch&);       \
+  extern template cudaError_t launch_step_async<Q, S>(const KParams&, int, int, const Launch&);    \
   extern template cudaError_t launch_export<Q, S>(const KParams&, int, int, const ExportArgs&,     \
                                                   const Launch&);                                  \
   extern template cudaError_t launch_init_eq<Q, S>(const KParams&, const float*, const float*,     \

@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(TMA_TX, CL == CL_MLP ? 4 : 5) k_step_tma(const
     }
     outflow_fix<Q>(p, x, f, outmask);
     if (cls == CLS_SKIP) continue;
-    const float rho = collide<Q, CL>(p, f);
+    const float rho = collide<Q, CL, float, acc_form<S>>(p, f);
     if (!(rho > 0.f && rho < 3.0e38f)) atomicOr(p.status, 1);
     store_state<Q, S, PAR>(p, x, y, z, cell, cls, f);
   }

@@ -25,7 +25,7 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ESTATE, LBM_EUNSUP
     0, -1, -2, -3, -4, -5, -6
 PRECISION = {"f32": 0, "f16": 1, "bf16": 2}
 STREAMING = {"aa": 0, "pull": 1}
-PIPELINE = {"tma": 0, "direct": 1, "prefetch": 2}
+PIPELINE = {"tma": 0, "direct": 1, "prefetch": 2, "async": 3}
 CLOSURE = {"none": 0, "smag": 1, "mlp": 2}
 FACE = {"periodic": 0, "wall": 1, "freeslip": 2, "inflow": 3, "outflow": 4}
 CELL = {"fluid": 0, "solid": 1, "inflow": 2}

@@ -14,12 +14,13 @@ FACES_TUNNEL = ("inflow", "outflow", "freeslip", "freeslip", "freeslip", "freesl
 
 def make_pair(nx, ny, nz, q=19, tau=0.8, lam=3.0 / 16.0, closure="none", cs=0.1,
               faces=("periodic",) * 6, u_w=(0.0, 0.0, 0.0), rho_w=1.0, force=(0.0, 0.0, 0.0),
-              flags=None, precision="f32", mlp=None, mlp_scale=(1.0, 1.0)):
+              flags=None, precision="f32", mlp=None, mlp_scale=(1.0, 1.0), pipeline="direct"):
     import oracle
     from paper_2305_09910_gb300 import lbm
 
     lat = lbm.Lattice(nx, ny, nz, stencil=q, tau=tau, precision=precision, closure=closure,
-                      magic_lambda=lam, cs_smag=cs, faces=faces, u_inflow=u_w, rho_inflow=rho_w)
+                      magic_lambda=lam, cs_smag=cs, faces=faces, u_inflow=u_w, rho_inflow=rho_w,
+                      pipeline=pipeline)
     if flags is not None:
         lat.set_flags(np.ascontiguousarray(flags, dtype=np.uint8))
     lat.set_force(*force)

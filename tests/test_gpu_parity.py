@@ -358,20 +358,23 @@ def test_instability_is_reported_not_trapped():
     lat.sync()
 
 
+@pytest.mark.parametrize("pipeline", ["tma", "prefetch", "async"])
 @pytest.mark.parametrize("name", ["channel19", "tunnel27", "mixed19", "periodic27"])
 @pytest.mark.parametrize("precision", ["f32", "f16"])
-def test_tma_and_direct_pipelines_agree_bit_for_bit(name, precision):
-    """The shared-memory-staged (TMA) step and the direct-load step compute the same update."""
+def test_staged_and_direct_pipelines_agree_bit_for_bit(name, precision, pipeline):
+    """The staged steps (TMA bulk copies, register prefetch, cp.async) and the direct-load
+    step compute the same update."""
     from paper_2305_09910_gb300 import lbm
 
     case = dict(CASES[name])
     flags = case.pop("flags", None)
-    a, ora = make_pair(precision=precision, flags=flags, **case)
+    a, ora = make_pair(precision=precision, flags=flags, pipeline=pipeline, **case)
     kw = {k: case[k] for k in ("q", "tau", "closure") if k in case}
     b = lbm.Lattice(case["nx"], case["ny"], case["nz"], stencil=kw.get("q", 19), tau=kw.get("tau", 0.8),
                     precision=precision, closure=kw.get("closure", "none"), cs_smag=case.get("cs", 0.1),
                     faces=case.get("faces", ("periodic",) * 6), u_inflow=case.get("u_w", (0, 0, 0)),
                     pipeline="direct")
+    assert a.params.pipeline == lbm.PIPELINE[pipeline] and b.params.pipeline == lbm.PIPELINE["direct"]
     if flags is not None:
         b.set_flags(flags)
     b.set_force(*case.get("force", (0.0, 0.0, 0.0)))
@@ -383,19 +386,46 @@ def test_tma_and_direct_pipelines_agree_bit_for_bit(name, precision):
         assert np.array_equal(a.get_populations(), b.get_populations())
 
 
-def test_tma_pipeline_large_periodic_seams():
-    """Several tiles per row, a ragged last tile, periodic seams in x, y and z."""
+@pytest.mark.parametrize("pipeline", ["tma", "prefetch", "async"])
+@pytest.mark.parametrize("faces", ["periodic", "channel"])
+@pytest.mark.parametrize("precision,nx", [("f32", 300), ("f16", 300), ("bf16", 301)])
+def test_staged_pipelines_large_seams(pipeline, faces, precision, nx):
+    """Several tiles per row, a ragged last tile and z block, seams in x, y and z.  For half
+    storage the direct step updates x-pairs (a ragged last pair when nx is odd) and the staged
+    ones single cells."""
     from paper_2305_09910_gb300 import inputs, lbm
 
-    nx, ny, nz = 300, 7, 5
-    a = lbm.Lattice(nx, ny, nz, tau=0.6, closure="smag", pipeline="tma")
-    b = lbm.Lattice(nx, ny, nz, tau=0.6, closure="smag", pipeline="direct")
+    ny, nz = 7, 21
+    fc = ("periodic",) * 6 if faces == "periodic" else FACES_CHANNEL
+    a = lbm.Lattice(nx, ny, nz, tau=0.6, closure="smag", faces=fc, pipeline=pipeline, precision=precision)
+    b = lbm.Lattice(nx, ny, nz, tau=0.6, closure="smag", faces=fc, pipeline="direct", precision=precision)
     rho, u = inputs.channel_init(nx, ny, nz, seed=6)
     for lat in (a, b):
         lat.set_force(1e-5, 2e-6, 0)
         lat.init_equilibrium(rho, u)
         lat.step(7)
     assert np.array_equal(a.get_populations(), b.get_populations())
+
+
+@pytest.mark.parametrize("precision", ["f32", "f16"])
+def test_async_pull_matches_direct_pull(precision):
+    from paper_2305_09910_gb300 import lbm
+
+    case = dict(CASES["tunnel19"])
+    flags = case.pop("flags")
+    common = dict(stencil=19, tau=case["tau"], closure="smag", cs_smag=case["cs"], faces=case["faces"],
+                  u_inflow=case["u_w"], precision=precision, streaming="pull")
+    a = lbm.Lattice(case["nx"], case["ny"], case["nz"], pipeline="async", **common)
+    b = lbm.Lattice(case["nx"], case["ny"], case["nz"], pipeline="direct", **common)
+    _, ora = make_pair(flags=flags, **case)
+    for lat in (a, b):
+        lat.set_flags(flags)
+    df = _start(a, ora, dict(CASES["tunnel19"]), seed=23)
+    b.set_populations(df)
+    for n in (1, 2, 3):
+        a.step(n)
+        b.step(n)
+        assert np.array_equal(a.get_populations(), b.get_populations())
 
 
 @pytest.mark.parametrize("name", ["channel19", "tunnel27", "mixed19", "periodic27"])
