@@ -17,26 +17,14 @@ namespace lbm {
 template <int Q, class S, int LOAD, int STORE>
 static void step_mode(const KParams& p, int closure, const Launch& L) {
   if constexpr (sizeof(S) == 2 && Q == 19) {  // half storage: x-pairs, 64 x per warp (D3Q19)
-    if (closure != CL_MLP) {
-      dim3 g = L.grid;
-      g.x = (p.nxp + 63) / 64;
-      if (closure == CL_NONE) k_step_h2<Q, S, CL_NONE, LOAD, STORE><<<g, L.block, 0, L.stream>>>(p);
-      else k_step_h2<Q, S, CL_SMAG, LOAD, STORE><<<g, L.block, 0, L.stream>>>(p);
-      return;
-    }
+    dim3 g = L.grid;
+    g.x = (p.nxp + 63) / 64;
+    if (closure == CL_NONE) k_step_h2<Q, S, CL_NONE, LOAD, STORE><<<g, L.block, 0, L.stream>>>(p);
+    else k_step_h2<Q, S, CL_SMAG, LOAD, STORE><<<g, L.block, 0, L.stream>>>(p);
+    return;
   }
-#ifndef LBM_PAIR
   if (closure == CL_NONE) k_step<Q, S, CL_NONE, LOAD, STORE><<<L.grid, L.block, 0, L.stream>>>(p);
-  else if (closure == CL_SMAG) k_step<Q, S, CL_SMAG, LOAD, STORE><<<L.grid, L.block, 0, L.stream>>>(p);
-  else k_step<Q, S, CL_MLP, LOAD, STORE><<<L.grid, L.block, 0, L.stream>>>(p);
-  return;
-#endif
-  // two cells (y, y + 1) per thread without the learned closure: half the grid rows
-  dim3 g2 = L.grid;
-  g2.y = (p.ny + 2 * L.block.y - 1) / (2 * L.block.y);
-  if (closure == CL_NONE) k_step2<Q, S, CL_NONE, LOAD, STORE><<<g2, L.block, 0, L.stream>>>(p);
-  else if (closure == CL_SMAG) k_step2<Q, S, CL_SMAG, LOAD, STORE><<<g2, L.block, 0, L.stream>>>(p);
-  else k_step<Q, S, CL_MLP, LOAD, STORE><<<L.grid, L.block, 0, L.stream>>>(p);
+  else k_step<Q, S, CL_SMAG, LOAD, STORE><<<L.grid, L.block, 0, L.stream>>>(p);
 }
 
 // mode: 0 AA even, 1 AA odd, 2 first pull step after an import, 3 pull step
@@ -72,8 +60,7 @@ static cudaError_t async_one(const KParams& p, const Launch& L0) {
 template <int Q, int LOAD, int STORE>
 static cudaError_t async_mode(const KParams& p, int closure, const Launch& L) {
   if (closure == CL_NONE) return async_one<Q, CL_NONE, LOAD, STORE>(p, L);
-  if (closure == CL_SMAG) return async_one<Q, CL_SMAG, LOAD, STORE>(p, L);
-  return async_one<Q, CL_MLP, LOAD, STORE>(p, L);
+  return async_one<Q, CL_SMAG, LOAD, STORE>(p, L);
 }
 
 // Staged (cp.async) step; FP32 storage only, the half forms take the direct kernels.
@@ -98,14 +85,42 @@ cudaError_t launch_step_zp(const KParams& p, int closure, int parity, const Laun
   L.grid.z = (p.nz + ZC - 1) / ZC;
   if (parity == 0) {
     if (closure == CL_NONE) k_step_zp<Q, S, CL_NONE, 0, ZC><<<L.grid, L.block, 0, L.stream>>>(p);
-    else if (closure == CL_SMAG) k_step_zp<Q, S, CL_SMAG, 0, ZC><<<L.grid, L.block, 0, L.stream>>>(p);
-    else k_step_zp<Q, S, CL_MLP, 0, ZC><<<L.grid, L.block, 0, L.stream>>>(p);
+    else k_step_zp<Q, S, CL_SMAG, 0, ZC><<<L.grid, L.block, 0, L.stream>>>(p);
   } else {
     if (closure == CL_NONE) k_step_zp<Q, S, CL_NONE, 1, ZC><<<L.grid, L.block, 0, L.stream>>>(p);
-    else if (closure == CL_SMAG) k_step_zp<Q, S, CL_SMAG, 1, ZC><<<L.grid, L.block, 0, L.stream>>>(p);
-    else k_step_zp<Q, S, CL_MLP, 1, ZC><<<L.grid, L.block, 0, L.stream>>>(p);
+    else k_step_zp<Q, S, CL_SMAG, 1, ZC><<<L.grid, L.block, 0, L.stream>>>(p);
   }
   return cudaGetLastError();
+}
+
+template <int Q, class S, int LOAD, int STORE>
+static cudaError_t mlp_one(const KParams& p, cudaStream_t stream, int nsm) {
+  constexpr int smem = (int)sizeof(MlpSmem);
+  auto kern = k_step_mlp<Q, S, LOAD, STORE>;
+  static int blocks_per_sm = 0;  // per instantiation, found once (one: the kernel allocates TMEM)
+  if (blocks_per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, 128 * MLP_NG, smem);
+    if (e != cudaSuccess) return e;
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+  }
+  const long long ntiles = (long long)(p.nxp / 32) * ((p.ny + 3) / 4) * p.nz;
+  const long long groups = (ntiles + MLP_NG - 1) / MLP_NG;
+  const long long grid = std::min<long long>(groups, (long long)nsm * blocks_per_sm);
+  kern<<<(unsigned)grid, dim3(32, 4 * MLP_NG, 1), smem, stream>>>(p, ntiles);
+  return cudaGetLastError();
+}
+
+// The step with the learned closure (tensor-core hidden layer); mode as in launch_step.
+template <int Q, class S>
+cudaError_t launch_step_mlp(const KParams& p, int mode, cudaStream_t stream, int nsm) {
+  switch (mode) {
+    case 0: return mlp_one<Q, S, 0, 0>(p, stream, nsm);
+    case 1: return mlp_one<Q, S, 1, 1>(p, stream, nsm);
+    case 2: return mlp_one<Q, S, 0, 2>(p, stream, nsm);
+    default: return mlp_one<Q, S, 2, 2>(p, stream, nsm);
+  }
 }
 
 template <int Q, class S, int CL, int PAR>
@@ -131,12 +146,10 @@ template <int Q, class S>
 cudaError_t launch_step_tma(const KParams& p, int closure, int parity, cudaStream_t stream, int nsm) {
   if (parity == 0) {
     if (closure == CL_NONE) return tma_one<Q, S, CL_NONE, 0>(p, stream, nsm);
-    if (closure == CL_SMAG) return tma_one<Q, S, CL_SMAG, 0>(p, stream, nsm);
-    return tma_one<Q, S, CL_MLP, 0>(p, stream, nsm);
+    return tma_one<Q, S, CL_SMAG, 0>(p, stream, nsm);
   }
   if (closure == CL_NONE) return tma_one<Q, S, CL_NONE, 1>(p, stream, nsm);
-  if (closure == CL_SMAG) return tma_one<Q, S, CL_SMAG, 1>(p, stream, nsm);
-  return tma_one<Q, S, CL_MLP, 1>(p, stream, nsm);
+  return tma_one<Q, S, CL_SMAG, 1>(p, stream, nsm);
 }
 
 template <int Q, class S, int PAR>
@@ -176,6 +189,7 @@ template cudaError_t launch_step<LBM_Q, LBM_S>(const KParams&, int, int, const L
 template cudaError_t launch_step_tma<LBM_Q, LBM_S>(const KParams&, int, int, cudaStream_t, int);
 template cudaError_t launch_step_zp<LBM_Q, LBM_S>(const KParams&, int, int, const Launch&);
 template cudaError_t launch_step_async<LBM_Q, LBM_S>(const KParams&, int, int, const Launch&);
+template cudaError_t launch_step_mlp<LBM_Q, LBM_S>(const KParams&, int, cudaStream_t, int);
 template cudaError_t launch_export<LBM_Q, LBM_S>(const KParams&, int, int, const ExportArgs&, const Launch&);
 template cudaError_t launch_init_eq<LBM_Q, LBM_S>(const KParams&, const float*, const float*, const Launch&);
 template cudaError_t launch_set_pop<LBM_Q, LBM_S>(const KParams&, const float*, const Launch&);

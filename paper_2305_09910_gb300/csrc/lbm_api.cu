@@ -144,6 +144,14 @@ static KParams kparams(const lbm_s* h) {
 template <int Q>
 static cudaError_t dispatch_step(const lbm_s* h, const KParams& p, int closure, int parity) {
   const Launch L = launch_cfg(h);
+  if (closure == CL_MLP) {  // one kernel for every pipeline: the tensor-core closure step
+    const int mode = h->prm.streaming == LBM_PULL ? (parity == 0 ? 2 : 3) : parity;
+    switch (h->prm.precision) {
+      case LBM_F32: return launch_step_mlp<Q, float>(p, mode, h->stream, h->nsm);
+      case LBM_F16_SHIFTED: return launch_step_mlp<Q, __half>(p, mode, h->stream, h->nsm);
+      default: return launch_step_mlp<Q, __nv_bfloat16>(p, mode, h->stream, h->nsm);
+    }
+  }
   if (h->prm.streaming == LBM_PULL) {  // direct or staged loads
     const int mode = parity == 0 ? 2 : 3;
     if (h->prm.pipeline == LBM_PIPE_ASYNC) {

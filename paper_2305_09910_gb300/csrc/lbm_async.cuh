@@ -66,7 +66,7 @@ __device__ __forceinline__ void stage_cell(const KParams& p, int x, int y, int z
 // LOAD / STORE modes as in k_step.  Block (32, 4); grid (nxp/32, ceil(ny/4), ceil(nz/ZC)).
 // FP32 storage only (the copies are 4 bytes, one population each).
 template <int Q, int CL, int LOAD, int STORE, int ZC, int NST>
-__global__ void __launch_bounds__(128, CL == CL_MLP ? 4 : LBM_ASYNC_MINB) k_step_async(const __grid_constant__ KParams p) {
+__global__ void __launch_bounds__(128, LBM_ASYNC_MINB) k_step_async(const __grid_constant__ KParams p) {
   extern __shared__ __align__(16) float sbuf[];  // [NST][Q][128]
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;

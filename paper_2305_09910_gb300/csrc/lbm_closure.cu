@@ -175,10 +175,6 @@ __global__ void __launch_bounds__(128) k_filter2(const __grid_constant__ KParams
 // ---- network -------------------------------------------------------------------------------
 constexpr int TB = 128;  // samples per block in the training kernels
 
-__device__ __forceinline__ float gelu_grad_f(float a) {
-  return 0.5f * (1.f + erff(a * 0.70710678118654752f)) + a * 0.39894228040143268f * expf(-0.5f * a * a);
-}
-
 __device__ __forceinline__ float mlp_forward_one(const float* W, const float* x, float* h1, float* g1,
                                                  float* h2, float* g2) {
   const float* W1 = W;

@@ -360,40 +360,28 @@ __device__ __forceinline__ void store_state(const KParams& p, int x, int y, int 
   }
 }
 
-// ---- closure network (per cell): C_s^2 from the non-equilibrium stress ------------------
-__device__ __forceinline__ float gelu_erf(float a) { return 0.5f * a * (1.f + erff(a * 0.70710678118654752f)); }
-
-__device__ __forceinline__ float softplus_f(float y) { return fmaxf(y, 0.f) + log1pf(expf(-fabsf(y))); }
-
-__device__ __forceinline__ float mlp_cs2(const KParams& p, const float (&pi)[6], float drho) {
-  const float* W1 = p.mlp;
-  const float* b1 = W1 + MLP_NH * MLP_NIN;
-  const float* W2 = b1 + MLP_NH;
-  const float* b2 = W2 + MLP_NH * MLP_NH;
-  const float* W3 = b2 + MLP_NH;
-  const float* b3 = W3 + MLP_NH;
-  float xin[MLP_NIN];
-#pragma unroll
-  for (int k = 0; k < 6; k++) xin[k] = fminf(fmaxf(p.mlp_scale[0] * pi[k], -MLP_XCLAMP), MLP_XCLAMP);
-  xin[6] = fminf(fmaxf(p.mlp_scale[1] * drho, -MLP_XCLAMP), MLP_XCLAMP);
-  float h1[MLP_NH];
-#pragma unroll
-  for (int j = 0; j < MLP_NH; j++) {
-    float s = __ldg(b1 + j);
-#pragma unroll
-    for (int k = 0; k < MLP_NIN; k++) s = fmaf(__ldg(W1 + j * MLP_NIN + k), xin[k], s);
-    h1[j] = gelu_erf(s);
-  }
-  float y = __ldg(b3);
-#pragma unroll 4
-  for (int j = 0; j < MLP_NH; j++) {
-    float s = __ldg(b2 + j);
-#pragma unroll
-    for (int k = 0; k < MLP_NH; k++) s = fmaf(__ldg(W2 + j * MLP_NH + k), h1[k], s);
-    y = fmaf(__ldg(W3 + j), gelu_erf(s), y);
-  }
-  return softplus_f(y) * p.cs2 * 1.4426950408889634f;  // / ln 2
+// ---- closure network: activation functions ------------------------------------------------
+// erf by the rational approximation of Abramowitz & Stegun, formula 7.1.26 (after Hastings):
+// erf(z) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-z^2), t = 1 / (1 + p z) for
+// z >= 0, erf(-z) = -erf(z); absolute error below 1.5e-7, about one float32 ulp of erf near 1.
+__device__ __forceinline__ float erf_as(float z) {
+  const float a = fabsf(z);
+  const float t = __fdividef(1.f, fmaf(0.3275911f, a, 1.f));
+  float q = fmaf(1.061405429f, t, -1.453152027f);
+  q = fmaf(q, t, 1.421413741f);
+  q = fmaf(q, t, -0.284496736f);
+  q = fmaf(q, t, 0.254829592f);
+  const float r = fmaf(-q * t, __expf(-a * a), 1.f);
+  return copysignf(r, z);
 }
+
+// GELU in its erf form, x Phi(x) = x (1 + erf(x / sqrt 2)) / 2, and its derivative.
+__device__ __forceinline__ float gelu_erf(float a) { return 0.5f * a * (1.f + erf_as(a * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad_f(float a) {
+  return 0.5f * (1.f + erf_as(a * 0.70710678118654752f)) + a * 0.39894228040143268f * __expf(-0.5f * a * a);
+}
+
+__device__ __forceinline__ float softplus_f(float y) { return fmaxf(y, 0.f) + log1pf(__expf(-fabsf(y))); }
 
 // ---- moments and TRT collision (in place on shifted populations) -----------------------
 template <int Q>
@@ -433,33 +421,22 @@ __device__ __forceinline__ Mom<Q> moments(const KParams& p, const float (&f)[Q])
   return m;
 }
 
-// ---- arithmetic on one cell (float) or two cells (float2, the packed FP32x2 pipe) ---------
-// Every operation rounds once to nearest even and none is contracted by the compiler, so
-// a thread that updates two cells gives each the bits a one-cell thread gives it.
+// ---- arithmetic, written for a value type V (float: one cell per thread) ----------------------
+// Every operation rounds once to nearest even and none is contracted by the compiler, so every
+// kernel form (direct, staged, x-pair, closure) gives a cell the same bits.
 __device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
-// a - b as b * (-1) + a: the product is exact, so this is the correctly rounded difference
-__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
-__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 template <class V> __device__ __forceinline__ V vset(float a);
 template <> __device__ __forceinline__ float vset<float>(float a) { return a; }
-template <> __device__ __forceinline__ float2 vset<float2>(float a) { return make_float2(a, a); }
 
 template <class V> struct Lanes;
 template <> struct Lanes<float> {
   static constexpr int n = 1;
   __device__ __forceinline__ static float get(float v, int) { return v; }
   __device__ __forceinline__ static void put(float& v, int, float a) { v = a; }
-};
-template <> struct Lanes<float2> {
-  static constexpr int n = 2;
-  __device__ __forceinline__ static float get(float2 v, int k) { return k ? v.y : v.x; }
-  __device__ __forceinline__ static void put(float2& v, int k, float a) { (k ? v.y : v.x) = a; }
 };
 
 // Orientation of the +/- pair (I, I+1), I odd: the member whose first non-zero velocity
@@ -612,59 +589,63 @@ __device__ __forceinline__ void les_rates(const KParams& p, float qn, float inv,
 template <class S>
 constexpr bool acc_form = std::is_same<S, float>::value;
 
-template <int Q, int CL, class V, bool ACC = true>
-__device__ __forceinline__ V collide(const KParams& p, V (&f)[Q]) {
+// Macroscopic fields of a cell (or two): density, momentum j = sum c df + F/2, velocity and,
+// when STRESS, the non-equilibrium stress Pi^neq and its invariant Q = Pi:Pi.
+template <class V>
+struct Macro {
+  V drho, rho, jx, jy, jz, inv, ux, uy, uz;
+  V pi[6], qn;
+};
+
+template <int Q, bool STRESS, class V>
+__device__ __forceinline__ Macro<V> macro(const KParams& p, const V (&f)[Q]) {
   using Pairs = std::make_integer_sequence<int, (Q - 1) / 2>;
   using L = Lanes<V>;
   V m[10];
   m[0] = f[0];
   all_pair_moments<Q, V>(f, m, Pairs{});
-  const V drho = m[0];
-  const V rho = vadd(drho, vset<V>(1.f));
-  const V jx = vadd(m[1], vset<V>(0.5f * p.F[0]));
-  const V jy = vadd(m[2], vset<V>(0.5f * p.F[1]));
-  const V jz = vadd(m[3], vset<V>(0.5f * p.F[2]));
-  V inv;
+  Macro<V> M;
+  M.drho = m[0];
+  M.rho = vadd(M.drho, vset<V>(1.f));
+  M.jx = vadd(m[1], vset<V>(0.5f * p.F[0]));
+  M.jy = vadd(m[2], vset<V>(0.5f * p.F[1]));
+  M.jz = vadd(m[3], vset<V>(0.5f * p.F[2]));
 #pragma unroll
-  for (int k = 0; k < L::n; k++) L::put(inv, k, __fdividef(1.f, L::get(rho, k)));
-  const V ux = vmul(jx, inv), uy = vmul(jy, inv), uz = vmul(jz, inv);
-  V wp = vset<V>(p.omega_p), wm = vset<V>(p.omega_m);
-  if (CL != CL_NONE) {
+  for (int k = 0; k < L::n; k++) L::put(M.inv, k, __fdividef(1.f, L::get(M.rho, k)));
+  M.ux = vmul(M.jx, M.inv);
+  M.uy = vmul(M.jy, M.inv);
+  M.uz = vmul(M.jz, M.inv);
+  if (STRESS) {
     // Pi^neq = sum_i c c df_i - (drho/3) I - j u   (shifted form of sum c c (f - feq))
-    const V d3 = vmul(drho, vset<V>(1.f / 3.f));
-    V pi[6];
-    pi[0] = vsub(vsub(m[4], d3), vmul(jx, ux));
-    pi[1] = vsub(vsub(m[5], d3), vmul(jy, uy));
-    pi[2] = vsub(vsub(m[6], d3), vmul(jz, uz));
-    pi[3] = vsub(m[7], vmul(jx, uy));
-    pi[4] = vsub(m[8], vmul(jx, uz));
-    pi[5] = vsub(m[9], vmul(jy, uz));
-    V qn = vfma(pi[5], pi[5], vfma(pi[4], pi[4], vmul(pi[3], pi[3])));
-    qn = vfma(pi[2], pi[2], vfma(pi[1], pi[1], vfma(pi[0], pi[0], vadd(qn, qn))));
-#pragma unroll
-    for (int k = 0; k < L::n; k++) {
-      float cs2 = p.cs2;
-      if constexpr (CL == CL_MLP) {
-        static_assert(L::n == 1, "the learned closure runs one cell per thread");
-        cs2 = fmaxf(mlp_cs2(p, pi, drho), p.cs2_min);
-      }
-      float a, b;
-      les_rates(p, L::get(qn, k), L::get(inv, k), cs2, a, b);
-      L::put(wp, k, a);
-      L::put(wm, k, b);
-    }
+    const V d3 = vmul(M.drho, vset<V>(1.f / 3.f));
+    M.pi[0] = vsub(vsub(m[4], d3), vmul(M.jx, M.ux));
+    M.pi[1] = vsub(vsub(m[5], d3), vmul(M.jy, M.uy));
+    M.pi[2] = vsub(vsub(m[6], d3), vmul(M.jz, M.uz));
+    M.pi[3] = vsub(m[7], vmul(M.jx, M.uy));
+    M.pi[4] = vsub(m[8], vmul(M.jx, M.uz));
+    M.pi[5] = vsub(m[9], vmul(M.jy, M.uz));
+    V qn = vfma(M.pi[5], M.pi[5], vfma(M.pi[4], M.pi[4], vmul(M.pi[3], M.pi[3])));
+    M.qn = vfma(M.pi[2], M.pi[2], vfma(M.pi[1], M.pi[1], vfma(M.pi[0], M.pi[0], vadd(qn, qn))));
   }
+  return M;
+}
+
+// TRT relaxation with Guo forcing at the rates omega+ (wp) and omega- (wm), in place.
+// ACC: the accurate pair update (float32 storage) or the lean one (half storage).
+template <int Q, class V, bool ACC>
+__device__ __forceinline__ void relax(const KParams& p, V (&f)[Q], const Macro<V>& M, V wp, V wm) {
+  using Pairs = std::make_integer_sequence<int, (Q - 1) / 2>;
   CollCtx<V> c;
-  c.ux = ux;
-  c.uy = uy;
-  c.uz = uz;
-  c.jx = jx;
-  c.jy = jy;
-  c.jz = jz;
-  const V usq = vfma(uz, uz, vfma(uy, uy, vmul(ux, ux)));
-  const V uF = vfma(uz, vset<V>(p.F[2]), vfma(uy, vset<V>(p.F[1]), vmul(ux, vset<V>(p.F[0]))));
-  c.A = vfma(vmul(rho, vset<V>(-1.5f)), usq, drho);
-  c.B = vmul(rho, vset<V>(4.5f));
+  c.ux = M.ux;
+  c.uy = M.uy;
+  c.uz = M.uz;
+  c.jx = M.jx;
+  c.jy = M.jy;
+  c.jz = M.jz;
+  const V usq = vfma(M.uz, M.uz, vfma(M.uy, M.uy, vmul(M.ux, M.ux)));
+  const V uF = vfma(M.uz, vset<V>(p.F[2]), vfma(M.uy, vset<V>(p.F[1]), vmul(M.ux, vset<V>(p.F[0]))));
+  c.A = vfma(vmul(M.rho, vset<V>(-1.5f)), usq, M.drho);
+  c.B = vmul(M.rho, vset<V>(4.5f));
   c.nhwp = vmul(wp, vset<V>(-0.5f));
   c.nhwm = vmul(wm, vset<V>(-0.5f));
   c.gp = vadd(c.nhwp, vset<V>(1.f));
@@ -684,12 +665,32 @@ __device__ __forceinline__ V collide(const KParams& p, V (&f)[Q]) {
       const float w = (float)(k == 0 ? wgt_d<Q>(1) : k == 1 ? wgt_d<Q>(7) : wgt_d<Q>(19 % Q));
       kw[k][0] = vmul(c.A, vset<V>(2.f * w));
       kw[k][1] = vmul(c.B, vset<V>(2.f * w));
-      kw[k][2] = vmul(rho, vset<V>(6.f * w));
+      kw[k][2] = vmul(M.rho, vset<V>(6.f * w));
       kw[k][3] = vmul(c.gu3, vset<V>(-w));
     }
     trt_pairs_lean<Q, V>(p, f, c, kw, Pairs{});
   }
-  return rho;
+}
+
+// Stream-collide arithmetic of one cell (or two) without a learned closure: plain TRT or
+// TRT with the Smagorinsky relaxation time.  Returns rho.
+template <int Q, int CL, class V, bool ACC = true>
+__device__ __forceinline__ V collide(const KParams& p, V (&f)[Q]) {
+  static_assert(CL != CL_MLP, "the learned closure has its own kernel");
+  using L = Lanes<V>;
+  const Macro<V> M = macro<Q, CL != CL_NONE, V>(p, f);
+  V wp = vset<V>(p.omega_p), wm = vset<V>(p.omega_m);
+  if (CL != CL_NONE) {
+#pragma unroll
+    for (int k = 0; k < L::n; k++) {
+      float a, b;
+      les_rates(p, L::get(M.qn, k), L::get(M.inv, k), p.cs2, a, b);
+      L::put(wp, k, a);
+      L::put(wm, k, b);
+    }
+  }
+  relax<Q, V, ACC>(p, f, M, wp, wm);
+  return M.rho;
 }
 
 // ---- kernels ------------------------------------------------------------------------------
@@ -705,7 +706,7 @@ __device__ __forceinline__ V collide(const KParams& p, V (&f)[Q]) {
 // LOAD / STORE modes as in load_state / store_state: AA even (0, 0), AA odd (1, 1), first
 // pull step after an import (0, 2), pull step (2, 2).
 template <int Q, class S, int CL, int LOAD, int STORE>
-__global__ void __launch_bounds__(128, CL == CL_MLP ? 4 : 8) k_step(const __grid_constant__ KParams p) {
+__global__ void __launch_bounds__(128, 8) k_step(const __grid_constant__ KParams p) {
   LBM_CELL_COORDS
   float f[Q];
   unsigned outmask;
@@ -717,54 +718,12 @@ __global__ void __launch_bounds__(128, CL == CL_MLP ? 4 : 8) k_step(const __grid
   store_state<Q, S, STORE>(p, x, y, z, cell, cls, f);
 }
 
-// The step for two cells per thread, (x, y) and (x, y + 1): their loads and stores are the
-// one-cell kernel's, and the collision runs on float2 pairs in the packed FP32x2 pipe
-// (half the arithmetic instructions of two one-cell threads, twice the loads in flight per
-// thread).  Block (32, 4) covers 32 x 8 cells; grid (nxp/32, ceil(ny/8), nz).  The learned
-// closure keeps the one-cell kernel.
-#ifndef LBM_PAIR_MINB
-#define LBM_PAIR_MINB 4
-#endif
-template <int Q, class S, int CL, int LOAD, int STORE>
-__global__ void __launch_bounds__(128, LBM_PAIR_MINB) k_step2(const __grid_constant__ KParams p) {
-  static_assert(CL != CL_MLP, "the learned closure runs one cell per thread");
-  const int x = blockIdx.x * 32 + threadIdx.x;
-  const int y = (blockIdx.y * blockDim.y + threadIdx.y) * 2;
-  const int z = blockIdx.z;
-  if (y >= p.ny) return;  // whole warp
-  const int cell0 = cidx(p, x, y, z);
-  const int cell1 = cell0 + p.nxp;
-  const int cls0 = x < p.nx ? p.cls[cell0] : CLS_SKIP;
-  const int cls1 = (x < p.nx && y + 1 < p.ny) ? p.cls[cell1] : CLS_SKIP;
-  float fa[Q], fb[Q];
-  unsigned oa, ob;
-  load_state<Q, S, LOAD>(p, x, y, z, cell0, cls0, fa, oa);
-  load_state<Q, S, LOAD>(p, x, y + 1, z, cell1, cls1, fb, ob);
-  outflow_fix<Q>(p, x, fa, oa);
-  outflow_fix<Q>(p, x, fb, ob);
-  if (cls0 == CLS_SKIP && cls1 == CLS_SKIP) return;
-  float2 f[Q];
-#pragma unroll
-  for (int i = 0; i < Q; i++) f[i] = make_float2(fa[i], fb[i]);
-  const float2 rho = collide<Q, CL, float2, acc_form<S>>(p, f);
-  const bool bad0 = cls0 != CLS_SKIP && !(rho.x > 0.f && rho.x < 3.0e38f);
-  const bool bad1 = cls1 != CLS_SKIP && !(rho.y > 0.f && rho.y < 3.0e38f);
-  if (bad0 || bad1) atomicOr(p.status, 1);
-#pragma unroll
-  for (int i = 0; i < Q; i++) {
-    fa[i] = f[i].x;
-    fb[i] = f[i].y;
-  }
-  if (cls0 != CLS_SKIP) store_state<Q, S, STORE>(p, x, y, z, cell0, cls0, fa);
-  if (cls1 != CLS_SKIP) store_state<Q, S, STORE>(p, x, y + 1, z, cell1, cls1, fb);
-}
-
 // The same step with register double-buffering along z: each thread updates ZC cells
 // (x, y, z0 .. z0+ZC-1) and loads the next cell's populations before colliding the current
 // one, so a warp keeps one cell's loads in flight through its arithmetic.  Consecutive
 // cells of a thread own disjoint slots in both AA launches, so the early load is safe.
 template <int Q, class S, int CL, int PAR, int ZC>
-__global__ void __launch_bounds__(128, CL == CL_MLP ? 4 : 5) k_step_zp(const __grid_constant__ KParams p) {
+__global__ void __launch_bounds__(128, 5) k_step_zp(const __grid_constant__ KParams p) {
   const int x = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z0 = blockIdx.z * ZC;

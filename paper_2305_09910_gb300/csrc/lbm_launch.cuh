@@ -6,6 +6,7 @@
 #include "lbm_tma.cuh"
 #include "lbm_async.cuh"
 #include "lbm_h2.cuh"
+#include "lbm_mlp.cuh"
 
 namespace lbm {
 
@@ -18,6 +19,8 @@ template <int Q, class S>
 cudaError_t launch_step(const KParams& p, int closure, int parity, const Launch& L);
 template <int Q, class S>
 cudaError_t launch_step_tma(const KParams& p, int closure, int parity, cudaStream_t stream, int nsm);
+template <int Q, class S>
+cudaError_t launch_step_mlp(const KParams& p, int mode, cudaStream_t stream, int nsm);
 template <int Q, class S>
 cudaError_t launch_step_async(const KParams& p, int closure, int mode, const Launch& L);
 template <int Q, class S>
@@ -34,6 +37,7 @@ cudaError_t launch_set_pop(const KParams& p, const float* df, const Launch& L);
   extern template cudaError_t launch_step_tma<Q, S>(const KParams&, int, int, cudaStream_t, int);  \
   extern template cudaError_t launch_step_zp<Q, S>(const KParams&, int, int, const Launch&);       \
   extern template cudaError_t launch_step_async<Q, S>(const KParams&, int, int, const Launch&);    \
+  extern template cudaError_t launch_step_mlp<Q, S>(const KParams&, int, cudaStream_t, int);      \
   extern template cudaError_t launch_export<Q, S>(const KParams&, int, int, const ExportArgs&,     \
                                                   const Launch&);                                  \
   extern template cudaError_t launch_init_eq<Q, S>(const KParams&, const float*, const float*,     \

@@ -137,7 +137,7 @@ __device__ __noinline__ void issue_tile(const KParams& p, long long t, unsigned 
 }
 
 template <int Q, class S, int CL, int PAR>
-__global__ void __launch_bounds__(TMA_TX, CL == CL_MLP ? 4 : 5) k_step_tma(const __grid_constant__ KParams p,
+__global__ void __launch_bounds__(TMA_TX, 5) k_step_tma(const __grid_constant__ KParams p,
                                                                            long long ntiles) {
   using G = TmaGeom<S>;
   constexpr int RL = G::template rowlen<PAR>();
