@@ -4,7 +4,8 @@ Workload (default): the turbulent channel of the paper's Sec. 5.1 benchmark clas
 synthetic stand-in: 512 x 256 x 256 cells, D3Q19 TRT + Smagorinsky (C_s = 0.1), float32
 populations, walls at the y faces, periodic x/z, body force for Re_tau ~ 180, initial
 state = equilibrium of the seeded perturbed parabola.  One step = one lattice update of
-every cell (one AA kernel launch).  MLUPS counts all cells, like the paper (Sec. 5.2).
+every cell (one kernel launch; two-grid pull streaming by default, the in-place AA pattern
+is reported as a form).  MLUPS counts all cells, like the paper (Sec. 5.2).
 
 Roofline (Sec. 5.2, Eq. roofline: P_max = b_s / n_b): n_b = 2 q s + 1 bytes per update
 (q populations of s bytes read and written, one flag byte), b_s = the measured copy
@@ -34,7 +35,7 @@ if ROOT not in sys.path:
 
 METRIC = "MLUPS & % of HBM roofline per form (FP32/FP16/MLP closure) at stated error"
 FALLBACK_HBM_GBS = 6800.0
-WORKLOAD = "turbulent channel 512x256x256 D3Q19 TRT+Smagorinsky FP32 (AA in place)"
+WORKLOAD = "turbulent channel 512x256x256 D3Q19 TRT+Smagorinsky FP32 (two-grid pull)"
 FACES_CHANNEL = ("periodic", "periodic", "wall", "wall", "periodic", "periodic")
 
 
@@ -154,14 +155,14 @@ def _barrier_max(dist, value):
     return float(t.item())
 
 
-def _channel_lattice(nx, ny, nz, precision, closure="smag"):
+def _channel_lattice(nx, ny, nz, precision, closure="smag", streaming="pull"):
     import torch
 
     from paper_2305_09910_gb300 import inputs, lbm
 
     par = inputs.channel_parameters(ny)
     lat = lbm.Lattice(nx, ny, nz, stencil=19, tau=par["tau"], precision=precision, closure=closure,
-                      cs_smag=0.1, faces=FACES_CHANNEL)
+                      cs_smag=0.1, faces=FACES_CHANNEL, streaming=streaming)
     lat.set_force(par["force"])
     rho = torch.empty((nz, ny, nx), dtype=torch.float32, device="cuda")
     u = torch.empty((3, nz, ny, nx), dtype=torch.float32, device="cuda")
@@ -236,8 +237,10 @@ def _extra_forms(nsteps, warmup, peak, peak_kind):
       * precision form: channel 1024x512x512 (268M cells), FP32 and FP16-shifted storage;
       * bluff body: 768x384x384 D3Q27 TRT+Smagorinsky tunnel (inflow 0.05, outflow, free-slip)
         with the landing-gear flags, FP32 and FP16-shifted storage;
-      * learned closure: channel 256x128x128, fused MLP closure vs Smagorinsky (network
-        weights from a fixed seed: the cost of the fused inference does not depend on them)."""
+      * learned closure: channel 256x128x128 and 512x256x256, fused MLP closure (tensor-core
+        hidden layer) vs Smagorinsky (network weights from a fixed seed: the cost of the fused
+        inference does not depend on them).
+    All forms use two-grid pull streaming except those named _aa (in-place AA pattern)."""
     import numpy as np
     import torch
 
@@ -247,7 +250,7 @@ def _extra_forms(nsteps, warmup, peak, peak_kind):
     par = inputs.channel_parameters(512)
     for prec in ("f32", "f16"):
         lat = lbm.Lattice(1024, 512, 512, stencil=19, tau=par["tau"], precision=prec, closure="smag",
-                          cs_smag=0.1, faces=FACES_CHANNEL)
+                          cs_smag=0.1, faces=FACES_CHANNEL, streaming="pull")
         lat.set_force(par["force"])
         lat.init_equilibrium()
         out[f"channel1024_{prec}"] = _form_line(lat, max(20, nsteps // 4), warmup, peak, peak_kind)
@@ -258,7 +261,7 @@ def _extra_forms(nsteps, warmup, peak, peak_kind):
     for prec in ("f32", "f16"):
         lat = lbm.Lattice(768, 384, 384, stencil=27, tau=tau, precision=prec, closure="smag", cs_smag=0.1,
                           faces=("inflow", "outflow", "freeslip", "freeslip", "freeslip", "freeslip"),
-                          u_inflow=(0.05, 0.0, 0.0))
+                          u_inflow=(0.05, 0.0, 0.0), streaming="pull")
         lat.set_flags(flags)
         u = torch.zeros((3, 384, 384, 768), dtype=torch.float32, device="cuda")
         u[0] = 0.05
@@ -269,15 +272,17 @@ def _extra_forms(nsteps, warmup, peak, peak_kind):
         torch.cuda.empty_cache()
     params = closure.init_params(7)
     params[closure.OUT_LAYER] = np.random.default_rng(7).normal(0, 0.1, 33).astype(np.float32)
-    for name in ("smag", "mlp"):
-        lat = closure.channel(256, 128, 128, closure=name)
+    for size, name in ((256, "smag"), (256, "mlp"), (512, "mlp")):
+        lat = closure.channel(size, size // 2, size // 2, closure=name, streaming="pull")
         if name == "mlp":
             lbm.lbm_set_closure_f32(lat.h, params, 600.0, 3000.0)
             lbm.lbm_set_closure_floor(lat.h, 0.1)
         line = _form_line(lat, nsteps, warmup, peak, peak_kind)
-        line["roofline"]["bound"] = "hbm" if name == "smag" else "alu (fused 7-32-32-1 network per cell)"
-        out[f"channel256_{name}"] = line
+        if name == "mlp":
+            line["roofline"]["bound"] = "alu (fused 7-32-32-1 network per cell; 32x32 layer on tcgen05)"
+        out[f"channel{size}_{name}"] = line
         lat.close()
+        torch.cuda.empty_cache()
     return out
 
 
@@ -354,6 +359,8 @@ def main():
     ap.add_argument("--size", default="512x256x256", help="lattice NXxNYxNZ (profiling runs)")
     ap.add_argument("--form", default="f32", choices=["f32", "f16", "bf16"],
                     help="storage precision of the main line (profiling runs)")
+    ap.add_argument("--streaming", default="pull", choices=["pull", "aa"],
+                    help="streaming pattern of the main line (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -377,7 +384,7 @@ def main():
 
     nx, ny, nz = (int(v) for v in args.size.lower().split("x"))
     ncell = nx * ny * nz
-    lat, par = _channel_lattice(nx, ny, nz, args.form)
+    lat, par = _channel_lattice(nx, ny, nz, args.form, streaming=args.streaming)
     clocks = ClockSampler(gpu_id)
     time.sleep(1.0)  # let nvidia-smi start
     for _ in range(args.warmup):
@@ -388,7 +395,7 @@ def main():
     clocks.stop()
     total_ms = _barrier_max(dist, total_ms)
     value = world * ncell * args.steps / (total_ms * 1e-3) / 1e6
-    traffic = _profile_traffic(f"k_step_q19_{args.form}_smag_channel{nx}")
+    traffic = _profile_traffic(f"k_step_q19_{args.form}_smag_{args.streaming}_channel{nx}")
     roof = _roofline(ncell, lat.bytes_per_update, per, peak, peak_kind, traffic)
     mass = lat.reduce()[0]
     lat_bytes = ncell * 19 * lat.bytes_per_pop
@@ -425,14 +432,17 @@ def main():
     forms = {}
     if not args.no_forms:
         nsteps = max(50, args.steps // 4)
-        for prec in ("f16", "bf16"):
-            fl, _ = _channel_lattice(nx, ny, nz, prec)
-            forms[f"channel512_{prec}_shifted"] = _form_line(fl, nsteps, args.warmup, peak, peak_kind)
+        for prec, streaming in (("f32", "aa"), ("f16", "pull"), ("bf16", "pull"), ("f16", "aa")):
+            fl, _ = _channel_lattice(nx, ny, nz, prec, streaming=streaming)
+            tag = "" if streaming == "pull" else "_aa"
+            name = f"channel{nx}_{prec}{tag}" if prec == "f32" else f"channel{nx}_{prec}_shifted{tag}"
+            forms[name] = _form_line(fl, nsteps, args.warmup, peak, peak_kind)
             fl.close()
+            torch.cuda.empty_cache()
         forms.update(_extra_forms(nsteps, args.warmup, peak, peak_kind))
 
-    workload = WORKLOAD if (nx, ny, nz, args.form) == (512, 256, 256, "f32") else \
-        f"turbulent channel {nx}x{ny}x{nz} D3Q19 TRT+Smagorinsky {args.form} (AA in place)"
+    workload = WORKLOAD if (nx, ny, nz, args.form, args.streaming) == (512, 256, 256, "f32", "pull") else \
+        f"turbulent channel {nx}x{ny}x{nz} D3Q19 TRT+Smagorinsky {args.form} ({args.streaming})"
     out = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,

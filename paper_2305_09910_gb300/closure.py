@@ -25,7 +25,7 @@ OUT_LAYER = slice(32 * 7 + 32 + 32 * 32 + 32, NP)
 
 
 def channel(nx, ny, nz, closure="smag", cs0=0.1, precision="f32", re_tau=180.0, u_bulk=0.05,
-            seed=inputs.DEFAULT_SEED, tau=None, force=None, amp=0.1):
+            seed=inputs.DEFAULT_SEED, tau=None, force=None, amp=0.1, streaming="aa"):
     """A channel lattice (walls at the y faces) initialised from the perturbed parabola."""
     import torch
 
@@ -33,7 +33,7 @@ def channel(nx, ny, nz, closure="smag", cs0=0.1, precision="f32", re_tau=180.0, 
     tau = par["tau"] if tau is None else tau
     force = par["force"] if force is None else force
     lat = lbm.Lattice(nx, ny, nz, stencil=19, tau=tau, precision=precision, closure=closure,
-                      cs_smag=cs0, faces=FACES_CHANNEL)
+                      cs_smag=cs0, faces=FACES_CHANNEL, streaming=streaming)
     lat.set_force(force)
     rho = torch.empty((nz, ny, nx), dtype=torch.float32, device="cuda")
     u = torch.empty((3, nz, ny, nx), dtype=torch.float32, device="cuda")

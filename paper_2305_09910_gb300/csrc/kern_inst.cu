@@ -154,14 +154,18 @@ cudaError_t launch_step_tma(const KParams& p, int closure, int parity, cudaStrea
 
 template <int Q, class S, int PAR>
 static void export_par(const KParams& p, int mode, const ExportArgs& a, const Launch& L) {
-  // plane sums: a grid of (ny, z chunks) blocks, about four per multiprocessor
-  const int zchunk = std::max(1, (int)((long long)p.nz * p.ny / 608 + 1));
-  const dim3 sgrid((unsigned)p.ny, (unsigned)((p.nz + zchunk - 1) / zchunk));
+  const dim3 rows((unsigned)p.ny, (unsigned)p.nz);
   switch (mode) {
     case EX_POP: k_export<Q, S, PAR, EX_POP><<<L.grid, L.block, 0, L.stream>>>(p, a); break;
     case EX_MOM: k_export<Q, S, PAR, EX_MOM><<<L.grid, L.block, 0, L.stream>>>(p, a); break;
-    case EX_SUM: k_plane_sums<Q, S, PAR, EX_SUM><<<sgrid, 128, 0, L.stream>>>(p, a.sums, zchunk); break;
-    default: k_plane_sums<Q, S, PAR, EX_STATS><<<sgrid, 128, 0, L.stream>>>(p, a.sums, zchunk); break;
+    case EX_SUM:
+      k_row_sums<Q, S, PAR, EX_SUM><<<rows, ROW_THREADS, 0, L.stream>>>(p, a.partial);
+      k_row_total<EX_SUM><<<1, 256, 0, L.stream>>>(a.partial, p.ny, p.nz, a.sums);
+      break;
+    default:
+      k_row_sums<Q, S, PAR, EX_STATS><<<rows, ROW_THREADS, 0, L.stream>>>(p, a.partial);
+      k_row_total<EX_STATS><<<(unsigned)p.ny, 256, 0, L.stream>>>(a.partial, p.ny, p.nz, a.sums);
+      break;
   }
 }
 

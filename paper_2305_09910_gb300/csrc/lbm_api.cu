@@ -31,6 +31,7 @@ struct lbm_s {
   int* status = nullptr;      // device status word
   int* status_host = nullptr; // pinned copy
   double* sums = nullptr;     // 4 doubles (lbm_reduce)
+  double* partial = nullptr;  // nz * ny * 10 doubles: per-row sums of the reductions
   double* stats = nullptr;    // ny * LBM_STATS_K doubles
   float* mlp = nullptr;       // MLP parameters widened to float
   float mlp_scale[2] = {0.f, 0.f};
@@ -350,6 +351,7 @@ lbm_status lbm_destroy(lbm_handle h) {
   if (h->rules) cudaFreeAsync(h->rules, h->stream);
   if (h->status) cudaFreeAsync(h->status, h->stream);
   if (h->sums) cudaFreeAsync(h->sums, h->stream);
+  if (h->partial) cudaFreeAsync(h->partial, h->stream);
   if (h->stats) cudaFreeAsync(h->stats, h->stream);
   if (h->mlp) cudaFreeAsync(h->mlp, h->stream);
   cudaStreamSynchronize(h->stream);
@@ -427,6 +429,7 @@ lbm_status lbm_create(int nx, int ny, int nz, int stencil, double tau, const lbm
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->rules, (size_t)plane * 8, h->stream);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->status, sizeof(int), h->stream);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->sums, 4 * sizeof(double), h->stream);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->partial, (size_t)ny * nz * 10 * sizeof(double), h->stream);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->stats, (size_t)ny * LBM_STATS_K * sizeof(double), h->stream);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&h->status_host, sizeof(int));
   if (e == cudaSuccess) e = cudaMemsetAsync(h->f, 0, fbytes, h->stream);
@@ -641,9 +644,9 @@ lbm_status lbm_get_populations(lbm_handle h, float* df, int on_device) {
 lbm_status lbm_reduce(lbm_handle h, double out[4]) {
   if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
   if (!out) return fail(h, LBM_EINVAL, "out is NULL");
-  CUDA_TRY(h, cudaMemsetAsync(h->sums, 0, 4 * sizeof(double), h->stream));
   ExportArgs a{};
   a.sums = h->sums;
+  a.partial = h->partial;
   lbm_status s = run_export(h, EX_SUM, a);
   if (s != LBM_OK) return s;
   CUDA_TRY(h, cudaMemcpyAsync(out, h->sums, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -662,6 +665,7 @@ lbm_status lbm_stats_sample(lbm_handle h) {
   if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
   ExportArgs a{};
   a.sums = h->stats;
+  a.partial = h->partial;
   lbm_status s = run_export(h, EX_STATS, a);
   if (s != LBM_OK) return s;
   h->nsamples++;

@@ -4,10 +4,11 @@
 // c_x = 0 (and every own-cell slot) is one aligned 32-bit word holding both cells' 16-bit
 // values: one load and one store move two populations.  Slots shifted in x by the odd AA
 // gather (c_x != 0) straddle two words and move as two 16-bit accesses.  The loaded words
-// stay packed (one register per direction for both cells); cell x is unpacked and collided
-// first, then cell x+1, and the two results are rounded and packed into one word each.
-// This halves the memory instructions and address arithmetic per cell and doubles the
-// bytes a thread keeps in flight, at the register cost of the one-cell kernel.
+// stay packed (one register per direction for both cells) until the collision, which runs on
+// both cells at once in the packed FP32x2 pipe (float2 operands: FFMA2/FADD2/FMUL2); the two
+// results are rounded and packed into one word each.  This halves the memory instructions,
+// the address arithmetic and the arithmetic instructions per cell and doubles the bytes a
+// thread keeps in flight (LBM_H2_VEC=0 collides the two cells one after the other instead).
 //
 // Warps with any non-interior cell (boundary rules, periodic y/z wrap, skipped cells) take
 // the one-cell code for each of their two cells instead; the zero-gradient outflow passes
@@ -30,6 +31,16 @@ template <> __device__ __forceinline__ float hi_of<__half>(uint32_t v) {
 template <> __device__ __forceinline__ float lo_of<__nv_bfloat16>(uint32_t v) { return __uint_as_float(v << 16); }
 template <> __device__ __forceinline__ float hi_of<__nv_bfloat16>(uint32_t v) {
   return __uint_as_float(v & 0xffff0000u);
+}
+
+template <class S> __device__ __forceinline__ uint32_t pack2(float a, float b);  // a in the low half
+template <> __device__ __forceinline__ uint32_t pack2<__half>(float a, float b) {
+  const __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+template <> __device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
 }
 
 // 16-bit pattern of v rounded to the storage precision (round to nearest even)
@@ -86,8 +97,11 @@ __device__ __noinline__ void pair_fallback(const KParams& p, int x, int y, int z
   }
 }
 
+#ifndef LBM_H2_VEC
+#define LBM_H2_VEC 1
+#endif
 #ifndef LBM_H2_MINB
-#define LBM_H2_MINB 8
+#define LBM_H2_MINB (LBM_H2_VEC ? 7 : 8)
 #endif
 template <int Q, class S, int CL, int LOAD, int STORE>
 __global__ void __launch_bounds__(128, LBM_H2_MINB) k_step_h2(const __grid_constant__ KParams p) {
@@ -125,6 +139,16 @@ __global__ void __launch_bounds__(128, LBM_H2_MINB) k_step_h2(const __grid_const
         }
       }
     }
+#if LBM_H2_VEC
+    // both cells at once in the packed FP32x2 pipe
+    float2 f[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) f[i] = make_float2(lo_of<S>(h[i]), hi_of<S>(h[i]));
+    const float2 rho = collide<Q, CL, float2, false>(p, f);
+#pragma unroll
+    for (int i = 0; i < Q; i++) h[i] = pack2<S>(f[i].x, f[i].y);
+    const float ra = rho.x, rb = rho.y;
+#else
     // first cell: unpack, collide, round back into the low halves
     float f[Q];
 #pragma unroll
@@ -138,6 +162,7 @@ __global__ void __launch_bounds__(128, LBM_H2_MINB) k_step_h2(const __grid_const
     const float rb = collide<Q, CL, float, false>(p, f);
 #pragma unroll
     for (int i = 0; i < Q; i++) h[i] = __byte_perm(h[i], bits16<S>(f[i]), 0x5410);
+#endif
     if (!(ra > 0.f && ra < 3.0e38f) || !(rb > 0.f && rb < 3.0e38f)) atomicOr(p.status, 1);
 #pragma unroll
     for (int i = 0; i < Q; i++) {

@@ -421,22 +421,34 @@ __device__ __forceinline__ Mom<Q> moments(const KParams& p, const float (&f)[Q])
   return m;
 }
 
-// ---- arithmetic, written for a value type V (float: one cell per thread) ----------------------
+// ---- arithmetic, written for a value type V (float: one cell, float2: two cells per thread) ---
 // Every operation rounds once to nearest even and none is contracted by the compiler, so every
 // kernel form (direct, staged, x-pair, closure) gives a cell the same bits.
 __device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+// two cells in the packed FP32x2 pipe (sm_100 family): the same roundings per component
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b as b * (-1) + a: the product is exact, so this is the correctly rounded difference
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 template <class V> __device__ __forceinline__ V vset(float a);
 template <> __device__ __forceinline__ float vset<float>(float a) { return a; }
+template <> __device__ __forceinline__ float2 vset<float2>(float a) { return make_float2(a, a); }
 
 template <class V> struct Lanes;
 template <> struct Lanes<float> {
   static constexpr int n = 1;
   __device__ __forceinline__ static float get(float v, int) { return v; }
   __device__ __forceinline__ static void put(float& v, int, float a) { v = a; }
+};
+template <> struct Lanes<float2> {
+  static constexpr int n = 2;
+  __device__ __forceinline__ static float get(float2 v, int k) { return k ? v.y : v.x; }
+  __device__ __forceinline__ static void put(float2& v, int k, float a) { (k ? v.y : v.x) = a; }
 };
 
 // Orientation of the +/- pair (I, I+1), I odd: the member whose first non-zero velocity
@@ -518,33 +530,6 @@ struct CollCtx {
 // exactly; eln = -el), and the non-equilibrium parts are formed by subtracting it from f
 // first, where the operands nearly cancel.  This keeps the per-step momentum error at the
 // level of one rounding of f, which matters at the small velocities of laminar runs.
-// The same pair update for half-precision storage, where the rounding of the stored value
-// (2^-11 or 2^-8 relative) dominates: the non-equilibrium parts are formed from the pair sum
-// and difference, and the antisymmetric equilibrium as 3 w rho (c.u) in one rounding.
-// kw: per-weight-class factors 2 w A, 2 w B, 6 w rho, -w gu3, indexed by |c|^2 - 1.
-template <int Q, int I, class V>
-__device__ __forceinline__ void trt_pair_lean(const KParams& p, V (&f)[Q], const CollCtx<V>& c,
-                                              const V (&kw)[3][4]) {
-  constexpr int P = prim(I), R = P == I ? I + 1 : I;
-  constexpr int X = cx(P), Y = cy(P), Z = cz(P), K = csq(P) - 1;
-  const V cu = cdot<X, Y, Z>(c.ux, c.uy, c.uz);
-  const V s = vadd(f[P], f[R]);
-  const V d = vsub(f[P], f[R]);
-  const V t1 = vsub(s, vfma(kw[K][1], vmul(cu, cu), kw[K][0]));
-  const V t2 = vsub(d, vmul(cu, kw[K][2]));
-  const V fsym = vfma(vmul(c.gp, vset<V>(p.F9w[P])), cu, kw[K][3]);
-  const V ds = vfma(c.nhwp, t1, fsym);
-  const V da = vfma(c.nhwm, t2, vmul(c.gm, vset<V>(p.F3w[P])));
-  f[P] = vadd(f[P], vadd(ds, da));
-  f[R] = vadd(f[R], vsub(ds, da));
-}
-
-template <int Q, class V, int... P>
-__device__ __forceinline__ void trt_pairs_lean(const KParams& p, V (&f)[Q], const CollCtx<V>& c,
-                                               const V (&kw)[3][4], std::integer_sequence<int, P...>) {
-  (trt_pair_lean<Q, 2 * P + 1, V>(p, f, c, kw), ...);
-}
-
 template <int Q, int I, class V>
 __device__ __forceinline__ void trt_pair(const KParams& p, V (&f)[Q], const CollCtx<V>& c) {
   constexpr int P = prim(I), R = P == I ? I + 1 : I;
@@ -571,6 +556,38 @@ template <int Q, class V, int... P>
 __device__ __forceinline__ void trt_pairs(const KParams& p, V (&f)[Q], const CollCtx<V>& c,
                                           std::integer_sequence<int, P...>) {
   (trt_pair<Q, 2 * P + 1, V>(p, f, c), ...);
+}
+
+// The pair update for half-precision storage, where the rounding of the stored value (2^-11
+// or 2^-8 relative) dominates.  With s = f_P + f_R and d = f_P - f_R the TRT update reads
+//   f*_P = S + D, f*_R = S - D,
+//   S = (1 - omega+) s / 2 + omega+ f^eq+ + F+,   D = (1 - omega-) d / 2 + omega- f^eq- + F-,
+// f^eq+ = w (A + B (c.u)^2), f^eq- = 3 w rho (c.u), F+ = (1 - omega+/2) w (9 (c.u)(c.F) - 3 u.F),
+// F- = (1 - omega-/2) 3 w (c.F).  Per weight class k: kb = omega+ w B, kc = omega+ w A - w gu3,
+// kr = 3 omega- w rho; hp = (1 - omega+)/2, hm = (1 - omega-)/2.
+template <class V>
+struct LeanCtx {
+  V ux, uy, uz, hp, hm, gp, gm;
+  V kb[3], kc[3], kr[3];
+};
+
+template <int Q, int I, class V>
+__device__ __forceinline__ void trt_pair_lean(const KParams& p, V (&f)[Q], const LeanCtx<V>& c) {
+  constexpr int P = prim(I), R = P == I ? I + 1 : I;
+  constexpr int X = cx(P), Y = cy(P), Z = cz(P), K = csq(P) - 1;
+  const V cu = cdot<X, Y, Z>(c.ux, c.uy, c.uz);
+  const V s = vadd(f[P], f[R]);
+  const V d = vsub(f[P], f[R]);
+  const V S = vfma(c.hp, s, vfma(vmul(c.gp, vset<V>(p.F9w[P])), cu, vfma(c.kb[K], vmul(cu, cu), c.kc[K])));
+  const V D = vfma(c.hm, d, vfma(c.kr[K], cu, vmul(c.gm, vset<V>(p.F3w[P]))));
+  f[P] = vadd(S, D);
+  f[R] = vsub(S, D);
+}
+
+template <int Q, class V, int... P>
+__device__ __forceinline__ void trt_pairs_lean(const KParams& p, V (&f)[Q], const LeanCtx<V>& c,
+                                               std::integer_sequence<int, P...>) {
+  (trt_pair_lean<Q, 2 * P + 1, V>(p, f, c), ...);
 }
 
 // sqrt of a non-negative value from the hardware reciprocal square root (x = 0 gives 0).
@@ -635,40 +652,55 @@ __device__ __forceinline__ Macro<V> macro(const KParams& p, const V (&f)[Q]) {
 template <int Q, class V, bool ACC>
 __device__ __forceinline__ void relax(const KParams& p, V (&f)[Q], const Macro<V>& M, V wp, V wm) {
   using Pairs = std::make_integer_sequence<int, (Q - 1) / 2>;
-  CollCtx<V> c;
-  c.ux = M.ux;
-  c.uy = M.uy;
-  c.uz = M.uz;
-  c.jx = M.jx;
-  c.jy = M.jy;
-  c.jz = M.jz;
   const V usq = vfma(M.uz, M.uz, vfma(M.uy, M.uy, vmul(M.ux, M.ux)));
   const V uF = vfma(M.uz, vset<V>(p.F[2]), vfma(M.uy, vset<V>(p.F[1]), vmul(M.ux, vset<V>(p.F[0]))));
-  c.A = vfma(vmul(M.rho, vset<V>(-1.5f)), usq, M.drho);
-  c.B = vmul(M.rho, vset<V>(4.5f));
-  c.nhwp = vmul(wp, vset<V>(-0.5f));
-  c.nhwm = vmul(wm, vset<V>(-0.5f));
-  c.gp = vadd(c.nhwp, vset<V>(1.f));
-  c.gm = vadd(c.nhwm, vset<V>(1.f));
-  c.gu3 = vmul(c.gp, vmul(uF, vset<V>(3.f)));
-  {
-    constexpr float w0 = (float)wgt_d<Q>(0);
-    const V n0 = vfma(c.A, vset<V>(-w0), f[0]);
-    f[0] = vadd(f[0], vfma(vadd(c.nhwp, c.nhwp), n0, vmul(c.gu3, vset<V>(-w0))));
-  }
+  const V A = vfma(vmul(M.rho, vset<V>(-1.5f)), usq, M.drho);
+  const V nhwp = vmul(wp, vset<V>(-0.5f)), nhwm = vmul(wm, vset<V>(-0.5f));
+  const V gp = vadd(nhwp, vset<V>(1.f)), gm = vadd(nhwm, vset<V>(1.f));
+  const V gu3 = vmul(gp, vmul(uF, vset<V>(3.f)));
   if constexpr (ACC) {
+    CollCtx<V> c;
+    c.ux = M.ux;
+    c.uy = M.uy;
+    c.uz = M.uz;
+    c.jx = M.jx;
+    c.jy = M.jy;
+    c.jz = M.jz;
+    c.A = A;
+    c.B = vmul(M.rho, vset<V>(4.5f));
+    c.nhwp = nhwp;
+    c.nhwm = nhwm;
+    c.gp = gp;
+    c.gm = gm;
+    c.gu3 = gu3;
+    {
+      constexpr float w0 = (float)wgt_d<Q>(0);
+      const V n0 = vfma(c.A, vset<V>(-w0), f[0]);
+      f[0] = vadd(f[0], vfma(vadd(c.nhwp, c.nhwp), n0, vmul(c.gu3, vset<V>(-w0))));
+    }
     trt_pairs<Q, V>(p, f, c, Pairs{});
   } else {
-    V kw[3][4];
+    LeanCtx<V> c;
+    c.ux = M.ux;
+    c.uy = M.uy;
+    c.uz = M.uz;
+    c.gp = gp;
+    c.gm = gm;
+    c.hp = vfma(wp, vset<V>(-0.5f), vset<V>(0.5f));
+    c.hm = vfma(wm, vset<V>(-0.5f), vset<V>(0.5f));
+    const V wpA = vmul(wp, A), wpB = vmul(wp, vmul(M.rho, vset<V>(4.5f))), wmr = vmul(wm, vmul(M.rho, vset<V>(3.f)));
 #pragma unroll
     for (int k = 0; k < 3; k++) {
       const float w = (float)(k == 0 ? wgt_d<Q>(1) : k == 1 ? wgt_d<Q>(7) : wgt_d<Q>(19 % Q));
-      kw[k][0] = vmul(c.A, vset<V>(2.f * w));
-      kw[k][1] = vmul(c.B, vset<V>(2.f * w));
-      kw[k][2] = vmul(M.rho, vset<V>(6.f * w));
-      kw[k][3] = vmul(c.gu3, vset<V>(-w));
+      c.kb[k] = vmul(wpB, vset<V>(w));
+      c.kc[k] = vfma(wpA, vset<V>(w), vmul(gu3, vset<V>(-w)));
+      c.kr[k] = vmul(wmr, vset<V>(w));
     }
-    trt_pairs_lean<Q, V>(p, f, c, kw, Pairs{});
+    {
+      constexpr float w0 = (float)wgt_d<Q>(0);
+      f[0] = vfma(vadd(c.hp, c.hp), f[0], vfma(wpA, vset<V>(w0), vmul(gu3, vset<V>(-w0))));
+    }
+    trt_pairs_lean<Q, V>(p, f, c, Pairs{});
   }
 }
 
@@ -764,7 +796,8 @@ struct ExportArgs {
   float* df;       // EX_POP: [q][nz][ny][nx]
   float* rho;      // EX_MOM: [nz][ny][nx] (may be null)
   float* u;        // EX_MOM: [3][nz][ny][nx] (may be null)
-  double* sums;    // EX_SUM: 4 doubles; EX_STATS: ny * 10 doubles
+  double* sums;    // EX_SUM: 4 doubles; EX_STATS: ny * 10 doubles (added to)
+  double* partial; // EX_SUM / EX_STATS: nz * ny * 10 doubles of scratch (per-row sums)
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -801,66 +834,88 @@ __global__ void __launch_bounds__(128) k_export(const __grid_constant__ KParams 
     }
     return;
   }
-  if (MODE == EX_SUM) {
-    double r = fluid ? (double)m.rho : 0.0;
-    double v[4] = {r, r * m.ux, r * m.uy, r * m.uz};
+}
+
+// Sums over fluid cells, in two passes.  k_row_sums: one block per (y, z) row; a thread adds
+// the values of its few cells of the row in FP32, the block adds the threads' partials in
+// FP64 and writes partial[(z ny + y) K + k].  k_row_total then adds the rows in FP64:
+//   EX_SUM   (K = 5: count, drho, j_x, j_y, j_z) -> sums[0] = count + sum drho = sum rho,
+//            sums[1..3] = sum j = sum rho u (j includes F/2, so u = j / rho);
+//   EX_STATS (K = 10: count, u_x, u_y, u_z, u_x^2, u_y^2, u_z^2, u_x u_y, u_x u_z, u_y u_z)
+//            -> sums[y * 10 + k] += sum over the x-z plane y.
+template <int MODE>
+__host__ __device__ constexpr int row_k() { return MODE == EX_SUM ? 5 : 10; }
+
+constexpr int ROW_THREADS = 256;
+
+template <int Q, class S, int PAR, int MODE>
+__global__ void __launch_bounds__(ROW_THREADS) k_row_sums(const __grid_constant__ KParams p, double* partial) {
+  constexpr int K = row_k<MODE>();
+  constexpr int NW = ROW_THREADS / 32;
+  const int y = blockIdx.x, z = blockIdx.y;
+  const int warp = threadIdx.x >> 5;
+  float acc[K];
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
-      const double s = warp_sum(v[k]);
-      if ((threadIdx.x & 31) == 0) atomicAdd(a.sums + k, s);
+  for (int k = 0; k < K; k++) acc[k] = 0.f;
+  for (int xb = 0; xb < p.nxp; xb += ROW_THREADS) {
+    if (xb + warp * 32 >= p.nxp) break;  // warp-uniform (nxp is a multiple of 32)
+    const int x = xb + threadIdx.x;
+    const int cell = cidx(p, x, y, z);
+    const int cls = x < p.nx ? p.cls[cell] : CLS_SKIP;
+    float f[Q];
+    unsigned outmask;
+    load_state<Q, S, PAR>(p, x, y, z, cell, cls, f, outmask);
+    outflow_fix<Q>(p, x, f, outmask);
+    if (cls == CLS_SKIP) continue;
+    const Mom<Q> m = moments<Q>(p, f);
+    if (MODE == EX_SUM) {
+      const float v[5] = {1.f, m.drho, m.jx, m.jy, m.jz};
+#pragma unroll
+      for (int k = 0; k < K; k++) acc[k] += v[k];
+    } else {
+      const float v[10] = {1.f, m.ux, m.uy, m.uz, m.ux * m.ux, m.uy * m.uy, m.uz * m.uz,
+                           m.ux * m.uy, m.ux * m.uz, m.uy * m.uz};
+#pragma unroll
+      for (int k = 0; k < K; k++) acc[k] += v[k];
     }
-    return;
   }
-  if (MODE == EX_STATS) {  // per y plane; a warp is one row segment at fixed y
-    const double ux = m.ux, uy = m.uy, uz = m.uz;
-    double v[10] = {fluid ? 1.0 : 0.0, ux, uy, uz, ux * ux, uy * uy, uz * uz, ux * uy, ux * uz, uy * uz};
+  __shared__ double red[K][NW];
 #pragma unroll
-    for (int k = 0; k < 10; k++) {
-      const double s = warp_sum(v[k]);
-      if ((threadIdx.x & 31) == 0) atomicAdd(a.sums + (long long)y * 10 + k, s);
-    }
+  for (int k = 0; k < K; k++) {
+    const double v = warp_sum((double)acc[k]);
+    if ((threadIdx.x & 31) == 0) red[k][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+    const int k = threadIdx.x;
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < NW; w++) t += red[k][w];
+    partial[((long long)z * p.ny + y) * K + k] = t;
   }
 }
 
-// FP64 sums over fluid cells: MODE EX_SUM -> sums[0..3] = (rho, rho u); MODE EX_STATS ->
-// per y plane, sums[y*10 + k] = (count, u, u^2 components, u_x u_y, u_x u_z, u_y u_z).
-// Grid (ny, z chunks) of 128-thread blocks; each block walks whole rows of one y plane (a warp
-// covers 32 aligned x, as the outflow shuffle needs), reduces in the block and adds once.
-template <int Q, class S, int PAR, int MODE>
-__global__ void __launch_bounds__(128) k_plane_sums(const __grid_constant__ KParams p, double* sums, int zchunk) {
-  constexpr int K = MODE == EX_SUM ? 4 : 10;
-  const int y = blockIdx.x;
-  const int z0 = blockIdx.y * zchunk, z1 = min(p.nz, z0 + zchunk);
+// EX_STATS: one block per plane y (its nz rows); EX_SUM: one block for all rows.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_row_total(const double* partial, int ny, int nz, double* sums) {
+  constexpr int K = row_k<MODE>();
   double acc[K];
 #pragma unroll
   for (int k = 0; k < K; k++) acc[k] = 0.0;
-  for (int z = z0; z < z1; z++) {
-    for (int xb = 0; xb < p.nxp; xb += 128) {
-      const int x = xb + threadIdx.x;
-      const bool in = x < p.nxp;
-      const int cell = in ? cidx(p, x, y, z) : 0;
-      const int cls = (in && x < p.nx) ? p.cls[cell] : CLS_SKIP;
-      float f[Q];
-      unsigned outmask;
-      load_state<Q, S, PAR>(p, x, y, z, cell, cls, f, outmask);
-      outflow_fix<Q>(p, x, f, outmask);
-      if (cls == CLS_SKIP) continue;
-      const Mom<Q> m = moments<Q>(p, f);
-      if (MODE == EX_SUM) {
-        const double r = m.rho;
-        acc[0] += r;
-        acc[1] += r * m.ux;
-        acc[2] += r * m.uy;
-        acc[3] += r * m.uz;
-      } else {
-        const double ux = m.ux, uy = m.uy, uz = m.uz;
-        const double v[10] = {1.0, ux, uy, uz, ux * ux, uy * uy, uz * uz, ux * uy, ux * uz, uy * uz};
+  if (MODE == EX_STATS) {
+    const int y = blockIdx.x;
+    for (int z = threadIdx.x; z < nz; z += blockDim.x) {
 #pragma unroll
-        for (int k = 0; k < K; k++) acc[k] += v[k];
-      }
+      for (int k = 0; k < K; k++) acc[k] += partial[((long long)z * ny + y) * K + k];
+    }
+  } else {
+    const long long nrow = (long long)ny * nz;
+    for (long long r = threadIdx.x; r < nrow; r += blockDim.x) {
+#pragma unroll
+      for (int k = 0; k < K; k++) acc[k] += partial[r * K + k];
     }
   }
-  __shared__ double red[K][4];
+  __shared__ double red[K][8];
 #pragma unroll
   for (int k = 0; k < K; k++) {
     const double v = warp_sum(acc[k]);
@@ -868,9 +923,18 @@ __global__ void __launch_bounds__(128) k_plane_sums(const __grid_constant__ KPar
   }
   __syncthreads();
   if (threadIdx.x < K) {
-    const double v = red[threadIdx.x][0] + red[threadIdx.x][1] + red[threadIdx.x][2] + red[threadIdx.x][3];
-    if (MODE == EX_SUM) atomicAdd(sums + threadIdx.x, v);
-    else atomicAdd(sums + (long long)y * 10 + threadIdx.x, v);
+    const int k = threadIdx.x;
+    double t = 0.0;
+    for (int w = 0; w < 8; w++) t += red[k][w];
+    if (MODE == EX_STATS) {
+      sums[blockIdx.x * 10 + k] += t;
+    } else if (k == 0) {
+      double t1 = 0.0;
+      for (int w = 0; w < 8; w++) t1 += red[1][w];
+      sums[0] = t + t1;  // count + sum drho
+    } else if (k >= 2) {
+      sums[k - 1] = t;
+    }
   }
 }
 
