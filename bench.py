@@ -179,8 +179,9 @@ def _channel_lattice(nx, ny, nz, precision, closure="smag", streaming="pull"):
 
 def _time_steps(lat, steps, warmup, dist, stats_every=0):
     """Device time of `steps` single-launch steps (CUDA events on the handle's stream); with
-    stats_every > 0 the FP64 profile statistics are sampled every that many steps inside the
-    timed region (the turbulent-channel job accumulates mean and RMS profiles)."""
+    stats_every > 0 the profile statistics of the state every stats_every-th step starts from
+    are sampled inside the timed region (the turbulent-channel job accumulates mean and RMS
+    profiles), by that step's own kernel (lbm_step_stats)."""
     import torch
 
     from paper_2305_09910_gb300 import lbm
@@ -201,10 +202,11 @@ def _time_steps(lat, steps, warmup, dist, stats_every=0):
     t0.record(stream)
     for k in range(steps):
         starts[k].record(stream)
-        lbm.lbm_step(lat.h, 1)
+        if stats_every and k % stats_every == 0:
+            lbm.lbm_step_stats(lat.h, 1, 1)
+        else:
+            lbm.lbm_step(lat.h, 1)
         ends[k].record(stream)
-        if stats_every and (k + 1) % stats_every == 0:
-            lbm.lbm_stats_sample(lat.h)
     t1.record(stream)
     torch.cuda.synchronize()
     if dist is not None:
@@ -450,7 +452,7 @@ def main():
            "config": {"workload": workload, "storage": args.form, "nx": nx, "ny": ny, "nz": nz, "stencil": 19,
                       "tau": round(par["tau"], 6), "force": par["force"], "cs_smag": 0.1,
                       "global_batch": world * ncell, "parallelism": f"replicas x{world}",
-                      "stats": "FP64 mean/RMS profile sample every 10 steps, inside the timed region",
+                      "stats": "mean/RMS profile sample (FP64 plane sums) every 10 steps, taken by the step kernel, inside the timed region",
                       "l2": f"inputs larger than L2 ({lat_bytes / 1e9:.2f} GB population array vs 129 MB L2)"},
            "roofline": roof, "e2e": e2e, "gpu_launches": args.steps + args.steps // 10,
            "clocks": clocks.summary(), "mass_after": mass, "forms": forms}

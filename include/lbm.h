@@ -184,10 +184,21 @@ lbm_status lbm_set_populations(lbm_handle h, const float* df, int on_device);
 lbm_status lbm_reduce(lbm_handle h, double out[4]);
 
 /* Turbulence statistics in FP64, per y plane (LBM_STATS_K values each, see above):
- * reset, add one sample of the current state, read ny*LBM_STATS_K doubles (host). */
+ * reset, add one sample of the current state, read ny*LBM_STATS_K doubles (host).  What the
+ * channel assesses (Sec. 4.1): mean and fluctuation profiles over the homogeneous x-z planes.
+ * Per-cell values are float32 (the moments of lbm_moments); sums are FP64. */
 lbm_status lbm_stats_reset(lbm_handle h);
 lbm_status lbm_stats_sample(lbm_handle h);
 lbm_status lbm_stats_get(lbm_handle h, double* out, int64_t* nsamples);
+
+/* Advances n >= 0 steps like lbm_step and adds one statistics sample of the state that each
+ * step k = 0, every, 2 every, ... (k counted from this call, every >= 1) starts from, i.e.
+ * ceil(n / every) samples.  With the direct pipeline and no learned closure the sample is
+ * taken by that step's own kernel (per-warp float32 sums of 32 or 64 cells, then FP64 plane
+ * sums), so sampling adds no pass over the populations; otherwise a separate pass runs
+ * before the step.  Per-warp partial sums live in a scratch array allocated on the first
+ * call (10 floats per warp slot, about 1.25 bytes per cell).  EINVAL for n < 0 or every < 1. */
+lbm_status lbm_step_stats(lbm_handle h, int64_t n, int64_t every);
 
 /* MLP closure parameters (host, bfloat16 bit patterns, n == LBM_MLP_NPARAM) and feature
  * scales.  Needed before stepping with closure LBM_CLOSURE_MLP. */

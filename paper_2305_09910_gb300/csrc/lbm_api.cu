@@ -32,6 +32,7 @@ struct lbm_s {
   int* status_host = nullptr; // pinned copy
   double* sums = nullptr;     // 4 doubles (lbm_reduce)
   double* partial = nullptr;  // nz * ny * 10 doubles: per-row sums of the reductions
+  float* stats_w = nullptr;   // per-warp plane statistics of sampling steps (allocated on first use)
   double* stats = nullptr;    // ny * LBM_STATS_K doubles
   float* mlp = nullptr;       // MLP parameters widened to float
   float mlp_scale[2] = {0.f, 0.f};
@@ -109,6 +110,7 @@ static KParams kparams(const lbm_s* h) {
   p.flags = h->flags;
   p.cls = h->cls;
   p.rules = h->rules;
+  p.stats_w = h->stats_w;
   p.mlp = h->mlp;
   p.status = h->status;
   p.plane = plane_of(h);
@@ -142,8 +144,15 @@ static KParams kparams(const lbm_s* h) {
   return p;
 }
 
+// True when the step kernel of this handle can sample the statistics itself (direct loads,
+// no learned closure); the other forms sample them in a separate pass before the step.
+static bool fused_stats(const lbm_s* h) {
+  return h->prm.pipeline == LBM_PIPE_DIRECT && h->prm.closure != LBM_CLOSURE_MLP;
+}
+
 template <int Q>
-static cudaError_t dispatch_step(const lbm_s* h, const KParams& p, int closure, int parity) {
+static cudaError_t dispatch_step(const lbm_s* h, const KParams& p, int closure, int parity, bool stats = false,
+                                 int* nws = nullptr) {
   const Launch L = launch_cfg(h);
   if (closure == CL_MLP) {  // one kernel for every pipeline: the tensor-core closure step
     const int mode = h->prm.streaming == LBM_PULL ? (parity == 0 ? 2 : 3) : parity;
@@ -155,6 +164,13 @@ static cudaError_t dispatch_step(const lbm_s* h, const KParams& p, int closure, 
   }
   if (h->prm.streaming == LBM_PULL) {  // direct or staged loads
     const int mode = parity == 0 ? 2 : 3;
+    if (stats) {
+      switch (h->prm.precision) {
+        case LBM_F32: return launch_step<Q, float>(p, closure, mode, L, true, nws);
+        case LBM_F16_SHIFTED: return launch_step<Q, __half>(p, closure, mode, L, true, nws);
+        default: return launch_step<Q, __nv_bfloat16>(p, closure, mode, L, true, nws);
+      }
+    }
     if (h->prm.pipeline == LBM_PIPE_ASYNC) {
       switch (h->prm.precision) {
         case LBM_F32: return launch_step_async<Q, float>(p, closure, mode, L);
@@ -163,9 +179,9 @@ static cudaError_t dispatch_step(const lbm_s* h, const KParams& p, int closure, 
       }
     }
     switch (h->prm.precision) {
-      case LBM_F32: return launch_step<Q, float>(p, closure, mode, L);
-      case LBM_F16_SHIFTED: return launch_step<Q, __half>(p, closure, mode, L);
-      default: return launch_step<Q, __nv_bfloat16>(p, closure, mode, L);
+      case LBM_F32: return launch_step<Q, float>(p, closure, mode, L, false, nullptr);
+      case LBM_F16_SHIFTED: return launch_step<Q, __half>(p, closure, mode, L, false, nullptr);
+      default: return launch_step<Q, __nv_bfloat16>(p, closure, mode, L, false, nullptr);
     }
   }
   if (h->prm.pipeline == LBM_PIPE_ASYNC) {
@@ -190,9 +206,9 @@ static cudaError_t dispatch_step(const lbm_s* h, const KParams& p, int closure, 
     }
   }
   switch (h->prm.precision) {
-    case LBM_F32: return launch_step<Q, float>(p, closure, parity, L);
-    case LBM_F16_SHIFTED: return launch_step<Q, __half>(p, closure, parity, L);
-    default: return launch_step<Q, __nv_bfloat16>(p, closure, parity, L);
+    case LBM_F32: return launch_step<Q, float>(p, closure, parity, L, stats, nws);
+    case LBM_F16_SHIFTED: return launch_step<Q, __half>(p, closure, parity, L, stats, nws);
+    default: return launch_step<Q, __nv_bfloat16>(p, closure, parity, L, stats, nws);
   }
 }
 
@@ -352,6 +368,7 @@ lbm_status lbm_destroy(lbm_handle h) {
   if (h->status) cudaFreeAsync(h->status, h->stream);
   if (h->sums) cudaFreeAsync(h->sums, h->stream);
   if (h->partial) cudaFreeAsync(h->partial, h->stream);
+  if (h->stats_w) cudaFreeAsync(h->stats_w, h->stream);
   if (h->stats) cudaFreeAsync(h->stats, h->stream);
   if (h->mlp) cudaFreeAsync(h->mlp, h->stream);
   cudaStreamSynchronize(h->stream);
@@ -551,17 +568,40 @@ lbm_status lbm_set_populations(lbm_handle h, const float* df, int on_device) {
   return reset_status(h);
 }
 
-lbm_status lbm_step(lbm_handle h, int64_t n) {
-  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
-  if (n < 0) return fail(h, LBM_EINVAL, "n must be >= 0");
+static lbm_status run_export(lbm_handle h, int mode, const ExportArgs& a);
+
+// n steps; with every > 0 the plane statistics of the state each step k (k % every == 0)
+// starts from are added to the accumulated sums, inside that step's kernel where it can.
+static lbm_status run_steps(lbm_handle h, int64_t n, int64_t every) {
   if (h->prm.closure == LBM_CLOSURE_MLP && !h->mlp_set)
     return fail(h, LBM_ESTATE, "MLP closure selected but lbm_set_closure was not called");
+  if (every > 0 && fused_stats(h) && !h->stats_w) {
+    const size_t slots = (size_t)((h->nxp + 31) / 32) * h->ny * h->nz;
+    CUDA_TRY(h, cudaMallocAsync((void**)&h->stats_w, slots * 10 * sizeof(float), h->stream));
+  }
   KParams p = kparams(h);
   for (int64_t k = 0; k < n; k++) {
     p.nat_valid = h->nat_valid;
-    cudaError_t e = h->q == 19 ? dispatch_step<19>(h, p, h->prm.closure, h->parity)
-                               : dispatch_step<27>(h, p, h->prm.closure, h->parity);
+    const bool sample = every > 0 && k % every == 0;
+    bool fused = false;
+    if (sample && !fused_stats(h)) {
+      ExportArgs a{};
+      a.sums = h->stats;
+      a.partial = h->partial;
+      lbm_status s = run_export(h, EX_STATS, a);
+      if (s != LBM_OK) return s;
+    } else if (sample) {
+      fused = true;
+    }
+    int nws = 0;
+    cudaError_t e = h->q == 19 ? dispatch_step<19>(h, p, h->prm.closure, h->parity, fused, &nws)
+                               : dispatch_step<27>(h, p, h->prm.closure, h->parity, fused, &nws);
     CUDA_TRY(h, e);
+    if (fused) {
+      k_stats_total<<<(unsigned)h->ny, 256, 0, h->stream>>>(h->stats_w, h->ny, h->nz, nws, h->stats);
+      CUDA_TRY(h, cudaGetLastError());
+    }
+    if (sample) h->nsamples++;
     if (h->prm.streaming == LBM_PULL) {  // the destination array holds the new state
       h->cur ^= 1;
       h->parity = 2;
@@ -572,6 +612,19 @@ lbm_status lbm_step(lbm_handle h, int64_t n) {
     }
   }
   return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_handle h, int64_t n) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (n < 0) return fail(h, LBM_EINVAL, "n must be >= 0");
+  return run_steps(h, n, 0);
+}
+
+lbm_status lbm_step_stats(lbm_handle h, int64_t n, int64_t every) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (n < 0) return fail(h, LBM_EINVAL, "n must be >= 0");
+  if (every < 1) return fail(h, LBM_EINVAL, "every must be >= 1");
+  return run_steps(h, n, every);
 }
 
 lbm_status lbm_sync(lbm_handle h) {

@@ -78,22 +78,32 @@ __device__ __forceinline__ void xsrc(int c, const KParams& p, int x, int cell, i
 
 // One-cell code for both cells of a lane (warps with a non-interior cell).  Kept out of
 // line so that the rare path does not take registers from the fast one.
-template <int Q, class S, int CL, int LOAD, int STORE>
-__device__ __noinline__ void pair_fallback(const KParams& p, int x, int y, int z, int cell, int clsA, int clsB) {
+template <int Q, class S, int CL, int LOAD, int STORE, bool STATS>
+__device__ __noinline__ void pair_fallback(const KParams& p, int x, int y, int z, int cell, int clsA, int clsB,
+                                           float (&v)[NSTAT]) {
   float fa[Q], fb[Q];
   unsigned oa, ob;
   load_state<Q, S, LOAD>(p, x, y, z, cell, clsA, fa, oa);
   load_state<Q, S, LOAD>(p, x + 1, y, z, cell + 1, clsB, fb, ob);
   outflow_fix2<Q>(p, 64 * blockIdx.x, fa, fb, oa, ob);
   if (clsA != CLS_SKIP) {
-    const float r = collide<Q, CL, float, false>(p, fa);
+    Macro<float> M;
+    const float r = collide<Q, CL, float, false>(p, fa, STATS ? &M : nullptr);
     if (!(r > 0.f && r < 3.0e38f)) atomicOr(p.status, 1);
     store_state<Q, S, STORE>(p, x, y, z, cell, clsA, fa);
+    if (STATS) stat_values(M, v);
   }
   if (clsB != CLS_SKIP) {
-    const float r = collide<Q, CL, float, false>(p, fb);
+    Macro<float> M;
+    const float r = collide<Q, CL, float, false>(p, fb, STATS ? &M : nullptr);
     if (!(r > 0.f && r < 3.0e38f)) atomicOr(p.status, 1);
     store_state<Q, S, STORE>(p, x + 1, y, z, cell + 1, clsB, fb);
+    if (STATS) {
+      float w[NSTAT];
+      stat_values(M, w);
+#pragma unroll
+      for (int k = 0; k < NSTAT; k++) v[k] += w[k];
+    }
   }
 }
 
@@ -103,7 +113,9 @@ __device__ __noinline__ void pair_fallback(const KParams& p, int x, int y, int z
 #ifndef LBM_H2_MINB
 #define LBM_H2_MINB (LBM_H2_VEC ? 7 : 8)
 #endif
-template <int Q, class S, int CL, int LOAD, int STORE>
+// STATS: also write the plane statistics of the state this step starts from (warp slot
+// blockIdx.x of each row, ceil(nxp/64) slots per row).
+template <int Q, class S, int CL, int LOAD, int STORE, bool STATS = false>
 __global__ void __launch_bounds__(128, LBM_H2_MINB) k_step_h2(const __grid_constant__ KParams p) {
   static_assert(sizeof(S) == 2, "two 16-bit populations per word");
   const int x = 2 * (blockIdx.x * 32 + threadIdx.x);
@@ -120,6 +132,9 @@ __global__ void __launch_bounds__(128, LBM_H2_MINB) k_step_h2(const __grid_const
   const int clsA = ca_, clsB = cb_;
   const bool fast = LOAD == 0 ? ((clsA == CLS_INTERIOR || clsA == CLS_WRAP) && (clsB == CLS_INTERIOR || clsB == CLS_WRAP))
                               : (clsA == CLS_INTERIOR && clsB == CLS_INTERIOR);
+  float v[NSTAT];
+#pragma unroll
+  for (int k = 0; k < NSTAT; k++) v[k] = 0.f;
   if (__all_sync(0xffffffffu, fast)) {
     uint32_t h[Q];
 #pragma unroll
@@ -144,22 +159,41 @@ __global__ void __launch_bounds__(128, LBM_H2_MINB) k_step_h2(const __grid_const
     float2 f[Q];
 #pragma unroll
     for (int i = 0; i < Q; i++) f[i] = make_float2(lo_of<S>(h[i]), hi_of<S>(h[i]));
-    const float2 rho = collide<Q, CL, float2, false>(p, f);
+    Macro<float2> M2;
+    const float2 rho = collide<Q, CL, float2, false>(p, f, STATS ? &M2 : nullptr);
+    if (STATS) {
+      float va[NSTAT], vb[NSTAT];
+      Macro<float> Ma, Mb;
+      Ma.ux = M2.ux.x; Ma.uy = M2.uy.x; Ma.uz = M2.uz.x;
+      Mb.ux = M2.ux.y; Mb.uy = M2.uy.y; Mb.uz = M2.uz.y;
+      stat_values(Ma, va);
+      stat_values(Mb, vb);
+#pragma unroll
+      for (int k = 0; k < NSTAT; k++) v[k] = va[k] + vb[k];
+    }
 #pragma unroll
     for (int i = 0; i < Q; i++) h[i] = pack2<S>(f[i].x, f[i].y);
     const float ra = rho.x, rb = rho.y;
 #else
     // first cell: unpack, collide, round back into the low halves
     float f[Q];
+    Macro<float> Ma, Mb;
 #pragma unroll
     for (int i = 0; i < Q; i++) f[i] = lo_of<S>(h[i]);
-    const float ra = collide<Q, CL, float, false>(p, f);
+    const float ra = collide<Q, CL, float, false>(p, f, STATS ? &Ma : nullptr);
 #pragma unroll
     for (int i = 0; i < Q; i++) h[i] = __byte_perm(h[i], bits16<S>(f[i]), 0x3254);
     // second cell: the high halves
 #pragma unroll
     for (int i = 0; i < Q; i++) f[i] = hi_of<S>(h[i]);
-    const float rb = collide<Q, CL, float, false>(p, f);
+    const float rb = collide<Q, CL, float, false>(p, f, STATS ? &Mb : nullptr);
+    if (STATS) {
+      float va[NSTAT], vb[NSTAT];
+      stat_values(Ma, va);
+      stat_values(Mb, vb);
+#pragma unroll
+      for (int k = 0; k < NSTAT; k++) v[k] = va[k] + vb[k];
+    }
 #pragma unroll
     for (int i = 0; i < Q; i++) h[i] = __byte_perm(h[i], bits16<S>(f[i]), 0x5410);
 #endif
@@ -172,20 +206,21 @@ __global__ void __launch_bounds__(128, LBM_H2_MINB) k_step_h2(const __grid_const
         *reinterpret_cast<uint32_t*>(static_cast<S*>(p.fq[i]) + cell) = h[i];
       } else {  // back into the slots the gather of direction i read: f*_opp(i)
         S* base = static_cast<S*>(p.ga[i]);
-        const uint32_t v = h[opp(i)];
+        const uint32_t w = h[opp(i)];
         if (cx(i) == 0) {
-          *reinterpret_cast<uint32_t*>(base + cell) = v;
+          *reinterpret_cast<uint32_t*>(base + cell) = w;
         } else {
           int a, b;
           xsrc(cx(i), p, x, cell, a, b);
-          *reinterpret_cast<unsigned short*>(base + a) = (unsigned short)(v & 0xffffu);
-          *reinterpret_cast<unsigned short*>(base + b) = (unsigned short)(v >> 16);
+          *reinterpret_cast<unsigned short*>(base + a) = (unsigned short)(w & 0xffffu);
+          *reinterpret_cast<unsigned short*>(base + b) = (unsigned short)(w >> 16);
         }
       }
     }
-    return;
+  } else {
+    pair_fallback<Q, S, CL, LOAD, STORE, STATS>(p, x, y, z, cell, clsA, clsB, v);
   }
-  pair_fallback<Q, S, CL, LOAD, STORE>(p, x, y, z, cell, clsA, clsB);
+  if (STATS) stat_warp_store(p, y, z, blockIdx.x, (p.nxp + 63) / 64, v);
 }
 
 }  // namespace lbm

@@ -83,6 +83,7 @@ struct KParams {
   const unsigned long long* rules;
   const float* mlp;      // MLP parameters (bf16 values widened to float), device
   int* status;           // bit 0: non-finite or non-positive density seen
+  float* stats_w;        // sampling steps: per-warp plane sums, [(z ny + y) nws + ws][10]
   long long plane;       // nxp * ny * nz
   int nx, ny, nz, nxp;
   int outflow;           // +x face is an outflow
@@ -396,31 +397,6 @@ struct Mom {
   float drho, rho, jx, jy, jz, ux, uy, uz;  // j = sum c df + F/2 = rho u
 };
 
-// Moments from the populations (used by the exports; the collision forms them from pair
-// sums).  Reciprocal of rho with the fast approximate division (relative error < 2^-22).
-template <int Q>
-__device__ __forceinline__ Mom<Q> moments(const KParams& p, const float (&f)[Q]) {
-  float d = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-  for (int i = 0; i < Q; i++) {
-    d += f[i];
-    if (cx(i)) jx += cx(i) > 0 ? f[i] : -f[i];
-    if (cy(i)) jy += cy(i) > 0 ? f[i] : -f[i];
-    if (cz(i)) jz += cz(i) > 0 ? f[i] : -f[i];
-  }
-  Mom<Q> m;
-  m.drho = d;
-  m.rho = 1.f + d;
-  m.jx = jx + 0.5f * p.F[0];
-  m.jy = jy + 0.5f * p.F[1];
-  m.jz = jz + 0.5f * p.F[2];
-  const float inv = __fdividef(1.f, m.rho);
-  m.ux = m.jx * inv;
-  m.uy = m.jy * inv;
-  m.uz = m.jz * inv;
-  return m;
-}
-
 // ---- arithmetic, written for a value type V (float: one cell, float2: two cells per thread) ---
 // Every operation rounds once to nearest even and none is contracted by the compiler, so every
 // kernel form (direct, staged, x-pair, closure) gives a cell the same bits.
@@ -647,6 +623,23 @@ __device__ __forceinline__ Macro<V> macro(const KParams& p, const V (&f)[Q]) {
   return M;
 }
 
+// Moments of one cell for the exports: the collision's macroscopic fields, so an export and
+// the statistics sampled inside a step see the same per-cell values.
+template <int Q>
+__device__ __forceinline__ Mom<Q> moments(const KParams& p, const float (&f)[Q]) {
+  const Macro<float> M = macro<Q, false, float>(p, f);
+  Mom<Q> m;
+  m.drho = M.drho;
+  m.rho = M.rho;
+  m.jx = M.jx;
+  m.jy = M.jy;
+  m.jz = M.jz;
+  m.ux = M.ux;
+  m.uy = M.uy;
+  m.uz = M.uz;
+  return m;
+}
+
 // TRT relaxation with Guo forcing at the rates omega+ (wp) and omega- (wm), in place.
 // ACC: the accurate pair update (float32 storage) or the lean one (half storage).
 template <int Q, class V, bool ACC>
@@ -707,10 +700,11 @@ __device__ __forceinline__ void relax(const KParams& p, V (&f)[Q], const Macro<V
 // Stream-collide arithmetic of one cell (or two) without a learned closure: plain TRT or
 // TRT with the Smagorinsky relaxation time.  Returns rho.
 template <int Q, int CL, class V, bool ACC = true>
-__device__ __forceinline__ V collide(const KParams& p, V (&f)[Q]) {
+__device__ __forceinline__ V collide(const KParams& p, V (&f)[Q], Macro<V>* mout = nullptr) {
   static_assert(CL != CL_MLP, "the learned closure has its own kernel");
   using L = Lanes<V>;
   const Macro<V> M = macro<Q, CL != CL_NONE, V>(p, f);
+  if (mout) *mout = M;
   V wp = vset<V>(p.omega_p), wm = vset<V>(p.omega_m);
   if (CL != CL_NONE) {
 #pragma unroll
@@ -737,17 +731,90 @@ __device__ __forceinline__ V collide(const KParams& p, V (&f)[Q]) {
 
 // LOAD / STORE modes as in load_state / store_state: AA even (0, 0), AA odd (1, 1), first
 // pull step after an import (0, 2), pull step (2, 2).
-template <int Q, class S, int CL, int LOAD, int STORE>
+// ---- turbulence statistics sampled inside a step ----------------------------------------
+// The 10 per-cell values of the plane statistics (count, u, u_a u_b) of the state a step
+// starts from: u = j / rho of its macroscopic fields, so they equal those of the export.
+constexpr int NSTAT = 10;
+
+__device__ __forceinline__ void stat_values(const Macro<float>& M, float (&v)[NSTAT]) {
+  v[0] = 1.f;
+  v[1] = M.ux;
+  v[2] = M.uy;
+  v[3] = M.uz;
+  v[4] = M.ux * M.ux;
+  v[5] = M.uy * M.uy;
+  v[6] = M.uz * M.uz;
+  v[7] = M.ux * M.uy;
+  v[8] = M.ux * M.uz;
+  v[9] = M.uy * M.uz;
+}
+
+// Sum of v over the warp (FP32) written by lane 0 to the warp's slot ws of row (y, z).
+__device__ __forceinline__ void stat_warp_store(const KParams& p, int y, int z, int ws, int nws,
+                                                float (&v)[NSTAT]) {
+#pragma unroll
+  for (int k = 0; k < NSTAT; k++) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    float* dst = p.stats_w + (((long long)z * p.ny + y) * nws + ws) * NSTAT;
+#pragma unroll
+    for (int k = 0; k < NSTAT; k++) dst[k] = v[k];
+  }
+}
+
+// Plane sums of the sampled statistics: sums[y * 10 + k] += sum over z and the nws warp
+// slots of each row (FP64).  One block per plane y.
+static __global__ void __launch_bounds__(256) k_stats_total(const float* stats_w, int ny, int nz, int nws, double* sums) {
+  const int y = blockIdx.x;
+  double acc[NSTAT];
+#pragma unroll
+  for (int k = 0; k < NSTAT; k++) acc[k] = 0.0;
+  const long long n = (long long)nz * nws;
+  for (long long r = threadIdx.x; r < n; r += blockDim.x) {
+    const long long z = r / nws, ws = r % nws;
+    const float* src = stats_w + ((z * ny + y) * nws + ws) * NSTAT;
+#pragma unroll
+    for (int k = 0; k < NSTAT; k++) acc[k] += (double)src[k];
+  }
+  __shared__ double red[NSTAT][8];
+#pragma unroll
+  for (int k = 0; k < NSTAT; k++) {
+    double v = acc[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NSTAT) {
+    double t = 0.0;
+    for (int w = 0; w < 8; w++) t += red[threadIdx.x][w];
+    sums[y * NSTAT + threadIdx.x] += t;
+  }
+}
+
+// STATS: also write the plane statistics of the state this step starts from (warp slot
+// blockIdx.x of each row, nxp/32 slots per row).
+template <int Q, class S, int CL, int LOAD, int STORE, bool STATS = false>
 __global__ void __launch_bounds__(128, 8) k_step(const __grid_constant__ KParams p) {
   LBM_CELL_COORDS
   float f[Q];
   unsigned outmask;
   load_state<Q, S, LOAD>(p, x, y, z, cell, cls, f, outmask);
   outflow_fix<Q>(p, x, f, outmask);
-  if (cls == CLS_SKIP) return;
-  const float rho = collide<Q, CL, float, acc_form<S>>(p, f);
-  if (!(rho > 0.f && rho < 3.0e38f)) atomicOr(p.status, 1);
-  store_state<Q, S, STORE>(p, x, y, z, cell, cls, f);
+  if (!STATS && cls == CLS_SKIP) return;
+  float v[NSTAT];
+#pragma unroll
+  for (int k = 0; k < NSTAT; k++) v[k] = 0.f;
+  if (cls != CLS_SKIP) {
+    Macro<float> M;
+    const float rho = collide<Q, CL, float, acc_form<S>>(p, f, STATS ? &M : nullptr);
+    if (!(rho > 0.f && rho < 3.0e38f)) atomicOr(p.status, 1);
+    store_state<Q, S, STORE>(p, x, y, z, cell, cls, f);
+    if (STATS) stat_values(M, v);
+  }
+  if (STATS) stat_warp_store(p, y, z, blockIdx.x, p.nxp / 32, v);
 }
 
 // The same step with register double-buffering along z: each thread updates ZC cells
@@ -846,7 +913,7 @@ __global__ void __launch_bounds__(128) k_export(const __grid_constant__ KParams 
 template <int MODE>
 __host__ __device__ constexpr int row_k() { return MODE == EX_SUM ? 5 : 10; }
 
-constexpr int ROW_THREADS = 256;
+constexpr int ROW_THREADS = 128;
 
 template <int Q, class S, int PAR, int MODE>
 __global__ void __launch_bounds__(ROW_THREADS) k_row_sums(const __grid_constant__ KParams p, double* partial) {

@@ -16,7 +16,8 @@ struct Launch {
 };
 
 template <int Q, class S>
-cudaError_t launch_step(const KParams& p, int closure, int parity, const Launch& L);
+cudaError_t launch_step(const KParams& p, int closure, int parity, const Launch& L, bool stats = false,
+                        int* nws = nullptr);
 template <int Q, class S>
 cudaError_t launch_step_tma(const KParams& p, int closure, int parity, cudaStream_t stream, int nsm);
 template <int Q, class S>
@@ -33,7 +34,7 @@ template <int Q, class S>
 cudaError_t launch_set_pop(const KParams& p, const float* df, const Launch& L);
 
 #define LBM_DECLARE_INSTANCE(Q, S)                                                                 \
-  extern template cudaError_t launch_step<Q, S>(const KParams&, int, int, const Launch&);          \
+  extern template cudaError_t launch_step<Q, S>(const KParams&, int, int, const Launch&, bool, int*); \
   extern template cudaError_t launch_step_tma<Q, S>(const KParams&, int, int, cudaStream_t, int);  \
   extern template cudaError_t launch_step_zp<Q, S>(const KParams&, int, int, const Launch&);       \
   extern template cudaError_t launch_step_async<Q, S>(const KParams&, int, int, const Launch&);    \

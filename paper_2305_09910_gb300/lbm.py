@@ -89,6 +89,7 @@ def load():
             "lbm_reduce": (I, [H, P]),
             "lbm_stats_reset": (I, [H]),
             "lbm_stats_sample": (I, [H]),
+            "lbm_step_stats": (I, [H, ctypes.c_int64, ctypes.c_int64]),
             "lbm_stats_get": (I, [H, P, ctypes.POINTER(ctypes.c_int64)]),
             "lbm_set_closure": (I, [H, P, I, D, D]),
             "lbm_info": (I, [H, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]),
@@ -252,6 +253,10 @@ def lbm_stats_reset(h):
 
 def lbm_stats_sample(h):
     _check(load().lbm_stats_sample(h), h)
+
+
+def lbm_step_stats(h, n: int, every: int):
+    _check(load().lbm_step_stats(h, int(n), int(every)), h)
 
 
 def lbm_stats_get(h, ny: int):

@@ -470,3 +470,54 @@ def test_pull_and_aa_agree_bit_for_bit(precision):
         a.step(n)
         b.step(n)
         assert np.array_equal(a.get_populations(), b.get_populations())
+
+
+@pytest.mark.parametrize("precision", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("streaming", ["aa", "pull"])
+@pytest.mark.parametrize("pipeline", ["direct", "tma"])
+def test_step_stats_matches_sampling_between_steps(precision, streaming, pipeline):
+    """lbm_step_stats(n, every) (sampled inside the step kernel on the direct pipeline, by a
+    separate pass otherwise) = a loop of lbm_stats_sample before every every-th lbm_step."""
+    from paper_2305_09910_gb300 import inputs, lbm
+
+    if pipeline == "tma" and streaming == "pull":
+        pytest.skip("the staged pipelines serve the AA pattern")
+    nx, ny, nz, n, every = 100, 18, 12, 7, 3   # ragged warps in x, wall rows, 3 samples
+    kw = dict(tau=0.56, closure="smag", cs_smag=0.12, faces=FACES_CHANNEL, precision=precision,
+              streaming=streaming, pipeline=pipeline)
+    a = lbm.Lattice(nx, ny, nz, **kw)
+    b = lbm.Lattice(nx, ny, nz, **kw)
+    rho, u = inputs.channel_init(nx, ny, nz, u_bulk=0.05, seed=31)
+    for lat in (a, b):
+        lat.set_force(2e-6)
+        lat.init_equilibrium(rho, u)
+        lat.step(2)
+        lbm.lbm_stats_reset(lat.h)
+    lbm.lbm_step_stats(a.h, n, every)
+    for k in range(n):
+        if k % every == 0:
+            lbm.lbm_stats_sample(b.h)
+        b.step(1)
+    a.sync()
+    b.sync()
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    sa, na = lbm.lbm_stats_get(a.h, ny)
+    sb, nb = lbm.lbm_stats_get(b.h, ny)
+    assert na == nb == 3
+    assert np.array_equal(sa[:, 0], sb[:, 0])
+    assert sa[0, 0] == 3 * nx * nz
+    assert np.abs(sa - sb).max() <= 1e-6 * nx * nz * 3
+
+
+def test_step_stats_rejects_bad_arguments():
+    from paper_2305_09910_gb300 import lbm
+
+    lat = lbm.Lattice(40, 6, 4)
+    lat.init_equilibrium()
+    for n, every in ((-1, 1), (3, 0)):
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_step_stats(lat.h, n, every)
+        assert e.value.status == lbm.LBM_EINVAL
+    lbm.lbm_step_stats(lat.h, 0, 5)
+    _, ns = lbm.lbm_stats_get(lat.h, 6)
+    assert ns == 0
