@@ -177,6 +177,39 @@ def _channel_lattice(nx, ny, nz, precision, closure="smag", streaming="pull"):
     return lat, par
 
 
+def _bluff_lattice(nx, ny, nz, precision, streaming="pull"):
+    """The landing-gear tunnel of the bluff-body form (D3Q27 TRT + Smagorinsky, inflow 0.05 at
+    x = 0, outflow at x = nx-1, free-slip y/z), geometry scaled by nx / 768, started from the
+    uniform inflow state."""
+    import torch
+
+    from paper_2305_09910_gb300 import inputs, lbm
+
+    scale = nx / 768
+    tau = 0.5 + 3 * 0.05 * (80 * scale) / 1e4
+    lat = lbm.Lattice(nx, ny, nz, stencil=27, tau=tau, precision=precision, closure="smag", cs_smag=0.1,
+                      faces=("inflow", "outflow", "freeslip", "freeslip", "freeslip", "freeslip"),
+                      u_inflow=(0.05, 0.0, 0.0), streaming=streaming)
+    lat.set_flags(torch.from_numpy(inputs.landing_gear_flags(nx, ny, nz, scale=scale)).cuda())
+    u = torch.zeros((3, nz, ny, nx), dtype=torch.float32, device="cuda")
+    u[0] = 0.05
+    lat.init_equilibrium(None, u)
+    del u
+    return lat, {"tau": tau, "force": 0.0}
+
+
+def _closure_params():
+    """Network weights of the learned-closure form (fixed seed; the cost of the fused inference
+    does not depend on them)."""
+    import numpy as np
+
+    from paper_2305_09910_gb300 import closure
+
+    params = closure.init_params(7)
+    params[closure.OUT_LAYER] = np.random.default_rng(7).normal(0, 0.1, 33).astype(np.float32)
+    return params
+
+
 def _time_steps(lat, steps, warmup, dist, stats_every=0):
     """Device time of `steps` single-launch steps (CUDA events on the handle's stream); with
     stats_every > 0 the profile statistics of the state every stats_every-th step starts from
@@ -272,8 +305,7 @@ def _extra_forms(nsteps, warmup, peak, peak_kind):
         out[f"bluffbody768_q27_{prec}"] = _form_line(lat, max(20, nsteps // 4), warmup, peak, peak_kind)
         lat.close()
         torch.cuda.empty_cache()
-    params = closure.init_params(7)
-    params[closure.OUT_LAYER] = np.random.default_rng(7).normal(0, 0.1, 33).astype(np.float32)
+    params = _closure_params()
     for size, name in ((256, "smag"), (256, "mlp"), (512, "mlp")):
         lat = closure.channel(size, size // 2, size // 2, closure=name, streaming="pull")
         if name == "mlp":
@@ -363,6 +395,10 @@ def main():
                     help="storage precision of the main line (profiling runs)")
     ap.add_argument("--streaming", default="pull", choices=["pull", "aa"],
                     help="streaming pattern of the main line (profiling runs)")
+    ap.add_argument("--closure", default="smag", choices=["smag", "mlp"],
+                    help="closure of the main line (profiling runs of the learned-closure kernel)")
+    ap.add_argument("--workload", default="channel", choices=["channel", "bluffbody"],
+                    help="main-line workload (profiling runs of the D3Q27 bluff-body kernel)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -386,21 +422,34 @@ def main():
 
     nx, ny, nz = (int(v) for v in args.size.lower().split("x"))
     ncell = nx * ny * nz
-    lat, par = _channel_lattice(nx, ny, nz, args.form, streaming=args.streaming)
+    channel = args.workload == "channel"
+    if channel:
+        lat, par = _channel_lattice(nx, ny, nz, args.form, closure=args.closure, streaming=args.streaming)
+        if args.closure == "mlp":
+            lbm.lbm_set_closure_f32(lat.h, _closure_params(), 600.0, 3000.0)
+            lbm.lbm_set_closure_floor(lat.h, 0.1)
+    else:
+        lat, par = _bluff_lattice(nx, ny, nz, args.form, streaming=args.streaming)
     clocks = ClockSampler(gpu_id)
     time.sleep(1.0)  # let nvidia-smi start
     for _ in range(args.warmup):
         lbm.lbm_step(lat.h, 1)
     torch.cuda.synchronize()
     clocks.start()
-    total_ms, per = _time_steps(lat, args.steps, 3, dist, stats_every=10)
+    total_ms, per = _time_steps(lat, args.steps, 3, dist, stats_every=10 if channel else 0)
     clocks.stop()
     total_ms = _barrier_max(dist, total_ms)
     value = world * ncell * args.steps / (total_ms * 1e-3) / 1e6
-    traffic = _profile_traffic(f"k_step_q19_{args.form}_smag_{args.streaming}_channel{nx}")
+    q = 19 if channel else 27
+    tag = f"k_step_q{q}_{args.form}_{args.closure}_{args.streaming}_{args.workload}{nx}"
+    traffic = _profile_traffic(tag)
     roof = _roofline(ncell, lat.bytes_per_update, per, peak, peak_kind, traffic)
     mass = lat.reduce()[0]
-    lat_bytes = ncell * 19 * lat.bytes_per_pop
+    lat_bytes = ncell * q * lat.bytes_per_pop
+    nsample = (args.steps + 9) // 10 if channel else 0
+    # our kernel launches in the timed region: one per step, plus per statistics sample the
+    # plane-sum pass (fused sampling) or the two reduction kernels (learned closure)
+    launches = args.steps + (2 * nsample if args.closure == "mlp" else nsample)
 
     # end to end through the C ABI with host buffers: upload (rho, u) from pinned memory,
     # K steps, read the moments back to pinned memory
@@ -443,18 +492,24 @@ def main():
             torch.cuda.empty_cache()
         forms.update(_extra_forms(nsteps, args.warmup, peak, peak_kind))
 
-    workload = WORKLOAD if (nx, ny, nz, args.form, args.streaming) == (512, 256, 256, "f32", "pull") else \
-        f"turbulent channel {nx}x{ny}x{nz} D3Q19 TRT+Smagorinsky {args.form} ({args.streaming})"
+    if (nx, ny, nz, args.form, args.streaming, args.closure, channel) == (512, 256, 256, "f32", "pull", "smag", True):
+        workload = WORKLOAD
+    elif channel:
+        workload = (f"turbulent channel {nx}x{ny}x{nz} D3Q19 TRT+" +
+                    ("learned closure" if args.closure == "mlp" else "Smagorinsky") + f" {args.form} ({args.streaming})")
+    else:
+        workload = f"bluff body {nx}x{ny}x{nz} D3Q27 TRT+Smagorinsky {args.form} ({args.streaming})"
     out = {"metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": workload, "storage": args.form, "nx": nx, "ny": ny, "nz": nz, "stencil": 19,
+           "config": {"workload": workload, "storage": args.form, "nx": nx, "ny": ny, "nz": nz, "stencil": q,
                       "tau": round(par["tau"], 6), "force": par["force"], "cs_smag": 0.1,
                       "global_batch": world * ncell, "parallelism": f"replicas x{world}",
-                      "stats": "mean/RMS profile sample (FP64 plane sums) every 10 steps, taken by the step kernel, inside the timed region",
+                      "stats": ("mean/RMS profile sample (FP64 plane sums) every 10 steps, taken by the step kernel, "
+                                "inside the timed region") if channel else "none",
                       "l2": f"inputs larger than L2 ({lat_bytes / 1e9:.2f} GB population array vs 129 MB L2)"},
-           "roofline": roof, "e2e": e2e, "gpu_launches": args.steps + args.steps // 10,
+           "roofline": roof, "e2e": e2e, "gpu_launches": launches,
            "clocks": clocks.summary(), "mass_after": mass, "forms": forms}
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = _cpu_baseline()

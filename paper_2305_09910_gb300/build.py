@@ -41,9 +41,9 @@ def _sources():
 
 def _digest(extra) -> str:
     h = hashlib.sha256()
-    for path in _sources():
+    for path in _sources():  # paths relative to the repository: the same stamp on every machine
         with open(path, "rb") as fh:
-            h.update(path.encode() + b"\0" + fh.read())
+            h.update(os.path.relpath(path, ROOT).encode() + b"\0" + fh.read())
     h.update(" ".join(ARCH + NVFLAGS + list(extra)).encode())
     return h.hexdigest()
 

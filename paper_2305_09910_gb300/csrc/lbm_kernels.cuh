@@ -361,27 +361,6 @@ __device__ __forceinline__ void store_state(const KParams& p, int x, int y, int 
   }
 }
 
-// ---- closure network: activation functions ------------------------------------------------
-// erf by the rational approximation of Abramowitz & Stegun, formula 7.1.26 (after Hastings):
-// erf(z) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-z^2), t = 1 / (1 + p z) for
-// z >= 0, erf(-z) = -erf(z); absolute error below 1.5e-7, about one float32 ulp of erf near 1.
-__device__ __forceinline__ float erf_as(float z) {
-  const float a = fabsf(z);
-  const float t = __fdividef(1.f, fmaf(0.3275911f, a, 1.f));
-  float q = fmaf(1.061405429f, t, -1.453152027f);
-  q = fmaf(q, t, 1.421413741f);
-  q = fmaf(q, t, -0.284496736f);
-  q = fmaf(q, t, 0.254829592f);
-  const float r = fmaf(-q * t, __expf(-a * a), 1.f);
-  return copysignf(r, z);
-}
-
-// GELU in its erf form, x Phi(x) = x (1 + erf(x / sqrt 2)) / 2, and its derivative.
-__device__ __forceinline__ float gelu_erf(float a) { return 0.5f * a * (1.f + erf_as(a * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_grad_f(float a) {
-  return 0.5f * (1.f + erf_as(a * 0.70710678118654752f)) + a * 0.39894228040143268f * __expf(-0.5f * a * a);
-}
-
 __device__ __forceinline__ float softplus_f(float y) { return fmaxf(y, 0.f) + log1pf(__expf(-fabsf(y))); }
 
 // ---- moments and TRT collision (in place on shifted populations) -----------------------
@@ -426,6 +405,55 @@ template <> struct Lanes<float2> {
   __device__ __forceinline__ static float get(float2 v, int k) { return k ? v.y : v.x; }
   __device__ __forceinline__ static void put(float2& v, int k, float a) { (k ? v.y : v.x) = a; }
 };
+
+// ---- closure network: activation functions ------------------------------------------------
+// erf by the rational approximation of Abramowitz & Stegun, formula 7.1.26 (after Hastings):
+// erf(z) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-z^2), t = 1 / (1 + p z) for
+// z >= 0, erf(-z) = -erf(z); absolute error below 1.5e-7, about one float32 ulp of erf near 1.
+// GELU in its erf form, x Phi(x) = x (1 + erf(x / sqrt 2)) / 2, written with m = q t e - 1
+// = -(1 - erf|z|) as  GELU(x) = x / 2 - |x| m / 2, for one value or two (packed FP32x2).
+__device__ __forceinline__ float ex2_approx(float v) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return r;
+}
+
+template <class V>
+__device__ __forceinline__ V gelu_v(V a) {
+  using L = Lanes<V>;
+  V az, t, e;
+#pragma unroll
+  for (int k = 0; k < L::n; k++) L::put(az, k, fabsf(L::get(a, k)) * 0.70710678118654752f);  // |z|
+  const V den = vfma(az, vset<V>(0.3275911f), vset<V>(1.f));
+#pragma unroll
+  for (int k = 0; k < L::n; k++) L::put(t, k, __fdividef(1.f, L::get(den, k)));
+  V q = vfma(vset<V>(1.061405429f), t, vset<V>(-1.453152027f));
+  q = vfma(q, t, vset<V>(1.421413741f));
+  q = vfma(q, t, vset<V>(-0.284496736f));
+  q = vfma(q, t, vset<V>(0.254829592f));
+  const V arg = vmul(az, vmul(az, vset<V>(-1.4426950408889634f)));  // -z^2 log2(e)
+#pragma unroll
+  for (int k = 0; k < L::n; k++) L::put(e, k, ex2_approx(L::get(arg, k)));
+  const V m = vfma(vmul(q, t), e, vset<V>(-1.f));
+  return vfma(vmul(az, vset<V>(-0.70710678118654752f)), m, vmul(a, vset<V>(0.5f)));
+}
+
+__device__ __forceinline__ float gelu_erf(float a) { return gelu_v<float>(a); }
+
+// erf of the same approximation, for the derivative Phi(x) + x phi(x) of the GELU
+__device__ __forceinline__ float erf_as(float z) {
+  const float a = fabsf(z);
+  const float t = __fdividef(1.f, fmaf(0.3275911f, a, 1.f));
+  float q = fmaf(1.061405429f, t, -1.453152027f);
+  q = fmaf(q, t, 1.421413741f);
+  q = fmaf(q, t, -0.284496736f);
+  q = fmaf(q, t, 0.254829592f);
+  const float r = fmaf(-q * t, ex2_approx(-a * a * 1.4426950408889634f), 1.f);
+  return copysignf(r, z);
+}
+__device__ __forceinline__ float gelu_grad_f(float a) {
+  return 0.5f * (1.f + erf_as(a * 0.70710678118654752f)) + a * 0.39894228040143268f * __expf(-0.5f * a * a);
+}
 
 // Orientation of the +/- pair (I, I+1), I odd: the member whose first non-zero velocity
 // component is positive is the primary one, so that c.u is a plain sum with a leading +.

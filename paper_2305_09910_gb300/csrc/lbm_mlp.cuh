@@ -29,8 +29,11 @@
 namespace lbm {
 
 constexpr int MLP_TILE = 128;                     // cells per tile (TMEM lanes, MMA M)
-constexpr int MLP_NG = 4;                         // tile groups per CTA
-constexpr unsigned MLP_TMEM_COLS = 32 * MLP_NG;   // accumulator columns (MMA N = 32 per group)
+#ifndef LBM_MLP_NG
+#define LBM_MLP_NG 7
+#endif
+constexpr int MLP_NG = LBM_MLP_NG;                // tile groups per CTA
+constexpr unsigned MLP_TMEM_COLS = MLP_NG <= 1 ? 32 : MLP_NG <= 2 ? 64 : MLP_NG <= 4 ? 128 : 256;  // allocation: 32 per group, power of 2
 // instruction descriptor of tcgen05.mma.kind::tf32: D f32 (bits 4-5 = 1), A and B tf32
 // (bits 7-9, 10-12 = 2), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28
 constexpr uint32_t MLP_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
@@ -93,7 +96,9 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 struct MlpSmem {
   float A[MLP_NG][MLP_TILE * MLP_NH];  // hidden layer 1 per group, TF32, core-matrix layout (16 KB each)
   float B[MLP_NH * MLP_NH];            // W2, core-matrix layout (4 KB)
-  float W1[MLP_NH * MLP_NIN], b1[MLP_NH], b2[MLP_NH], W3[MLP_NH], b3;
+  // layers 1 and 3 as pairs of hidden units (j, j+1) for the packed FP32x2 pipe
+  float2 W1[MLP_NH / 2][MLP_NIN], b1[MLP_NH / 2], b2[MLP_NH / 2], W3[MLP_NH / 2];
+  float b3;
   unsigned long long bar[MLP_NG];
   uint32_t tmem;
 };
@@ -128,11 +133,14 @@ __global__ void __launch_bounds__(128 * MLP_NG, 1) k_step_mlp(const __grid_const
       const int n = k / MLP_NH, kk = k % MLP_NH;  // output n, input kk
       sm.B[core_off(n, kk)] = W2[k];
     }
-    for (int k = tc; k < MLP_NH * MLP_NIN; k += 128 * MLP_NG) sm.W1[k] = W1[k];
-    if (tc < MLP_NH) {
-      sm.b1[tc] = b1[tc];
-      sm.b2[tc] = b2[tc];
-      sm.W3[tc] = W3[tc];
+    for (int k = tc; k < (MLP_NH / 2) * MLP_NIN; k += 128 * MLP_NG) {
+      const int jp = k / MLP_NIN, i = k % MLP_NIN;
+      sm.W1[jp][i] = make_float2(W1[(2 * jp) * MLP_NIN + i], W1[(2 * jp + 1) * MLP_NIN + i]);
+    }
+    if (tc < MLP_NH / 2) {
+      sm.b1[tc] = make_float2(b1[2 * tc], b1[2 * tc + 1]);
+      sm.b2[tc] = make_float2(b2[2 * tc], b2[2 * tc + 1]);
+      sm.W3[tc] = make_float2(W3[2 * tc], W3[2 * tc + 1]);
     }
     if (tc == 0) {
       sm.b3 = W3[MLP_NH];
@@ -174,23 +182,24 @@ __global__ void __launch_bounds__(128 * MLP_NG, 1) k_step_mlp(const __grid_const
     load_state<Q, S, LOAD>(p, x, y, z, cell, cls, f, outmask);
     outflow_fix<Q>(p, x, f, outmask);
     const Macro<float> M = macro<Q, true, float>(p, f);
-    // layer 1 (FP32), GELU, TF32 rounding, row t of the operand tile
+    // layer 1 (FP32, two hidden units per packed FP32x2 operation), GELU, TF32 rounding,
+    // row t of the operand tile
     float xin[MLP_NIN];
 #pragma unroll
     for (int k = 0; k < 6; k++) xin[k] = fminf(fmaxf(p.mlp_scale[0] * M.pi[k], -MLP_XCLAMP), MLP_XCLAMP);
     xin[6] = fminf(fmaxf(p.mlp_scale[1] * M.drho, -MLP_XCLAMP), MLP_XCLAMP);
 #pragma unroll
     for (int c4 = 0; c4 < MLP_NH / 4; c4++) {
-      uint32_t h[4];
+      float2 s01 = sm.b1[2 * c4], s23 = sm.b1[2 * c4 + 1];
 #pragma unroll
-      for (int jj = 0; jj < 4; jj++) {
-        const int j = 4 * c4 + jj;
-        float s = sm.b1[j];
-#pragma unroll
-        for (int k = 0; k < MLP_NIN; k++) s = fmaf(sm.W1[j * MLP_NIN + k], xin[k], s);
-        h[jj] = to_tf32(gelu_erf(s));
+      for (int k = 0; k < MLP_NIN; k++) {
+        const float2 xk = make_float2(xin[k], xin[k]);
+        s01 = vfma(sm.W1[2 * c4][k], xk, s01);
+        s23 = vfma(sm.W1[2 * c4 + 1][k], xk, s23);
       }
-      *reinterpret_cast<uint4*>(A + core_off(t, 4 * c4)) = make_uint4(h[0], h[1], h[2], h[3]);
+      const float2 g01 = gelu_v(s01), g23 = gelu_v(s23);
+      *reinterpret_cast<uint4*>(A + core_off(t, 4 * c4)) =
+          make_uint4(to_tf32(g01.x), to_tf32(g01.y), to_tf32(g23.x), to_tf32(g23.y));
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
@@ -214,15 +223,19 @@ __global__ void __launch_bounds__(128 * MLP_NG, 1) k_step_mlp(const __grid_const
       break;
     }
     tc_fence_after();
-    // epilogue: this thread's 32 accumulator columns, bias, GELU, output layer
-    float yv = sm.b3;
+    // epilogue: this thread's 32 accumulator columns, bias, GELU, output layer (pairs)
+    float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
     for (int half = 0; half < 2; half++) {
       float v[16];
       tmem_ld16(tl + 16 * half, v);
 #pragma unroll
-      for (int k = 0; k < 16; k++) yv = fmaf(sm.W3[16 * half + k], gelu_erf(v[k] + sm.b2[16 * half + k]), yv);
+      for (int pr = 0; pr < 8; pr++) {
+        const float2 a2 = vadd(make_float2(v[2 * pr], v[2 * pr + 1]), sm.b2[8 * half + pr]);
+        acc = vfma(sm.W3[8 * half + pr], gelu_v(a2), acc);
+      }
     }
+    const float yv = sm.b3 + (acc.x + acc.y);
     const float cs2 = fmaxf(softplus_f(yv) * p.cs2 * 1.4426950408889634f, p.cs2_min);  // / ln 2
     float wp, wm;
     les_rates(p, M.qn, M.inv, cs2, wp, wm);
