@@ -44,7 +44,8 @@ def _digest(extra) -> str:
     for path in _sources():  # paths relative to the repository: the same stamp on every machine
         with open(path, "rb") as fh:
             h.update(os.path.relpath(path, ROOT).encode() + b"\0" + fh.read())
-    h.update(" ".join(ARCH + NVFLAGS + list(extra)).encode())
+    flags = " ".join(ARCH + NVFLAGS + list(extra)).replace(ROOT, ".")  # no machine paths
+    h.update(flags.encode())
     return h.hexdigest()
 
 

@@ -8,6 +8,8 @@ each form the test states (prints) and bounds:
   * the relative errors of the mean u_x and RMS velocity profiles (x-z plane statistics),
   * the relative drift of the total mass (FP64 sums on the GPU).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -78,3 +80,60 @@ def test_precision_forms_against_oracle():
         assert r["mean_profile_err"] <= b_mean, (prec, r)
         assert r["rms_profile_err"] <= b_rms, (prec, r)
         assert r["mass_drift"] <= b_mass, (prec, r)
+
+
+# Bluff-body sub-case: D3Q27, 96 x 48 x 48 with the landing-gear geometry scaled by 1/8, inflow
+# 0.05, outflow, free-slip sides, 100 steps from the uniform inflow state.  Ceilings 3-8 times
+# above the errors measured on GB300 (f32 1.2e-7 / 1.6e-7 / 2.4e-9, f16 2.5e-4 / 5.2e-4 / 3.3e-5,
+# bf16 1.7e-3 / 3.9e-3 / 5.7e-5).  With inflow and outflow the mass is not conserved: the
+# half forms round the boundary fluxes, so their mass departs from the oracle's by ~1e-5 per
+# hundred steps, against 2e-8 in the closed channel.
+BLUFF_BOUNDS = {  # pop error, velocity-field relative error, mass difference vs the oracle
+    "f32": (1e-6, 1e-6, 1e-8),
+    "f16": (1e-3, 2e-3, 1.5e-4),
+    "bf16": (1e-2, 2e-2, 3e-4),
+}
+
+
+def test_bluff_body_precision_forms_against_oracle():
+    import torch
+
+    import oracle
+    from paper_2305_09910_gb300 import build, inputs, lbm
+
+    assert torch.cuda.is_available()
+    build.build()
+    nx, ny, nz, steps = 96, 48, 48, 100
+    flags = inputs.landing_gear_flags(nx, ny, nz, scale=1 / 8)
+    tau = 0.5 + 3 * 0.05 * 10 / 1e4
+    faces = ("inflow", "outflow", "freeslip", "freeslip", "freeslip", "freeslip")
+    ora = oracle.Oracle(nx, ny, nz, q=27, tau=tau, closure="smag", cs=0.1, faces=faces,
+                        u_w=(0.05, 0, 0), flags=flags)
+    u0 = np.zeros((3, nz, ny, nx))
+    u0[0] = 0.05
+    ora.init_equilibrium(1.0, u0)
+    ora.step(steps, threads=os.cpu_count() or 1)
+    _, ur = ora.moments()
+    ref_df = ora.shifted()
+    m_ref = ora.mass_momentum()[0]
+    report = {}
+    for prec in BLUFF_BOUNDS:
+        lat = lbm.Lattice(nx, ny, nz, stencil=27, tau=tau, precision=prec, closure="smag", cs_smag=0.1,
+                          faces=faces, u_inflow=(0.05, 0, 0))
+        lat.set_flags(flags)
+        lat.init_equilibrium(None, u0.astype(np.float32))
+        lat.step(steps)
+        lat.sync()
+        _, ug = lat.moments()
+        report[prec] = {
+            "pop_err": float(np.abs(lat.get_populations() - ref_df).max()),
+            "u_rel_err": float(np.linalg.norm(ug - ur) / np.linalg.norm(ur)),
+            "mass_rel_diff": float(abs(lat.reduce()[0] - m_ref) / m_ref),
+        }
+        lat.close()
+    print("bluff-body precision forms vs FP64 oracle after", steps, "steps:", report)
+    for prec, (b_pop, b_u, b_m) in BLUFF_BOUNDS.items():
+        r = report[prec]
+        assert r["pop_err"] <= b_pop, (prec, r)
+        assert r["u_rel_err"] <= b_u, (prec, r)
+        assert r["mass_rel_diff"] <= b_m, (prec, r)
