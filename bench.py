@@ -146,11 +146,13 @@ def _dist():
 
 
 def _barrier_max(dist, value):
+    """Maximum of a per-rank value over the ranks (device tensor under NCCL, host under gloo)."""
     if dist is None:
         return value
     import torch
 
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
