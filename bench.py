@@ -322,6 +322,39 @@ def _extra_forms(nsteps, warmup, peak, peak_kind):
     return out
 
 
+def _slab_form(nslab, nsteps, warmup, peak, peak_kind):
+    """The channel split into nslab z slabs on this GPU, a halo exchange after every step
+    (lbm_halo_pack/unpack of the 5 crossing directions per face): cost of the domain split."""
+    import torch
+
+    from paper_2305_09910_gb300 import inputs, slabs
+
+    par = inputs.channel_parameters(256)
+    sl = slabs.ZSlabs(512, 256, 256, nslab, stencil=19, tau=par["tau"], closure="smag", cs_smag=0.1,
+                      faces=FACES_CHANNEL)
+    sl.set_force(par["force"])
+    sl.init_equilibrium()
+    sl.step(warmup)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    sl.step(nsteps)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    sl.sync()
+    ms = t0.elapsed_time(t1) / nsteps
+    ncell = sl.ncell
+    halo = sum(b.numel() for b in sl.bufs)
+    sl.close()
+    achieved = ncell * 153 / (ms * 1e-3) / 1e9
+    return {"MLUPS": round(ncell / (ms * 1e-3) / 1e6, 1), "cells": ncell, "halo_bytes_per_step": halo,
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": None,
+                         "bytes_per_update": 153.0, "ms_per_step": round(ms, 4)}}
+
+
 def _cpu_baseline(target_s=12.0):
     """The FP64 oracle on this host's cores, on a 128x64x64 sub-lattice of the channel."""
     import numpy as np
@@ -493,6 +526,7 @@ def main():
             fl.close()
             torch.cuda.empty_cache()
         forms.update(_extra_forms(nsteps, args.warmup, peak, peak_kind))
+        forms["channel512_f32_2slabs_halo"] = _slab_form(2, nsteps, args.warmup, peak, peak_kind)
 
     if (nx, ny, nz, args.form, args.streaming, args.closure, channel) == (512, 256, 256, "f32", "pull", "smag", True):
         workload = WORKLOAD

@@ -91,7 +91,11 @@ enum {
   LBM_FACE_WALL = 1,
   LBM_FACE_FREESLIP = 2,
   LBM_FACE_INFLOW = 3,
-  LBM_FACE_OUTFLOW = 4 /* +x only; needs nx >= 2 and nx % 32 != 1 */
+  LBM_FACE_OUTFLOW = 4, /* +x only; needs nx >= 2 and nx % 32 != 1 */
+  /* -z / +z only, two-grid pull only: the lattice is one z slab of a larger one; the cells
+   * beyond the face live in a ghost plane (populations and flags) filled by
+   * lbm_halo_unpack from the neighbouring slab after every step */
+  LBM_FACE_HALO = 5
 };
 /* cell flags (uint8) */
 enum { LBM_CELL_FLUID = 0, LBM_CELL_SOLID = 1, LBM_CELL_INFLOW = 2 };
@@ -128,6 +132,24 @@ typedef struct {
  * All compute bit-identical updates. */
 enum { LBM_PIPE_TMA = 0, LBM_PIPE_DIRECT = 1, LBM_PIPE_PREFETCH = 2, LBM_PIPE_ASYNC = 3 };
 
+/* Halo exchange of z slabs (Sec. 3: a block's communication kernels pack and unpack the
+ * populations that cross a face; only the directions crossing it travel, 5 of 19 or 9 of 27).
+ * face: 4 (-z) or 5 (+z), a LBM_FACE_HALO face of a two-grid pull lattice that has stepped
+ * at least once since its last import (else LBM_ESTATE).
+ *   lbm_halo_bytes: size of one face's buffer, n_dir * ny * nxp * (4 or 2) bytes.
+ *   lbm_halo_pack: copies the post-collision populations of the plane next to the face
+ *     (z = 0 for -z, z = nz-1 for +z) that leave through it (c_z = -1 resp. +1) into buf,
+ *     layout [direction (ascending index)][ny][nxp] in the storage precision.
+ *   lbm_halo_unpack: copies buf into the ghost plane beyond the face (z = -1 resp. nz), for
+ *     the directions that enter through it (c_z = +1 resp. -1).
+ * The pack of slab A's +z face is the unpack of slab B's -z face and vice versa.  buf is a
+ * device pointer (or host memory the GPU can address: pinned or managed), 4-byte aligned,
+ * owned by the caller; one kernel per call, stream-ordered on the handle's stream.  Exchange
+ * after every step, before the next. */
+size_t lbm_halo_bytes(lbm_handle h, int face);
+lbm_status lbm_halo_pack(lbm_handle h, int face, void* buf);
+lbm_status lbm_halo_unpack(lbm_handle h, int face, const void* buf);
+
 /* Fills p with the defaults listed above. */
 void lbm_params_default(lbm_params* p);
 
@@ -148,7 +170,10 @@ lbm_status lbm_destroy(lbm_handle h);
 
 /* Cell flags, nx*ny*nz uint8 (LBM_CELL_*), x fastest; on_device != 0 if flags is a device
  * pointer.  Other values give EINVAL.  Cells that become fluid keep whatever populations
- * they held; call lbm_init_equilibrium or lbm_set_populations afterwards. */
+ * they held; call lbm_init_equilibrium or lbm_set_populations afterwards.  With a
+ * LBM_FACE_HALO z face the array holds nz + 2 planes, z = -1 .. nz: the ghost planes carry
+ * the flags of the neighbouring slabs' cells (so bounce-back against a solid cell across the
+ * face is resolved here). */
 lbm_status lbm_set_flags(lbm_handle h, const uint8_t* flags, int on_device);
 
 /* Constant body-force density F (lattice units), used by every later step. */

@@ -19,6 +19,7 @@ using namespace lbm;
 
 struct lbm_s {
   int nx = 0, ny = 0, nz = 0, nxp = 0, q = 0;
+  int zg = 0;  // ghost z planes on each side (1 with a LBM_FACE_HALO z face)
   double tau = 0.0;
   lbm_params prm{};
   cudaStream_t stream = nullptr;
@@ -74,6 +75,9 @@ static lbm_status fail(lbm_handle h, lbm_status s, const char* fmt, ...) {
 static size_t store_bytes(int precision) { return precision == LBM_F32 ? 4 : 2; }
 
 static long long plane_of(const lbm_s* h) { return (long long)h->nxp * h->ny * h->nz; }
+// allocated elements per direction (ghost planes included) and the offset of z = 0
+static long long plane_alloc(const lbm_s* h) { return (long long)h->nxp * h->ny * (h->nz + 2 * h->zg); }
+static long long ghost_off(const lbm_s* h) { return (long long)h->nxp * h->ny * h->zg; }
 
 static long long ncell(const lbm_s* h) { return (long long)h->nx * h->ny * h->nz; }
 
@@ -94,8 +98,9 @@ static KParams kparams(const lbm_s* h) {
     p.f = a;
     const size_t sb = store_bytes(h->prm.precision);
     for (int i = 0; i < 27; i++) {
-      p.fp[i] = i < h->q ? (void*)((char*)a + (size_t)i * (size_t)plane_of(h) * sb) : nullptr;
-      p.fq[i] = (i < h->q && b) ? (void*)((char*)b + (size_t)i * (size_t)plane_of(h) * sb) : nullptr;
+      const size_t off = ((size_t)i * (size_t)plane_alloc(h) + (size_t)ghost_off(h)) * sb;
+      p.fp[i] = i < h->q ? (void*)((char*)a + off) : nullptr;
+      p.fq[i] = (i < h->q && b) ? (void*)((char*)b + off) : nullptr;
     }
     int c[81];
     lbm_stencil(27, c, nullptr);
@@ -107,7 +112,7 @@ static KParams kparams(const lbm_s* h) {
     }
   }
   p.nat_valid = h->nat_valid;
-  p.flags = h->flags;
+  p.flags = h->flags + ghost_off(h);
   p.cls = h->cls;
   p.rules = h->rules;
   p.stats_w = h->stats_w;
@@ -278,7 +283,9 @@ __global__ void k_classify(const __grid_constant__ KParams p, uint8_t* cls, unsi
     for (int a = 0; a < 3; a++) {
       s[a] = xc[a] - d[a];
       if (s[a] < 0 || s[a] >= n[a]) {
-        if (p.face[2 * a] != FACE_PERIODIC) c = CLS_BOUNDARY;
+        const int ft = p.face[s[a] < 0 ? 2 * a : 2 * a + 1];
+        if (ft == FACE_HALO) continue;  // a ghost cell: plain streaming unless its flag says otherwise
+        if (ft != FACE_PERIODIC) c = CLS_BOUNDARY;
         else if (a > 0) wrap_yz = true;
         s[a] = s[a] < 0 ? s[a] + n[a] : s[a] - n[a];
       }
@@ -404,8 +411,11 @@ lbm_status lbm_create(int nx, int ny, int nz, int stencil, double tau, const lbm
     return fail(nullptr, LBM_EINVAL, "unknown pipeline %d", p.pipeline);
   if (!(p.cs_smag >= 0.0)) return fail(nullptr, LBM_EINVAL, "cs_smag must be >= 0");
   for (int k = 0; k < 6; k++)
-    if (p.face_bc[k] < LBM_FACE_PERIODIC || p.face_bc[k] > LBM_FACE_OUTFLOW)
+    if (p.face_bc[k] < LBM_FACE_PERIODIC || p.face_bc[k] > LBM_FACE_HALO)
       return fail(nullptr, LBM_EINVAL, "unknown face type %d", p.face_bc[k]);
+  for (int k = 0; k < 6; k++)
+    if (p.face_bc[k] == LBM_FACE_HALO && (k < 4 || p.streaming != LBM_PULL))
+      return fail(nullptr, LBM_EUNSUPPORTED, "halo faces are supported on the z faces of two-grid pull lattices");
   for (int a = 0; a < 3; a++)
     if ((p.face_bc[2 * a] == LBM_FACE_PERIODIC) != (p.face_bc[2 * a + 1] == LBM_FACE_PERIODIC))
       return fail(nullptr, LBM_EINVAL, "periodic faces must come in pairs (axis %d)", a);
@@ -426,6 +436,7 @@ lbm_status lbm_create(int nx, int ny, int nz, int stencil, double tau, const lbm
   h->nz = nz;
   h->nxp = nxp;
   h->q = stencil;
+  h->zg = (p.face_bc[4] == LBM_FACE_HALO || p.face_bc[5] == LBM_FACE_HALO) ? 1 : 0;
   h->tau = tau;
   h->prm = p;
   h->stream = (cudaStream_t)p.stream;
@@ -436,12 +447,13 @@ lbm_status lbm_create(int nx, int ny, int nz, int stencil, double tau, const lbm
     if (h->nsm < 1) h->nsm = 1;
   }
   const long long plane = plane_of(h);
-  const size_t fbytes = (size_t)plane * stencil * store_bytes(p.precision);
+  const long long gplane = plane_alloc(h);  // with the ghost planes (populations, flags)
+  const size_t fbytes = (size_t)gplane * stencil * store_bytes(p.precision);
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMallocAsync(&h->f, fbytes, h->stream);
   if (e == cudaSuccess && p.streaming == LBM_PULL) e = cudaMallocAsync(&h->f2, fbytes, h->stream);
   if (e == cudaSuccess && h->f2) e = cudaMemsetAsync(h->f2, 0, fbytes, h->stream);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->flags, (size_t)plane, h->stream);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->flags, (size_t)gplane, h->stream);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->cls, (size_t)plane, h->stream);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->rules, (size_t)plane * 8, h->stream);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->status, sizeof(int), h->stream);
@@ -450,7 +462,7 @@ lbm_status lbm_create(int nx, int ny, int nz, int stencil, double tau, const lbm
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->stats, (size_t)ny * LBM_STATS_K * sizeof(double), h->stream);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&h->status_host, sizeof(int));
   if (e == cudaSuccess) e = cudaMemsetAsync(h->f, 0, fbytes, h->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->flags, 0, (size_t)plane, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->flags, 0, (size_t)gplane, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(int), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->stats, 0, (size_t)ny * LBM_STATS_K * sizeof(double), h->stream);
   if (e != cudaSuccess) {
@@ -461,7 +473,7 @@ lbm_status lbm_create(int nx, int ny, int nz, int stencil, double tau, const lbm
   }
   // padding columns are never fluid
   if (nxp != nx) {
-    e = cudaMemset2DAsync(h->flags + nx, nxp, CELL_SOLID, nxp - nx, (size_t)ny * nz, h->stream);
+    e = cudaMemset2DAsync(h->flags + nx, nxp, CELL_SOLID, nxp - nx, (size_t)ny * (nz + 2 * h->zg), h->stream);
     if (e != cudaSuccess) {
       lbm_status s = fail(nullptr, LBM_ECUDA, "flag padding: %s", cudaGetErrorString(e));
       lbm_destroy(h);
@@ -481,7 +493,7 @@ lbm_status lbm_create(int nx, int ny, int nz, int stencil, double tau, const lbm
 lbm_status lbm_set_flags(lbm_handle h, const uint8_t* flags, int on_device) {
   if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
   if (!flags) return fail(h, LBM_EINVAL, "flags is NULL");
-  const long long n = ncell(h);
+  const long long n = (long long)h->nx * h->ny * (h->nz + 2 * h->zg);  // ghost planes included
   const uint8_t* src = flags;
   uint8_t* tmp = nullptr;
   if (!on_device) {
@@ -493,7 +505,7 @@ lbm_status lbm_set_flags(lbm_handle h, const uint8_t* flags, int on_device) {
   CUDA_TRY(h, cudaMallocAsync((void**)&bad, sizeof(int), h->stream));
   CUDA_TRY(h, cudaMemsetAsync(bad, 0, sizeof(int), h->stream));
   const int blocks = (int)std::min<long long>((n + 255) / 256, 152 * 32);
-  k_flags_in<<<blocks, 256, 0, h->stream>>>(src, h->flags, h->nx, h->ny, h->nz, h->nxp, bad);
+  k_flags_in<<<blocks, 256, 0, h->stream>>>(src, h->flags, h->nx, h->ny, h->nz + 2 * h->zg, h->nxp, bad);
   CUDA_TRY(h, cudaGetLastError());
   int nbad = 0;
   CUDA_TRY(h, cudaMemcpyAsync(h->status_host, bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -625,6 +637,81 @@ lbm_status lbm_step_stats(lbm_handle h, int64_t n, int64_t every) {
   if (n < 0) return fail(h, LBM_EINVAL, "n must be >= 0");
   if (every < 1) return fail(h, LBM_EINVAL, "every must be >= 1");
   return run_steps(h, n, every);
+}
+
+// ---- halo exchange of z slabs -------------------------------------------------------------
+// Directions that cross a z face: those with c_z = sign (+1 for the +z face when leaving).
+static int halo_dirs(const lbm_s* h, int sign, int* dirs) {
+  int c[81], n = 0;
+  lbm_stencil(h->q, c, nullptr);
+  for (int i = 0; i < h->q; i++)
+    if (c[3 * i + 2] == sign) dirs[n++] = i;
+  return n;
+}
+
+static lbm_status halo_check(lbm_handle h, int face) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (face != 4 && face != 5) return fail(h, LBM_EINVAL, "face must be 4 (-z) or 5 (+z)");
+  if (h->prm.face_bc[face] != LBM_FACE_HALO) return fail(h, LBM_EINVAL, "face %d is not a halo face", face);
+  if (h->parity != 2) return fail(h, LBM_ESTATE, "no post-collision state yet: step once after an import");
+  return LBM_OK;
+}
+
+// One z plane of up to 9 directions between the population array and a packed buffer
+// [k][ny][nxp], as 32-bit words (a plane row is a multiple of 32 elements).
+struct HaloPlanes {
+  uint32_t* plane[9];
+};
+
+__global__ void __launch_bounds__(256) k_halo_copy(HaloPlanes hp, int nd, long long words, uint32_t* buf, int pack) {
+  const long long n = (long long)nd * words;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(t / words);
+    const long long w = t - (long long)k * words;
+    if (pack) buf[t] = hp.plane[k][w];
+    else hp.plane[k][w] = buf[t];
+  }
+}
+
+static lbm_status halo_copy(lbm_handle h, int face, void* buf, bool pack) {
+  lbm_status st = halo_check(h, face);
+  if (st != LBM_OK) return st;
+  if (!buf) return fail(h, LBM_EINVAL, "buf is NULL");
+  if ((uintptr_t)buf % 4) return fail(h, LBM_EINVAL, "buf must be 4-byte aligned");
+  // the kernel dereferences buf: device, managed or pinned (registered) host memory only
+  cudaPointerAttributes attr{};
+  if (cudaPointerGetAttributes(&attr, buf) != cudaSuccess || attr.type == cudaMemoryTypeUnregistered) {
+    cudaGetLastError();  // clear the query's error state
+    return fail(h, LBM_EINVAL, "buf must be device memory or pinned host memory");
+  }
+  if (attr.type == cudaMemoryTypeHost) buf = attr.devicePointer;
+  int dirs[27];
+  // pack: leaving directions (c_z = -1 through -z, +1 through +z); unpack: entering ones
+  const int sign = pack ? (face == 5 ? 1 : -1) : (face == 4 ? 1 : -1);
+  const int nd = halo_dirs(h, sign, dirs);
+  const KParams p = kparams(h);
+  const size_t sb = store_bytes(h->prm.precision);
+  const size_t pb = (size_t)h->nxp * h->ny * sb;  // one z plane of one direction
+  const long long z = pack ? (face == 5 ? h->nz - 1 : 0) : (face == 4 ? -1 : h->nz);
+  HaloPlanes hp{};
+  for (int k = 0; k < nd; k++) hp.plane[k] = (uint32_t*)((char*)p.fp[dirs[k]] + z * (long long)pb);
+  const long long words = (long long)(pb / 4);
+  const int blocks = (int)std::min<long long>((nd * words + 255) / 256, (long long)h->nsm * 8);
+  k_halo_copy<<<blocks, 256, 0, h->stream>>>(hp, nd, words, (uint32_t*)buf, pack ? 1 : 0);
+  CUDA_TRY(h, cudaGetLastError());
+  return LBM_OK;
+}
+
+size_t lbm_halo_bytes(lbm_handle h, int face) {
+  if (!h || (face != 4 && face != 5)) return 0;
+  int dirs[27];
+  return (size_t)halo_dirs(h, face == 5 ? 1 : -1, dirs) * h->nxp * h->ny * store_bytes(h->prm.precision);
+}
+
+lbm_status lbm_halo_pack(lbm_handle h, int face, void* buf) { return halo_copy(h, face, buf, true); }
+
+lbm_status lbm_halo_unpack(lbm_handle h, int face, const void* buf) {
+  return halo_copy(h, face, const_cast<void*>(buf), false);
 }
 
 lbm_status lbm_sync(lbm_handle h) {

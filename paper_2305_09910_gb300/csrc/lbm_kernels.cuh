@@ -50,7 +50,8 @@ __host__ __device__ constexpr float wgt(int i) {
 
 // ---- flags, faces, cell classes ------------------------------------------------------
 enum : int { CELL_FLUID = 0, CELL_SOLID = 1, CELL_INFLOW = 2 };
-enum : int { FACE_PERIODIC = 0, FACE_WALL = 1, FACE_FREESLIP = 2, FACE_INFLOW = 3, FACE_OUTFLOW = 4 };
+// FACE_HALO: the cells beyond the face are ghost cells of a neighbouring slab (z faces)
+enum : int { FACE_PERIODIC = 0, FACE_WALL = 1, FACE_FREESLIP = 2, FACE_INFLOW = 3, FACE_OUTFLOW = 4, FACE_HALO = 5 };
 // cls: interior fluid (every source is a fluid cell reached by plain streaming, or by a
 // periodic wrap in x), wrap fluid (as interior, but a source wraps across a periodic y or z
 // face), boundary fluid (some source needs a rule), and everything that is not updated.
@@ -147,6 +148,7 @@ static __device__ __noinline__ int classify(const KParams& p, int x, int y, int 
   for (int a = 0; a < 3; a++) {
     s[a] = xc[a] - c[a];
     fc[a] = s[a] < 0 ? 2 * a : (s[a] >= n[a] ? 2 * a + 1 : -1);
+    if (fc[a] >= 0 && p.face[fc[a]] == FACE_HALO) fc[a] = -1;  // a ghost cell, not a face
     if (fc[a] >= 0) rank = max(rank, face_rank(p.face[fc[a]]));
   }
   plane = i;
@@ -199,7 +201,10 @@ static __device__ __noinline__ int resolve_special(const KParams& p, int x, int 
     s[a] = xc[a] - c[a];
     d[a] = c[a];
     if (s[a] < 0 || s[a] >= n[a]) {
-      if (p.face[s[a] < 0 ? 2 * a : 2 * a + 1] == FACE_PERIODIC) {
+      const int ft = p.face[s[a] < 0 ? 2 * a : 2 * a + 1];
+      if (ft == FACE_HALO) {
+        // the ghost cell beyond the face
+      } else if (ft == FACE_PERIODIC) {
         s[a] = s[a] < 0 ? s[a] + n[a] : s[a] - n[a];
       } else {
         s[a] = xc[a];
@@ -220,14 +225,16 @@ __device__ __forceinline__ S* plane_ptr(const KParams& p, int i) {
 // Interior cells: periodic-wrapped source of direction i (x - c_i).
 struct Nbr {
   int xs[3], ys[3], zs[3];  // index c+1 -> coordinate of x - c
+  // wraps only across periodic faces (a source across another face is either never read,
+  // as its rule is not plain streaming, or a ghost cell beyond a halo face)
   __device__ __forceinline__ void init(const KParams& p, int x, int y, int z) {
     xs[1] = x; ys[1] = y; zs[1] = z;
     xs[2] = x == 0 ? p.nx - 1 : x - 1;  // c = +1
     xs[0] = x == p.nx - 1 ? 0 : x + 1;  // c = -1
     ys[2] = y == 0 ? p.ny - 1 : y - 1;
     ys[0] = y == p.ny - 1 ? 0 : y + 1;
-    zs[2] = z == 0 ? p.nz - 1 : z - 1;
-    zs[0] = z == p.nz - 1 ? 0 : z + 1;
+    zs[2] = (z == 0 && p.face[4] == FACE_PERIODIC) ? p.nz - 1 : z - 1;
+    zs[0] = (z == p.nz - 1 && p.face[5] == FACE_PERIODIC) ? 0 : z + 1;
   }
   __device__ __forceinline__ int src(const KParams& p, int i) const {
     return (zs[cz(i) + 1] * p.ny + ys[cy(i) + 1]) * p.nxp + xs[cx(i) + 1];

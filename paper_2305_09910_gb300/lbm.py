@@ -27,7 +27,7 @@ PRECISION = {"f32": 0, "f16": 1, "bf16": 2}
 STREAMING = {"aa": 0, "pull": 1}
 PIPELINE = {"tma": 0, "direct": 1, "prefetch": 2, "async": 3}
 CLOSURE = {"none": 0, "smag": 1, "mlp": 2}
-FACE = {"periodic": 0, "wall": 1, "freeslip": 2, "inflow": 3, "outflow": 4}
+FACE = {"periodic": 0, "wall": 1, "freeslip": 2, "inflow": 3, "outflow": 4, "halo": 5}
 CELL = {"fluid": 0, "solid": 1, "inflow": 2}
 MLP_NPARAM = 1345
 STATS_K = 10
@@ -94,6 +94,9 @@ def load():
             "lbm_set_closure": (I, [H, P, I, D, D]),
             "lbm_info": (I, [H, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)]),
             "lbm_last_error": (ctypes.c_char_p, [H]),
+            "lbm_halo_bytes": (ctypes.c_size_t, [H, I]),
+            "lbm_halo_pack": (I, [H, I, P]),
+            "lbm_halo_unpack": (I, [H, I, P]),
             "lbm_reduce_noalloc": (I, [P, P, I, I, I, I, P, P, P]),
             "lbm_set_closure_f32": (I, [H, P, I, D, D]),
             "lbm_set_closure_floor": (I, [H, D]),
@@ -253,6 +256,36 @@ def lbm_stats_reset(h):
 
 def lbm_stats_sample(h):
     _check(load().lbm_stats_sample(h), h)
+
+
+def lbm_halo_bytes(h, face: int) -> int:
+    return int(load().lbm_halo_bytes(h, int(face)))
+
+
+def _raw_ptr(buf):
+    """Address of a contiguous torch tensor or numpy array (any dtype: the halo buffers hold
+    storage-precision values as raw bytes)."""
+    if type(buf).__module__.startswith("torch"):
+        if not buf.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(buf.data_ptr()), buf.numel() * buf.element_size()
+    if not isinstance(buf, np.ndarray) or not buf.flags.c_contiguous:
+        raise TypeError("expected a contiguous numpy array or torch tensor")
+    return ctypes.c_void_p(buf.ctypes.data), buf.nbytes
+
+
+def lbm_halo_pack(h, face: int, buf):
+    ptr, nbytes = _raw_ptr(buf)
+    if nbytes < lbm_halo_bytes(h, face):
+        raise ValueError("halo buffer too small")
+    _check(load().lbm_halo_pack(h, int(face), ptr), h)
+
+
+def lbm_halo_unpack(h, face: int, buf):
+    ptr, nbytes = _raw_ptr(buf)
+    if nbytes < lbm_halo_bytes(h, face):
+        raise ValueError("halo buffer too small")
+    _check(load().lbm_halo_unpack(h, int(face), ptr), h)
 
 
 def lbm_step_stats(h, n: int, every: int):
