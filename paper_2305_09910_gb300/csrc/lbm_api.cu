@@ -34,6 +34,13 @@ struct lbm_s {
   double* sums = nullptr;     // 4 doubles (lbm_reduce)
   double* partial = nullptr;  // nz * ny * 10 doubles: per-row sums of the reductions
   float* stats_w = nullptr;   // per-warp plane statistics of sampling steps (allocated on first use)
+  // CUDA graph of GRAPH_STEPS plain steps that lbm_step replays (captured on a private
+  // stream, keyed by the kernel parameters of its first step and the streaming state)
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  KParams gkey{};
+  int gkey_state[3] = {-1, -1, -1};  // parity, cur, nat_valid
+  bool graphs_off = false;
   double* stats = nullptr;    // ny * LBM_STATS_K doubles
   float* mlp = nullptr;       // MLP parameters widened to float
   float mlp_scale[2] = {0.f, 0.f};
@@ -379,6 +386,8 @@ lbm_status lbm_destroy(lbm_handle h) {
   if (h->stats) cudaFreeAsync(h->stats, h->stream);
   if (h->mlp) cudaFreeAsync(h->mlp, h->stream);
   cudaStreamSynchronize(h->stream);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->cap) cudaStreamDestroy(h->cap);
   if (h->status_host) cudaFreeHost(h->status_host);
   delete h;
   return LBM_OK;
@@ -626,9 +635,90 @@ static lbm_status run_steps(lbm_handle h, int64_t n, int64_t every) {
   return LBM_OK;
 }
 
+// ---- CUDA graph of plain steps ---------------------------------------------------------------
+// Small lattices are launch-bound: lbm_step replays a graph of GRAPH_STEPS steps (an even
+// number, so the streaming state returns to where it started) when the state is steady (pull
+// after its first step; AA once the outflow import state is settled) and the kernels are the
+// direct ones.  The graph is captured on a private stream and re-captured whenever the kernel
+// parameters of its first step differ (force, closure, flags, parity, arrays); replays give
+// the bits of single launches.
+constexpr int GRAPH_STEPS = 8;
+
+static void advance_state(lbm_handle h) {
+  if (h->prm.streaming == LBM_PULL) {
+    h->cur ^= 1;
+    h->parity = 2;
+  } else {
+    if (h->parity == 1) h->nat_valid = 0;
+    h->parity ^= 1;
+  }
+}
+
+static bool graph_ready(lbm_handle h) {
+  if (h->graphs_off || h->prm.pipeline != LBM_PIPE_DIRECT || h->prm.closure == LBM_CLOSURE_MLP) return false;
+  if (h->prm.streaming == LBM_PULL ? h->parity != 2 : (h->prm.face_bc[1] == LBM_FACE_OUTFLOW && h->nat_valid))
+    return false;
+  KParams p = kparams(h);
+  p.nat_valid = h->nat_valid;
+  const int state[3] = {h->parity, h->cur, h->nat_valid};
+  if (h->gexec && std::memcmp(&p, &h->gkey, sizeof p) == 0 && std::memcmp(state, h->gkey_state, sizeof state) == 0)
+    return true;
+  if (h->gexec) {
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
+  if (!h->cap && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    h->graphs_off = true;
+    return false;
+  }
+  const int saved[3] = {h->parity, h->cur, h->nat_valid};
+  cudaStream_t user = h->stream;
+  h->stream = h->cap;
+  cudaGraph_t graph = nullptr;
+  bool ok = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  for (int k = 0; ok && k < GRAPH_STEPS; k++) {
+    KParams q = kparams(h);
+    q.nat_valid = h->nat_valid;
+    ok = (h->q == 19 ? dispatch_step<19>(h, q, h->prm.closure, h->parity)
+                     : dispatch_step<27>(h, q, h->prm.closure, h->parity)) == cudaSuccess;
+    advance_state(h);
+  }
+  const bool ended = cudaStreamEndCapture(h->cap, &graph) == cudaSuccess;
+  h->stream = user;
+  h->parity = saved[0];
+  h->cur = saved[1];
+  h->nat_valid = saved[2];
+  ok = ok && ended && graph && cudaGraphInstantiate(&h->gexec, graph, 0) == cudaSuccess;
+  if (graph) cudaGraphDestroy(graph);
+  cudaGetLastError();  // a failed capture leaves no sticky error; fall back to launches
+  if (!ok) {
+    h->gexec = nullptr;
+    h->graphs_off = true;
+    return false;
+  }
+  h->gkey = p;
+  std::memcpy(h->gkey_state, state, sizeof state);
+  return true;
+}
+
 lbm_status lbm_step(lbm_handle h, int64_t n) {
   if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
   if (n < 0) return fail(h, LBM_EINVAL, "n must be >= 0");
+  if (h->prm.closure == LBM_CLOSURE_MLP && !h->mlp_set)
+    return fail(h, LBM_ESTATE, "MLP closure selected but lbm_set_closure was not called");
+  // settle the state with single launches first (the first pull step, the AA outflow import)
+  while (n > 0 && n >= 2 * GRAPH_STEPS && !graph_ready(h) && !h->graphs_off &&
+         (h->prm.streaming == LBM_PULL ? h->parity != 2 : h->nat_valid != 0) &&
+         h->prm.pipeline == LBM_PIPE_DIRECT && h->prm.closure != LBM_CLOSURE_MLP) {
+    lbm_status s = run_steps(h, 1, 0);
+    if (s != LBM_OK) return s;
+    n--;
+  }
+  while (n >= GRAPH_STEPS && graph_ready(h)) {
+    CUDA_TRY(h, cudaGraphLaunch(h->gexec, h->stream));
+    for (int k = 0; k < GRAPH_STEPS; k++) advance_state(h);
+    n -= GRAPH_STEPS;
+  }
   return run_steps(h, n, 0);
 }
 

@@ -521,3 +521,34 @@ def test_step_stats_rejects_bad_arguments():
     lbm.lbm_step_stats(lat.h, 0, 5)
     _, ns = lbm.lbm_stats_get(lat.h, 6)
     assert ns == 0
+
+
+@pytest.mark.parametrize("name,streaming,precision", [("tunnel19", "aa", "f32"), ("channel19", "pull", "f32"),
+                                                      ("channel27", "aa", "f16"), ("mixed19", "pull", "bf16")])
+def test_graph_replayed_steps_match_single_launches(name, streaming, precision):
+    """lbm_step(n) replays a CUDA graph of 8 steps on a steady state; the bits equal n single
+    launches, also across a change of the force between calls (the graph is re-captured)."""
+    from paper_2305_09910_gb300 import lbm
+
+    case = dict(CASES[name])
+    flags = case.pop("flags", None)
+    lats = []
+    for _ in range(2):
+        lat = lbm.Lattice(case["nx"], case["ny"], case["nz"], stencil=case.get("q", 19), tau=case["tau"],
+                          precision=precision, closure=case.get("closure", "none"), cs_smag=case.get("cs", 0.1),
+                          faces=case.get("faces", ("periodic",) * 6), u_inflow=case.get("u_w", (0, 0, 0)),
+                          streaming=streaming)
+        if flags is not None:
+            lat.set_flags(flags)
+        lat.set_force(*case.get("force", (0.0, 0.0, 0.0)))
+        lat.init_equilibrium()
+        lats.append(lat)
+    a, b = lats
+    for n, force in ((37, None), (16, (2e-5, 0.0, 0.0)), (21, None)):
+        if force is not None:
+            a.set_force(*force)
+            b.set_force(*force)
+        a.step(n)
+        for _ in range(n):
+            b.step(1)
+        assert np.array_equal(a.get_populations(), b.get_populations())
