@@ -45,6 +45,11 @@ def build(force: bool = False) -> str:
     return _SO
 
 
+def mrt_matrix():
+    """The oracle's 19 x 19 D3Q19 MRT moment basis M[k][i]."""
+    return np.array([[lib().ora_mrt_row(k, i) for i in range(19)] for k in range(19)])
+
+
 class _Cfg(ctypes.Structure):
     _fields_ = [
         ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
@@ -60,6 +65,8 @@ class _Cfg(ctypes.Structure):
         ("mlp", ctypes.c_void_p),
         ("mlp_scale", ctypes.c_double * 2),
         ("mlp_cs_min", ctypes.c_double),
+        ("collision", ctypes.c_int),
+        ("mrt_s", ctypes.c_double * 5),
     ]
 
 
@@ -75,6 +82,8 @@ def lib():
             L.ora_smag_tau.argtypes = [ctypes.c_double] * 4
             L.ora_smag_tau.restype = ctypes.c_double
             L.ora_collide.argtypes = [P, P, P, P]
+            L.ora_mrt_row.argtypes = [ctypes.c_int, ctypes.c_int]
+            L.ora_mrt_row.restype = ctypes.c_double
             L.ora_moments_cell.argtypes = [P, P, P, P]
             L.ora_check.argtypes = [P]
             L.ora_step.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int]
@@ -164,7 +173,8 @@ class Oracle:
 
     def __init__(self, nx, ny, nz, q=19, tau=0.8, lam=3.0 / 16.0, closure="none", cs=0.0,
                  faces=("periodic",) * 6, u_w=(0.0, 0.0, 0.0), rho_w=1.0,
-                 force=(0.0, 0.0, 0.0), flags=None, mlp=None, mlp_scale=(1.0, 1.0), mlp_cs_min=0.0):
+                 force=(0.0, 0.0, 0.0), flags=None, mlp=None, mlp_scale=(1.0, 1.0), mlp_cs_min=0.0,
+                 collision="trt", mrt_s=(1.19, 1.4, 1.2, 1.4, 1.98)):
         self.nx, self.ny, self.nz, self.q = int(nx), int(ny), int(nz), int(q)
         self.N = self.nx * self.ny * self.nz
         self._flags = None
@@ -191,6 +201,9 @@ class Oracle:
         c.mlp = None if self._mlp is None else self._mlp.ctypes.data
         c.mlp_scale[0], c.mlp_scale[1] = float(mlp_scale[0]), float(mlp_scale[1])
         c.mlp_cs_min = float(mlp_cs_min)
+        c.collision = {"trt": 0, "mrt": 1}[collision]
+        for k in range(5):
+            c.mrt_s[k] = float(mrt_s[k])
         self.cfg = c
         rc = lib().ora_check(ctypes.byref(c))
         if rc != 0:

@@ -208,6 +208,75 @@ void ora_mlp_features(const ora_cfg* cfg, const double* f, double* x) {
   x[6] = xclamp(cfg->mlp_scale[1] * (rho - 1.0));
 }
 
+/* ---- MRT collision (D3Q19) ----------------------------------------------------------------
+ * d'Humieres, Ginzburg, Krafczyk, Lallemand & Luo, "Multiple-relaxation-time lattice Boltzmann
+ * models in three dimensions", Phil. Trans. R. Soc. A 360 (2002) 437: moments m_k = sum_i M_ki f_i
+ * with the orthogonal polynomial rows below (c2 = |c_i|^2), each relaxed toward the moment of
+ * the equilibrium at its own rate s_k:
+ *   f* = f - M^-1 S M (f - f^eq) + M^-1 (I - S/2) M F,
+ * Guo's force F_i written in moment space.  The rows are orthogonal, so M^-1 = M^T diag(1/|M_k|^2). */
+double ora_mrt_row(int k, int i) {
+  const double cx = C27[i][0], cy = C27[i][1], cz = C27[i][2];
+  const double c2 = cx * cx + cy * cy + cz * cz;
+  switch (k) {
+    case 0: return 1.0;                                            /* rho */
+    case 1: return 19.0 * c2 - 30.0;                               /* e */
+    case 2: return (21.0 * c2 * c2 - 53.0 * c2 + 24.0) / 2.0;      /* eps */
+    case 3: return cx;                                             /* j_x */
+    case 4: return (5.0 * c2 - 9.0) * cx;                          /* q_x */
+    case 5: return cy;
+    case 6: return (5.0 * c2 - 9.0) * cy;
+    case 7: return cz;
+    case 8: return (5.0 * c2 - 9.0) * cz;
+    case 9: return 3.0 * cx * cx - c2;                             /* 3 p_xx */
+    case 10: return (3.0 * c2 - 5.0) * (3.0 * cx * cx - c2);       /* 3 pi_xx */
+    case 11: return cy * cy - cz * cz;                             /* p_ww */
+    case 12: return (3.0 * c2 - 5.0) * (cy * cy - cz * cz);        /* pi_ww */
+    case 13: return cx * cy;                                       /* p_xy */
+    case 14: return cy * cz;                                       /* p_yz */
+    case 15: return cx * cz;                                       /* p_xz */
+    case 16: return (cy * cy - cz * cz) * cx;                      /* m_x */
+    case 17: return (cz * cz - cx * cx) * cy;                      /* m_y */
+    default: return (cx * cx - cy * cy) * cz;                      /* m_z */
+  }
+}
+
+/* Rate of moment k: conserved moments 1 (they enter only through the force), stress moments
+ * 1/tau_eff, the others from cfg->mrt_s (e, eps, q, pi, m). */
+static double mrt_rate(const ora_cfg* cfg, int k, double tau) {
+  switch (k) {
+    case 0: case 3: case 5: case 7: return 1.0;
+    case 1: return cfg->mrt_s[0];
+    case 2: return cfg->mrt_s[1];
+    case 4: case 6: case 8: return cfg->mrt_s[2];
+    case 10: case 12: return cfg->mrt_s[3];
+    case 16: case 17: case 18: return cfg->mrt_s[4];
+    default: return 1.0 / tau; /* 9, 11, 13, 14, 15 */
+  }
+}
+
+static void mrt_collide(const ora_cfg* cfg, const double* f, const double* feq, const double* fi, double tau,
+                        double* fstar) {
+  double dm[19];
+  for (int k = 0; k < 19; k++) {
+    double m = 0.0, meq = 0.0, mf = 0.0, norm = 0.0;
+    for (int i = 0; i < 19; i++) {
+      const double r = ora_mrt_row(k, i);
+      m += r * f[i];
+      meq += r * feq[i];
+      mf += r * fi[i];
+      norm += r * r;
+    }
+    const double s = mrt_rate(cfg, k, tau);
+    dm[k] = (-s * (m - meq) + (1.0 - 0.5 * s) * mf) / norm;
+  }
+  for (int i = 0; i < 19; i++) {
+    double d = 0.0;
+    for (int k = 0; k < 19; k++) d += ora_mrt_row(k, i) * dm[k];
+    fstar[i] = f[i] + d;
+  }
+}
+
 void ora_collide(const ora_cfg* cfg, const double* f, double* fstar, double* tau_eff) {
   const int q = cfg->q;
   double rho, u[3], feq[27];
@@ -244,6 +313,10 @@ void ora_collide(const ora_cfg* cfg, const double* f, double* fstar, double* tau
     double cu = C27[i][0] * u[0] + C27[i][1] * u[1] + C27[i][2] * u[2];
     double cF = C27[i][0] * cfg->force[0] + C27[i][1] * cfg->force[1] + C27[i][2] * cfg->force[2];
     fi[i] = W_(q, i) * (3.0 * (cF - uF) + 9.0 * cu * cF);
+  }
+  if (cfg->collision == ORA_COLL_MRT) {
+    mrt_collide(cfg, f, feq, fi, tau, fstar);
+    return;
   }
   for (int i = 0; i < q; i++) {
     int j = OPP[i];
@@ -334,6 +407,12 @@ int ora_check(const ora_cfg* cfg) {
   }
   if (cfg->face[1] == ORA_FACE_OUTFLOW && cfg->nx < 2) return -7;
   if (cfg->closure == ORA_CLOSURE_MLP && !cfg->mlp) return -8;
+  if (cfg->collision != ORA_COLL_TRT && cfg->collision != ORA_COLL_MRT) return -9;
+  if (cfg->collision == ORA_COLL_MRT) {
+    if (cfg->q != 19) return -10;
+    for (int k = 0; k < 5; k++)
+      if (!(cfg->mrt_s[k] > 0.0 && cfg->mrt_s[k] < 2.0)) return -11;
+  }
   return 0;
 }
 

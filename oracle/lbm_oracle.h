@@ -38,6 +38,10 @@ enum {
   ORA_FACE_OUTFLOW = 4
 };
 enum { ORA_CLOSURE_NONE = 0, ORA_CLOSURE_SMAG = 1, ORA_CLOSURE_MLP = 2 };
+/* collision operator: TRT, or D3Q19 multiple-relaxation-time (MRT) in the orthogonal moment
+ * basis of d'Humieres, Ginzburg, Krafczyk, Lallemand & Luo (2002), the operator the paper's
+ * LAGOON runs use (Sec. 5.2) */
+enum { ORA_COLL_TRT = 0, ORA_COLL_MRT = 1 };
 
 /* MLP closure: 7 -> 32 -> 32 -> 1, parameters packed as
  * W1[32][7], b1[32], W2[32][32], b2[32], W3[32], b3[1]. */
@@ -60,6 +64,11 @@ typedef struct {
   const double* mlp;    /* ORA_MLP_NPARAM parameters (closure MLP) */
   double mlp_scale[2];  /* feature scales: stress components, density deviation */
   double mlp_cs_min;    /* lower bound on the learned C_s (0: none) */
+  int collision;        /* ORA_COLL_TRT (default) or ORA_COLL_MRT (D3Q19 only) */
+  /* MRT rates of the moment groups energy e, energy square eps, heat flux q, stress square
+   * pi and third-order m; the stress moments (3p_xx, p_ww, p_xy, p_yz, p_xz) relax with
+   * 1/tau_eff, the conserved density and momentum moments with rate 1 */
+  double mrt_s[5];
 } ora_cfg;
 
 /* Direction table in the published order; returns q or 0 on a bad q. */
@@ -70,6 +79,10 @@ void ora_equilibrium(int q, double rho, const double u[3], double* feq);
 
 /* Smagorinsky closed form: tau_eff = (tau0 + sqrt(tau0^2 + 18 sqrt2 cs2 sqrt(Qn)/rho))/2. */
 double ora_smag_tau(double tau0, double cs2, double qn, double rho);
+
+/* Row k of the D3Q19 MRT moment basis at direction i (k = 0..18: rho, e, eps, j_x, q_x, j_y,
+ * q_y, j_z, q_z, 3p_xx, 3pi_xx, p_ww, pi_ww, p_xy, p_yz, p_xz, m_x, m_y, m_z). */
+double ora_mrt_row(int k, int i);
 
 /* Collision of one cell (f -> f*).  tau_eff may be NULL. */
 void ora_collide(const ora_cfg* cfg, const double* f, double* fstar, double* tau_eff);
