@@ -157,14 +157,14 @@ def _barrier_max(dist, value):
     return float(t.item())
 
 
-def _channel_lattice(nx, ny, nz, precision, closure="smag", streaming="pull"):
+def _channel_lattice(nx, ny, nz, precision, closure="smag", streaming="pull", collision="trt"):
     import torch
 
     from paper_2305_09910_gb300 import inputs, lbm
 
     par = inputs.channel_parameters(ny)
     lat = lbm.Lattice(nx, ny, nz, stencil=19, tau=par["tau"], precision=precision, closure=closure,
-                      cs_smag=0.1, faces=FACES_CHANNEL, streaming=streaming)
+                      cs_smag=0.1, faces=FACES_CHANNEL, streaming=streaming, collision=collision)
     lat.set_force(par["force"])
     rho = torch.empty((nz, ny, nx), dtype=torch.float32, device="cuda")
     u = torch.empty((3, nz, ny, nx), dtype=torch.float32, device="cuda")
@@ -527,6 +527,9 @@ def main():
             torch.cuda.empty_cache()
         forms.update(_extra_forms(nsteps, args.warmup, peak, peak_kind))
         forms["channel512_f32_2slabs_halo"] = _slab_form(2, nsteps, args.warmup, peak, peak_kind)
+        fl, _ = _channel_lattice(nx, ny, nz, "f32", collision="mrt")
+        forms[f"channel{nx}_f32_mrt"] = _form_line(fl, nsteps, args.warmup, peak, peak_kind)
+        fl.close()
 
     if (nx, ny, nz, args.form, args.streaming, args.closure, channel) == (512, 256, 256, "f32", "pull", "smag", True):
         workload = WORKLOAD

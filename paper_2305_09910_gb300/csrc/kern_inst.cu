@@ -15,9 +15,17 @@
 namespace lbm {
 
 // stats: also write the warp-slot plane statistics of the starting state (p.stats_w); *nws
-// receives the number of warp slots per row.
+// receives the number of warp slots per row.  coll: 0 TRT, 1 MRT (D3Q19, one cell per thread).
 template <int Q, class S, int LOAD, int STORE, bool STATS>
-static void step_mode_s(const KParams& p, int closure, const Launch& L, int* nws) {
+static void step_mode_s(const KParams& p, int closure, const Launch& L, int coll, int* nws) {
+  if constexpr (Q == 19) {
+    if (coll == 1) {
+      if (nws) *nws = p.nxp / 32;
+      if (closure == CL_NONE) k_step<Q, S, CL_NONE, LOAD, STORE, STATS, 1><<<L.grid, L.block, 0, L.stream>>>(p);
+      else k_step<Q, S, CL_SMAG, LOAD, STORE, STATS, 1><<<L.grid, L.block, 0, L.stream>>>(p);
+      return;
+    }
+  }
   // half storage, D3Q19: x-pairs, 64 x per warp (for D3Q27 the pair kernel needs more
   // registers than it saves and the one-cell kernel is faster)
   if constexpr (sizeof(S) == 2 && Q == 19) {
@@ -34,19 +42,19 @@ static void step_mode_s(const KParams& p, int closure, const Launch& L, int* nws
 }
 
 template <int Q, class S, int LOAD, int STORE>
-static void step_mode(const KParams& p, int closure, const Launch& L, bool stats, int* nws) {
-  if (stats) step_mode_s<Q, S, LOAD, STORE, true>(p, closure, L, nws);
-  else step_mode_s<Q, S, LOAD, STORE, false>(p, closure, L, nws);
+static void step_mode(const KParams& p, int closure, const Launch& L, bool stats, int coll, int* nws) {
+  if (stats) step_mode_s<Q, S, LOAD, STORE, true>(p, closure, L, coll, nws);
+  else step_mode_s<Q, S, LOAD, STORE, false>(p, closure, L, coll, nws);
 }
 
 // mode: 0 AA even, 1 AA odd, 2 first pull step after an import, 3 pull step
 template <int Q, class S>
-cudaError_t launch_step(const KParams& p, int closure, int mode, const Launch& L, bool stats, int* nws) {
+cudaError_t launch_step(const KParams& p, int closure, int mode, const Launch& L, bool stats, int* nws, int coll) {
   switch (mode) {
-    case 0: step_mode<Q, S, 0, 0>(p, closure, L, stats, nws); break;
-    case 1: step_mode<Q, S, 1, 1>(p, closure, L, stats, nws); break;
-    case 2: step_mode<Q, S, 0, 2>(p, closure, L, stats, nws); break;
-    default: step_mode<Q, S, 2, 2>(p, closure, L, stats, nws); break;
+    case 0: step_mode<Q, S, 0, 0>(p, closure, L, stats, coll, nws); break;
+    case 1: step_mode<Q, S, 1, 1>(p, closure, L, stats, coll, nws); break;
+    case 2: step_mode<Q, S, 0, 2>(p, closure, L, stats, coll, nws); break;
+    default: step_mode<Q, S, 2, 2>(p, closure, L, stats, coll, nws); break;
   }
   return cudaGetLastError();
 }
@@ -79,7 +87,7 @@ static cudaError_t async_mode(const KParams& p, int closure, const Launch& L) {
 template <int Q, class S>
 cudaError_t launch_step_async(const KParams& p, int closure, int mode, const Launch& L) {
   if constexpr (!std::is_same<S, float>::value) {
-    return launch_step<Q, S>(p, closure, mode, L, false, nullptr);
+    return launch_step<Q, S>(p, closure, mode, L, false, nullptr, 0);
   } else {
     switch (mode) {
       case 0: return async_mode<Q, 0, 0>(p, closure, L);
@@ -201,7 +209,7 @@ cudaError_t launch_set_pop(const KParams& p, const float* df, const Launch& L) {
   return cudaGetLastError();
 }
 
-template cudaError_t launch_step<LBM_Q, LBM_S>(const KParams&, int, int, const Launch&, bool, int*);
+template cudaError_t launch_step<LBM_Q, LBM_S>(const KParams&, int, int, const Launch&, bool, int*, int);
 template cudaError_t launch_step_tma<LBM_Q, LBM_S>(const KParams&, int, int, cudaStream_t, int);
 template cudaError_t launch_step_zp<LBM_Q, LBM_S>(const KParams&, int, int, const Launch&);
 template cudaError_t launch_step_async<LBM_Q, LBM_S>(const KParams&, int, int, const Launch&);

@@ -153,19 +153,29 @@ static KParams kparams(const lbm_s* h) {
   p.mlp_scale[0] = h->mlp_scale[0];
   p.mlp_scale[1] = h->mlp_scale[1];
   p.cs2_min = (float)(h->cs_min * h->cs_min);
+  for (int k = 0; k < 5; k++) p.mrt_s[k] = (float)h->prm.mrt_rates[k];
   return p;
 }
 
 // True when the step kernel of this handle can sample the statistics itself (direct loads,
 // no learned closure); the other forms sample them in a separate pass before the step.
 static bool fused_stats(const lbm_s* h) {
-  return h->prm.pipeline == LBM_PIPE_DIRECT && h->prm.closure != LBM_CLOSURE_MLP;
+  return (h->prm.pipeline == LBM_PIPE_DIRECT || h->prm.collision == LBM_COLL_MRT) &&
+         h->prm.closure != LBM_CLOSURE_MLP;
 }
 
 template <int Q>
 static cudaError_t dispatch_step(const lbm_s* h, const KParams& p, int closure, int parity, bool stats = false,
                                  int* nws = nullptr) {
   const Launch L = launch_cfg(h);
+  if (h->prm.collision == LBM_COLL_MRT) {  // one kernel for every pipeline: the direct MRT step
+    const int mode = h->prm.streaming == LBM_PULL ? (parity == 0 ? 2 : 3) : parity;
+    switch (h->prm.precision) {
+      case LBM_F32: return launch_step<Q, float>(p, closure, mode, L, stats, nws, 1);
+      case LBM_F16_SHIFTED: return launch_step<Q, __half>(p, closure, mode, L, stats, nws, 1);
+      default: return launch_step<Q, __nv_bfloat16>(p, closure, mode, L, stats, nws, 1);
+    }
+  }
   if (closure == CL_MLP) {  // one kernel for every pipeline: the tensor-core closure step
     const int mode = h->prm.streaming == LBM_PULL ? (parity == 0 ? 2 : 3) : parity;
     switch (h->prm.precision) {
@@ -343,6 +353,9 @@ void lbm_params_default(lbm_params* p) {
   p->rho_inflow = 1.0;
   p->stream = nullptr;
   p->pipeline = LBM_PIPE_DIRECT;
+  p->collision = LBM_COLL_TRT;
+  const double rates[5] = {1.19, 1.4, 1.2, 1.4, 1.98};
+  for (int k = 0; k < 5; k++) p->mrt_rates[k] = rates[k];
 }
 
 int lbm_stencil(int q, int* c, double* w) {
@@ -419,6 +432,16 @@ lbm_status lbm_create(int nx, int ny, int nz, int stencil, double tau, const lbm
   if (p.pipeline < LBM_PIPE_TMA || p.pipeline > LBM_PIPE_ASYNC)
     return fail(nullptr, LBM_EINVAL, "unknown pipeline %d", p.pipeline);
   if (!(p.cs_smag >= 0.0)) return fail(nullptr, LBM_EINVAL, "cs_smag must be >= 0");
+  if (p.collision != LBM_COLL_TRT && p.collision != LBM_COLL_MRT)
+    return fail(nullptr, LBM_EINVAL, "unknown collision %d", p.collision);
+  if (p.collision == LBM_COLL_MRT) {
+    if (stencil != 19) return fail(nullptr, LBM_EUNSUPPORTED, "the MRT collision is defined for D3Q19");
+    if (p.closure == LBM_CLOSURE_MLP)
+      return fail(nullptr, LBM_EUNSUPPORTED, "the learned closure runs with the TRT collision");
+    for (int k = 0; k < 5; k++)
+      if (!(p.mrt_rates[k] > 0.0 && p.mrt_rates[k] < 2.0))
+        return fail(nullptr, LBM_EINVAL, "MRT rates must lie in (0, 2)");
+  }
   for (int k = 0; k < 6; k++)
     if (p.face_bc[k] < LBM_FACE_PERIODIC || p.face_bc[k] > LBM_FACE_HALO)
       return fail(nullptr, LBM_EINVAL, "unknown face type %d", p.face_bc[k]);

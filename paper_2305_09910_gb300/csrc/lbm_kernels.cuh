@@ -97,6 +97,7 @@ struct KParams {
   float F9w[27];          // 9 w_i (c_i . F): symmetric Guo term, times c_i . u
   float mlp_scale[2];
   float cs2_min;          // lower bound on the learned C_s^2 (0: none)
+  float mrt_s[5];         // MRT rates of the e, eps, q, pi and m moment groups
 };
 
 __device__ __forceinline__ int cidx(const KParams& p, int x, int y, int z) {
@@ -732,9 +733,154 @@ __device__ __forceinline__ void relax(const KParams& p, V (&f)[Q], const Macro<V
   }
 }
 
+// ---- MRT collision (D3Q19) ---------------------------------------------------------------
+// Multiple-relaxation-time operator in the orthogonal moment basis of d'Humieres, Ginzburg,
+// Krafczyk, Lallemand & Luo (2002), the collision of the paper's LAGOON runs (Sec. 5.2):
+// m_k = sum_i M_ki (f_i - f^eq_i) relaxes at rate s_k, Guo's force enters as (1 - s_k/2) M F,
+// and f* = f + M^T diag(1/|M_k|^2) dm (the rows are orthogonal).  Rows, with c2 = |c_i|^2:
+// rho, e = 19 c2 - 30, eps = (21 c2^2 - 53 c2 + 24)/2, j_a = c_a, q_a = (5 c2 - 9) c_a,
+// 3p_xx = 3 c_x^2 - c2, 3pi_xx = (3 c2 - 5)(3 c_x^2 - c2), p_ww = c_y^2 - c_z^2,
+// pi_ww = (3 c2 - 5)(c_y^2 - c_z^2), p_xy, p_yz, p_xz = c_a c_b, m_x = (c_y^2 - c_z^2) c_x,
+// m_y = (c_z^2 - c_x^2) c_y, m_z = (c_x^2 - c_y^2) c_z (all integer-valued).
+__host__ __device__ constexpr int mrt_row(int k, int i) {
+  const int x = cx(i), y = cy(i), z = cz(i), c2 = x * x + y * y + z * z;
+  return k == 0 ? 1 : k == 1 ? 19 * c2 - 30 : k == 2 ? (21 * c2 * c2 - 53 * c2 + 24) / 2
+       : k == 3 ? x : k == 4 ? (5 * c2 - 9) * x : k == 5 ? y : k == 6 ? (5 * c2 - 9) * y
+       : k == 7 ? z : k == 8 ? (5 * c2 - 9) * z : k == 9 ? 3 * x * x - c2
+       : k == 10 ? (3 * c2 - 5) * (3 * x * x - c2) : k == 11 ? y * y - z * z
+       : k == 12 ? (3 * c2 - 5) * (y * y - z * z) : k == 13 ? x * y : k == 14 ? y * z : k == 15 ? x * z
+       : k == 16 ? (y * y - z * z) * x : k == 17 ? (z * z - x * x) * y : (x * x - y * y) * z;
+}
+__host__ __device__ constexpr int mrt_norm(int k) {
+  int n = 0;
+  for (int i = 0; i < 19; i++) n += mrt_row(k, i) * mrt_row(k, i);
+  return n;
+}
+// rate group of moment k: -1 conserved (rate 1, the moment only carries the force),
+// -2 stress (1/tau_eff), 0..4 = e, eps, q, pi, m
+__host__ __device__ constexpr int mrt_group(int k) {
+  return (k == 0 || k == 3 || k == 5 || k == 7) ? -1 : k == 1 ? 0 : k == 2 ? 1
+       : (k == 4 || k == 6 || k == 8) ? 2 : (k == 10 || k == 12) ? 3 : k >= 16 ? 4 : -2;
+}
+
+// Moments of the populations from the +/- pair sums s_P = f_P + f_R and differences
+// a_P = f_P - f_R (P the primary member of a pair): even rows (rho, e, eps, p, pi) take the
+// same coefficient on both members, odd rows (j, q, m) opposite ones.
+__host__ __device__ constexpr bool mrt_even(int k) { return !(k >= 3 && k <= 8) && k < 16; }
+
+template <int K, int... P>
+__device__ __forceinline__ float mrt_pair_moment(float f0, const float (&sp)[9], const float (&ap)[9],
+                                                 std::integer_sequence<int, P...>) {
+  float m = (mrt_even(K) && mrt_row(K, 0) != 0) ? f0 * (float)mrt_row(K, 0) : 0.f;
+  ((m = mrt_row(K, prim(2 * P + 1)) != 0
+            ? vfma(mrt_even(K) ? sp[P] : ap[P], (float)mrt_row(K, prim(2 * P + 1)), m)
+            : m),
+   ...);
+  return m;
+}
+
+template <int... K>
+__device__ __forceinline__ void mrt_pair_moments(float f0, const float (&sp)[9], const float (&ap)[9],
+                                                 float (&m)[19], std::integer_sequence<int, K...>) {
+  ((m[K] = mrt_pair_moment<K>(f0, sp, ap, std::make_integer_sequence<int, 9>{})), ...);
+}
+
+// The update of pair P from the scaled moment increments dm: even part E, odd part O.
+template <int P>
+__device__ __forceinline__ void mrt_pair_back(float (&f)[19], const float (&dm)[19]) {
+  constexpr int I = 2 * P + 1, PP = prim(I), R = PP == I ? I + 1 : I;
+  float e = 0.f, o = 0.f;
+#pragma unroll
+  for (int k = 0; k < 19; k++) {
+    if (mrt_row(k, PP) == 0) continue;
+    if (mrt_even(k)) e = vfma(dm[k], (float)mrt_row(k, PP), e);
+    else o = vfma(dm[k], (float)mrt_row(k, PP), o);
+  }
+  f[PP] = vadd(f[PP], vadd(e, o));
+  f[R] = vadd(f[R], vsub(e, o));
+}
+
+template <int... P>
+__device__ __forceinline__ void mrt_pairs_back(float (&f)[19], const float (&dm)[19], std::integer_sequence<int, P...>) {
+  (mrt_pair_back<P>(f, dm), ...);
+}
+
+// With shifted populations df = f - w: m(df) = M f - M w, and the equilibrium and force
+// moments in closed form (the polynomial equilibrium and Guo's force on this lattice):
+//   rho: drho, 0;  e: -11 drho + 19 rho u^2, 38 u.F;  eps: 3 drho - 11/2 rho u^2, -11 u.F;
+//   j: rho u, F;  q: -2/3 rho u, -2/3 F;  3p_xx: rho (3u_x^2 - u^2), 6 u_x F_x - 2 u.F;
+//   3pi_xx: -1/2 of 3p_xx (both);  p_ww: rho (u_y^2 - u_z^2), 2 (u_y F_y - u_z F_z);
+//   pi_ww: -1/2 of p_ww;  p_ab: rho u_a u_b, u_a F_b + u_b F_a;  m: 0, 0.
+__device__ __forceinline__ void relax_mrt(const KParams& p, float (&f)[19], const Macro<float>& M, float wnu) {
+  float sp[9], ap[9];
+  {
+    // pair sums in the primary orientation
+    auto fill = [&](auto I_) {
+      constexpr int I = decltype(I_)::value;
+      constexpr int PP = prim(I), R = PP == I ? I + 1 : I;
+      sp[(I - 1) / 2] = vadd(f[PP], f[R]);
+      ap[(I - 1) / 2] = vsub(f[PP], f[R]);
+    };
+    fill(std::integral_constant<int, 1>{});
+    fill(std::integral_constant<int, 3>{});
+    fill(std::integral_constant<int, 5>{});
+    fill(std::integral_constant<int, 7>{});
+    fill(std::integral_constant<int, 9>{});
+    fill(std::integral_constant<int, 11>{});
+    fill(std::integral_constant<int, 13>{});
+    fill(std::integral_constant<int, 15>{});
+    fill(std::integral_constant<int, 17>{});
+  }
+  float m[19];
+  mrt_pair_moments(f[0], sp, ap, m, std::make_integer_sequence<int, 19>{});
+  const float ux = M.ux, uy = M.uy, uz = M.uz, rho = M.rho;
+  const float Fx = p.F[0], Fy = p.F[1], Fz = p.F[2];
+  const float u2 = vfma(uz, uz, vfma(uy, uy, vmul(ux, ux)));
+  const float uF = vfma(uz, Fz, vfma(uy, Fy, vmul(ux, Fx)));
+  const float ru2 = vmul(rho, u2);
+  const float p3xx = vmul(rho, vfma(3.f * ux, ux, -u2)), pww = vmul(rho, vsub(vmul(uy, uy), vmul(uz, uz)));
+  const float f3xx = vfma(6.f * ux, Fx, -2.f * uF), fww = 2.f * vsub(vmul(uy, Fy), vmul(uz, Fz));
+  float meq[19], mf[19];
+  meq[0] = M.drho;                         mf[0] = 0.f;
+  meq[1] = vfma(19.f, ru2, -11.f * M.drho); mf[1] = 38.f * uF;
+  meq[2] = vfma(-5.5f, ru2, 3.f * M.drho);  mf[2] = -11.f * uF;
+  meq[3] = M.jx;                           mf[3] = Fx;
+  meq[4] = (-2.f / 3.f) * M.jx;            mf[4] = (-2.f / 3.f) * Fx;
+  meq[5] = M.jy;                           mf[5] = Fy;
+  meq[6] = (-2.f / 3.f) * M.jy;            mf[6] = (-2.f / 3.f) * Fy;
+  meq[7] = M.jz;                           mf[7] = Fz;
+  meq[8] = (-2.f / 3.f) * M.jz;            mf[8] = (-2.f / 3.f) * Fz;
+  meq[9] = p3xx;                           mf[9] = f3xx;
+  meq[10] = -0.5f * p3xx;                  mf[10] = -0.5f * f3xx;
+  meq[11] = pww;                           mf[11] = fww;
+  meq[12] = -0.5f * pww;                   mf[12] = -0.5f * fww;
+  meq[13] = vmul(M.jx, uy);                mf[13] = vfma(ux, Fy, vmul(uy, Fx));
+  meq[14] = vmul(M.jy, uz);                mf[14] = vfma(uy, Fz, vmul(uz, Fy));
+  meq[15] = vmul(M.jx, uz);                mf[15] = vfma(ux, Fz, vmul(uz, Fx));
+  meq[16] = 0.f;                           mf[16] = 0.f;
+  meq[17] = 0.f;                           mf[17] = 0.f;
+  meq[18] = 0.f;                           mf[18] = 0.f;
+#pragma unroll
+  for (int k = 0; k < 19; k++) {
+    const int g = mrt_group(k);
+    const float s = g == -1 ? 1.f : g == -2 ? wnu : p.mrt_s[g];
+    // (the momentum rows of df lack the half force of j: m_j(df) - j = -F/2)
+    m[k] = vmul(vfma(-s, vsub(m[k], meq[k]), vmul(vfma(s, -0.5f, 1.f), mf[k])), 1.f / (float)mrt_norm(k));
+  }
+  {
+    float e0 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 19; k++)
+      if (mrt_even(k) && mrt_row(k, 0) != 0) e0 = vfma(m[k], (float)mrt_row(k, 0), e0);
+    f[0] = vadd(f[0], e0);
+  }
+  mrt_pairs_back(f, m, std::make_integer_sequence<int, 9>{});
+}
+
 // Stream-collide arithmetic of one cell (or two) without a learned closure: plain TRT or
 // TRT with the Smagorinsky relaxation time.  Returns rho.
-template <int Q, int CL, class V, bool ACC = true>
+// COLL: 0 TRT, 1 MRT (D3Q19, one cell per thread).
+template <int Q, int CL, class V, bool ACC = true, int COLL = 0>
 __device__ __forceinline__ V collide(const KParams& p, V (&f)[Q], Macro<V>* mout = nullptr) {
   static_assert(CL != CL_MLP, "the learned closure has its own kernel");
   using L = Lanes<V>;
@@ -750,7 +896,12 @@ __device__ __forceinline__ V collide(const KParams& p, V (&f)[Q], Macro<V>* mout
       L::put(wm, k, b);
     }
   }
-  relax<Q, V, ACC>(p, f, M, wp, wm);
+  if constexpr (COLL == 1) {
+    static_assert(Q == 19 && std::is_same<V, float>::value, "MRT: D3Q19, one cell per thread");
+    relax_mrt(p, f, M, wp);
+  } else {
+    relax<Q, V, ACC>(p, f, M, wp, wm);
+  }
   return M.rho;
 }
 
@@ -831,7 +982,7 @@ static __global__ void __launch_bounds__(256) k_stats_total(const float* stats_w
 
 // STATS: also write the plane statistics of the state this step starts from (warp slot
 // blockIdx.x of each row, nxp/32 slots per row).
-template <int Q, class S, int CL, int LOAD, int STORE, bool STATS = false>
+template <int Q, class S, int CL, int LOAD, int STORE, bool STATS = false, int COLL = 0>
 __global__ void __launch_bounds__(128, 8) k_step(const __grid_constant__ KParams p) {
   LBM_CELL_COORDS
   float f[Q];
@@ -844,7 +995,7 @@ __global__ void __launch_bounds__(128, 8) k_step(const __grid_constant__ KParams
   for (int k = 0; k < NSTAT; k++) v[k] = 0.f;
   if (cls != CLS_SKIP) {
     Macro<float> M;
-    const float rho = collide<Q, CL, float, acc_form<S>>(p, f, STATS ? &M : nullptr);
+    const float rho = collide<Q, CL, float, acc_form<S>, COLL>(p, f, STATS ? &M : nullptr);
     if (!(rho > 0.f && rho < 3.0e38f)) atomicOr(p.status, 1);
     store_state<Q, S, STORE>(p, x, y, z, cell, cls, f);
     if (STATS) stat_values(M, v);

@@ -17,7 +17,7 @@ struct Launch {
 
 template <int Q, class S>
 cudaError_t launch_step(const KParams& p, int closure, int parity, const Launch& L, bool stats = false,
-                        int* nws = nullptr);
+                        int* nws = nullptr, int coll = 0);
 template <int Q, class S>
 cudaError_t launch_step_tma(const KParams& p, int closure, int parity, cudaStream_t stream, int nsm);
 template <int Q, class S>
@@ -34,7 +34,7 @@ template <int Q, class S>
 cudaError_t launch_set_pop(const KParams& p, const float* df, const Launch& L);
 
 #define LBM_DECLARE_INSTANCE(Q, S)                                                                 \
-  extern template cudaError_t launch_step<Q, S>(const KParams&, int, int, const Launch&, bool, int*); \
+  extern template cudaError_t launch_step<Q, S>(const KParams&, int, int, const Launch&, bool, int*, int); \
   extern template cudaError_t launch_step_tma<Q, S>(const KParams&, int, int, cudaStream_t, int);  \
   extern template cudaError_t launch_step_zp<Q, S>(const KParams&, int, int, const Launch&);       \
   extern template cudaError_t launch_step_async<Q, S>(const KParams&, int, int, const Launch&);    \

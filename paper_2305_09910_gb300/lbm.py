@@ -26,6 +26,7 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ESTATE, LBM_EUNSUP
 PRECISION = {"f32": 0, "f16": 1, "bf16": 2}
 STREAMING = {"aa": 0, "pull": 1}
 PIPELINE = {"tma": 0, "direct": 1, "prefetch": 2, "async": 3}
+COLLISION = {"trt": 0, "mrt": 1}
 CLOSURE = {"none": 0, "smag": 1, "mlp": 2}
 FACE = {"periodic": 0, "wall": 1, "freeslip": 2, "inflow": 3, "outflow": 4, "halo": 5}
 CELL = {"fluid": 0, "solid": 1, "inflow": 2}
@@ -55,6 +56,8 @@ class lbm_params(ctypes.Structure):
         ("rho_inflow", ctypes.c_double),
         ("stream", ctypes.c_void_p),
         ("pipeline", ctypes.c_int32),
+        ("collision", ctypes.c_int32),
+        ("mrt_rates", ctypes.c_double * 5),
     ]
 
 
@@ -163,7 +166,8 @@ def _current_stream():
 
 def lbm_params_default(precision="f32", streaming="aa", closure="none", magic_lambda=3.0 / 16.0,
                        cs_smag=0.1, faces=("periodic",) * 6, u_inflow=(0.0, 0.0, 0.0),
-                       rho_inflow=1.0, stream=None, pipeline="direct") -> lbm_params:
+                       rho_inflow=1.0, stream=None, pipeline="direct", collision="trt",
+                       mrt_rates=None) -> lbm_params:
     p = lbm_params()
     load().lbm_params_default(ctypes.byref(p))
     p.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
@@ -178,6 +182,10 @@ def lbm_params_default(precision="f32", streaming="aa", closure="none", magic_la
     p.rho_inflow = float(rho_inflow)
     p.stream = stream if stream is not None else _current_stream()
     p.pipeline = PIPELINE[pipeline] if isinstance(pipeline, str) else int(pipeline)
+    p.collision = COLLISION[collision] if isinstance(collision, str) else int(collision)
+    if mrt_rates is not None:
+        for k in range(5):
+            p.mrt_rates[k] = float(mrt_rates[k])
     return p
 
 

@@ -14,19 +14,20 @@ FACES_TUNNEL = ("inflow", "outflow", "freeslip", "freeslip", "freeslip", "freesl
 
 def make_pair(nx, ny, nz, q=19, tau=0.8, lam=3.0 / 16.0, closure="none", cs=0.1,
               faces=("periodic",) * 6, u_w=(0.0, 0.0, 0.0), rho_w=1.0, force=(0.0, 0.0, 0.0),
-              flags=None, precision="f32", mlp=None, mlp_scale=(1.0, 1.0), pipeline="direct"):
+              flags=None, precision="f32", mlp=None, mlp_scale=(1.0, 1.0), pipeline="direct",
+              collision="trt", mrt_s=(1.19, 1.4, 1.2, 1.4, 1.98), streaming="aa"):
     import oracle
     from paper_2305_09910_gb300 import lbm
 
     lat = lbm.Lattice(nx, ny, nz, stencil=q, tau=tau, precision=precision, closure=closure,
                       magic_lambda=lam, cs_smag=cs, faces=faces, u_inflow=u_w, rho_inflow=rho_w,
-                      pipeline=pipeline)
+                      pipeline=pipeline, collision=collision, mrt_rates=mrt_s, streaming=streaming)
     if flags is not None:
         lat.set_flags(np.ascontiguousarray(flags, dtype=np.uint8))
     lat.set_force(*force)
     ora = oracle.Oracle(nx, ny, nz, q=q, tau=tau, lam=lam, closure=closure, cs=cs, faces=faces,
                         u_w=u_w, rho_w=rho_w, force=force, flags=flags, mlp=mlp,
-                        mlp_scale=mlp_scale)
+                        mlp_scale=mlp_scale, collision=collision, mrt_s=mrt_s)
     return lat, ora
 
 
