@@ -201,7 +201,8 @@ lbm_status lbm_step(lbm_handle h, int64_t n);
 
 /* Waits for the handle's stream.  LBM_EUNSTABLE if any step since the last state reset saw a
  * non-finite or non-positive density; LBM_ECUDA if a pipelined step gave up waiting for its
- * staged loads (a bounded wait that should never expire). */
+ * staged loads (a bounded wait that should never expire), or, in a library built with
+ * LBM_BOUNDS_CHECK (liblbm_check.so), if a kernel skipped an access outside its array. */
 lbm_status lbm_sync(lbm_handle h);
 
 /* Moments of the current state: rho (N floats) and u (3*N floats, includes +F/(2 rho)).

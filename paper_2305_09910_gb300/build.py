@@ -20,6 +20,9 @@ ROOT = os.path.dirname(PKG)
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "liblbm.so")
 BUILD = os.path.join(PKG, "_build")
+# variants: "check" = every global access of the direct kernels bounds-checked (a checked
+# access outside its array is skipped and reported by lbm_sync), for memory-safety tests
+VARIANTS = {None: ("liblbm.so", "_build", []), "check": ("liblbm_check.so", "_build_check", ["-DLBM_BOUNDS_CHECK"])}
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
@@ -49,23 +52,26 @@ def _digest(extra) -> str:
     return h.hexdigest()
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compiles (if needed) and returns the path of liblbm.so."""
-    extra = list(extra_flags)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), variant=None) -> str:
+    """Compiles (if needed) and returns the path of liblbm.so (or of a variant's library)."""
+    name, bdir, vflags = VARIANTS[variant]
+    lib_path = os.path.join(PKG, name)
+    build_dir = os.path.join(PKG, bdir)
+    extra = list(vflags) + list(extra_flags)
     digest = _digest(extra)
-    stamp = LIB + ".sha256"
-    if not force and os.path.exists(LIB) and os.path.exists(stamp):
+    stamp = lib_path + ".sha256"
+    if not force and os.path.exists(lib_path) and os.path.exists(stamp):
         with open(stamp) as fh:
             if fh.read().strip() == digest:
-                return LIB
+                return lib_path
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
-    jobs = [(os.path.join(CSRC, "lbm_api.cu"), os.path.join(BUILD, "lbm_api.o"), []),
-            (os.path.join(CSRC, "lbm_noalloc.cu"), os.path.join(BUILD, "lbm_noalloc.o"), []),
-            (os.path.join(CSRC, "lbm_closure.cu"), os.path.join(BUILD, "lbm_closure.o"), [])]
+    os.makedirs(build_dir, exist_ok=True)
+    jobs = [(os.path.join(CSRC, "lbm_api.cu"), os.path.join(build_dir, "lbm_api.o"), []),
+            (os.path.join(CSRC, "lbm_noalloc.cu"), os.path.join(build_dir, "lbm_noalloc.o"), []),
+            (os.path.join(CSRC, "lbm_closure.cu"), os.path.join(build_dir, "lbm_closure.o"), [])]
     for q, s in INSTANCES:
         tag = s.strip("_").replace("nv_", "")
-        jobs.append((os.path.join(CSRC, "kern_inst.cu"), os.path.join(BUILD, f"kern_q{q}_{tag}.o"),
+        jobs.append((os.path.join(CSRC, "kern_inst.cu"), os.path.join(build_dir, f"kern_q{q}_{tag}.o"),
                      [f"-DLBM_Q={q}", f"-DLBM_S={s}"]))
 
     def compile_one(job):
@@ -82,15 +88,15 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         for log in logs:
             if log:
                 sys.stderr.write(log)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp] + [j[1] for j in jobs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
-        raise RuntimeError(f"link of liblbm.so failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
+        raise RuntimeError(f"link of {name} failed:\n{r.stderr}")
+    os.replace(tmp, lib_path)
     with open(stamp, "w") as fh:
         fh.write(digest + "\n")
-    return LIB
+    return lib_path
 
 
 if __name__ == "__main__":

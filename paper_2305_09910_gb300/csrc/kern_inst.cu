@@ -27,7 +27,8 @@ static void step_mode_s(const KParams& p, int closure, const Launch& L, int coll
     }
   }
   // half storage, D3Q19: x-pairs, 64 x per warp (for D3Q27 the pair kernel needs more
-  // registers than it saves and the one-cell kernel is faster)
+  // registers than it saves, and on the bluff body the warps at the inflow and outflow faces
+  // take its one-cell fallback: the one-cell kernel is faster, measured)
   if constexpr (sizeof(S) == 2 && Q == 19) {
     dim3 g = L.grid;
     g.x = (p.nxp + 63) / 64;

@@ -30,6 +30,7 @@ struct lbm_s {
   uint8_t* cls = nullptr;     // cell classes, padded layout
   unsigned long long* rules = nullptr;  // per-direction rules of boundary cells, padded layout
   int* status = nullptr;      // device status word
+  int* chk_bad = nullptr;     // first out-of-range access seen by a bounds-checked build
   int* status_host = nullptr; // pinned copy
   double* sums = nullptr;     // 4 doubles (lbm_reduce)
   double* partial = nullptr;  // nz * ny * 10 doubles: per-row sums of the reductions
@@ -123,6 +124,20 @@ static KParams kparams(const lbm_s* h) {
   p.cls = h->cls;
   p.rules = h->rules;
   p.stats_w = h->stats_w;
+  {
+    const size_t fbytes = (size_t)plane_alloc(h) * h->q * store_bytes(h->prm.precision);
+    p.chk_lo[0] = (const char*)h->f;
+    p.chk_hi[0] = (const char*)h->f + fbytes;
+    p.chk_lo[1] = (const char*)h->f2;
+    p.chk_hi[1] = h->f2 ? (const char*)h->f2 + fbytes : nullptr;
+    p.chk_lo[2] = (const char*)h->flags;
+    p.chk_hi[2] = (const char*)h->flags + plane_alloc(h);
+    p.chk_lo[3] = (const char*)h->cls;
+    p.chk_hi[3] = (const char*)h->cls + plane_of(h);
+    p.chk_lo[4] = (const char*)h->rules;
+    p.chk_hi[4] = (const char*)h->rules + 8 * plane_of(h);
+    p.chk_bad = h->chk_bad;
+  }
   p.mlp = h->mlp;
   p.status = h->status;
   p.plane = plane_of(h);
@@ -286,7 +301,7 @@ __global__ void k_classify(const __grid_constant__ KParams p, uint8_t* cls, unsi
   const int z = blockIdx.z;
   if (y >= p.ny) return;
   const int cell = cidx(p, x, y, z);
-  if (x >= p.nx || p.flags[cell] != CELL_FLUID) {
+  if (x >= p.nx || flag_at(p, cell) != CELL_FLUID) {
     cls[cell] = CLS_SKIP;
     return;
   }
@@ -307,7 +322,7 @@ __global__ void k_classify(const __grid_constant__ KParams p, uint8_t* cls, unsi
         s[a] = s[a] < 0 ? s[a] + n[a] : s[a] - n[a];
       }
     }
-    if (c == CLS_INTERIOR && p.flags[cidx(p, s[0], s[1], s[2])] != CELL_FLUID) c = CLS_BOUNDARY;
+    if (c == CLS_INTERIOR && flag_at(p, cidx(p, s[0], s[1], s[2])) != CELL_FLUID) c = CLS_BOUNDARY;
   }
   if (c == CLS_INTERIOR && wrap_yz) c = CLS_WRAP;
   cls[cell] = (uint8_t)c;
@@ -393,6 +408,7 @@ lbm_status lbm_destroy(lbm_handle h) {
   if (h->cls) cudaFreeAsync(h->cls, h->stream);
   if (h->rules) cudaFreeAsync(h->rules, h->stream);
   if (h->status) cudaFreeAsync(h->status, h->stream);
+  if (h->chk_bad) cudaFreeAsync(h->chk_bad, h->stream);
   if (h->sums) cudaFreeAsync(h->sums, h->stream);
   if (h->partial) cudaFreeAsync(h->partial, h->stream);
   if (h->stats_w) cudaFreeAsync(h->stats_w, h->stream);
@@ -489,6 +505,8 @@ lbm_status lbm_create(int nx, int ny, int nz, int stencil, double tau, const lbm
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->cls, (size_t)plane, h->stream);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->rules, (size_t)plane * 8, h->stream);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->status, sizeof(int), h->stream);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->chk_bad, sizeof(int), h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->chk_bad, 0, sizeof(int), h->stream);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->sums, 4 * sizeof(double), h->stream);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->partial, (size_t)ny * nz * 10 * sizeof(double), h->stream);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->stats, (size_t)ny * LBM_STATS_K * sizeof(double), h->stream);
@@ -833,6 +851,14 @@ lbm_status lbm_sync(lbm_handle h) {
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   if (*h->status_host & 2)
     return fail(h, LBM_ECUDA, "a pipelined step timed out waiting for its staged loads");
+#ifdef LBM_BOUNDS_CHECK
+  int bad = 0;
+  CUDA_TRY(h, cudaMemcpy(&bad, h->chk_bad, sizeof(int), cudaMemcpyDeviceToHost));
+  if (bad) {
+    static const char* names[5] = {"populations", "populations", "flags", "classes", "rules"};
+    return fail(h, LBM_ECUDA, "bounds check: an access outside the %s array was skipped", names[(bad - 1) % 5]);
+  }
+#endif
   if (*h->status_host & 1)
     return fail(h, LBM_EUNSTABLE, "a step produced a non-finite or non-positive density");
   return LBM_OK;

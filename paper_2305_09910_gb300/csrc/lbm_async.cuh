@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(128, LBM_ASYNC_MINB) k_step_async(const __grid
     else cp_async_commit();
     cp_async_wait<NST - 1>();  // the group of cell z is complete
     const int cell = cidx(p, x, y, z);
-    const int cls = x < p.nx ? p.cls[cell] : CLS_SKIP;
+    const int cls = x < p.nx ? cls_at(p, cell) : CLS_SKIP;
     float f[Q];
     unsigned outmask = 0;
     const bool staged = LOAD == 0 ? (cls == CLS_INTERIOR || cls == CLS_WRAP) : (cls == CLS_INTERIOR && inner_row(p, y, z));

@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(128) k_closure_samples(const __grid_constant__
   for (int n = 0; n < 8; n++) {
     const int fx = 2 * X + (n & 1), fy = 2 * Y + ((n >> 1) & 1), fz = 2 * Z + (n >> 2);
     const int cell = cidx(p, fx, fy, fz);
-    const int cls = p.cls[cell];
+    const int cls = cls_at(p, cell);
     float f[Q];
     unsigned outmask;
     load_state<Q, S, PAR>(p, fx, fy, fz, cell, cls, f, outmask);
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(128) k_filter2(const __grid_constant__ KParams
   for (int n = 0; n < 8; n++) {
     const int fx = 2 * X + (n & 1), fy = 2 * Y + ((n >> 1) & 1), fz = 2 * Z + (n >> 2);
     const int cell = cidx(p, fx, fy, fz);
-    const int cls = p.cls[cell];
+    const int cls = cls_at(p, cell);
     if (cls == CLS_SKIP) continue;
     float f[Q];
     unsigned outmask;

@@ -50,6 +50,20 @@ template <> __device__ __forceinline__ uint32_t bits16<__nv_bfloat16>(float v) {
   return __bfloat16_as_ushort(__float2bfloat16_rn(v));
 }
 
+// Checked 32-bit (two cells) and 16-bit (one cell) population accesses.
+__device__ __forceinline__ uint32_t ld32(const KParams& p, const void* a) {
+  return chk(p, a, 4, CHK_POP) ? *static_cast<const uint32_t*>(a) : 0u;
+}
+__device__ __forceinline__ void st32(const KParams& p, void* a, uint32_t v) {
+  if (chk(p, a, 4, CHK_POP)) *static_cast<uint32_t*>(a) = v;
+}
+__device__ __forceinline__ uint32_t ld16(const KParams& p, const void* a) {
+  return chk(p, a, 2, CHK_POP) ? *static_cast<const unsigned short*>(a) : 0u;
+}
+__device__ __forceinline__ void st16(const KParams& p, void* a, uint32_t v) {
+  if (chk(p, a, 2, CHK_POP)) *static_cast<unsigned short*>(a) = (unsigned short)v;
+}
+
 // Zero-gradient outflow for x-pairs: cell x-1 of lane t's first cell is lane t-1's second.
 template <int Q>
 __device__ __forceinline__ void outflow_fix2(const KParams& p, int x0, float (&fa)[Q], float (&fb)[Q],
@@ -125,7 +139,7 @@ __global__ void __launch_bounds__(128, LBM_H2_MINB) k_step_h2(const __grid_const
   const int cell = cidx(p, x, y, z);
   int ca_ = CLS_SKIP, cb_ = CLS_SKIP;
   if (x < p.nx) {
-    const unsigned c2 = *reinterpret_cast<const unsigned short*>(p.cls + cell);
+    const unsigned c2 = chk(p, p.cls + cell, 2, CHK_CLS) ? *reinterpret_cast<const unsigned short*>(p.cls + cell) : 0x0202u;
     ca_ = c2 & 0xff;
     cb_ = x + 1 < p.nx ? (int)(c2 >> 8) : CLS_SKIP;
   }
@@ -140,16 +154,16 @@ __global__ void __launch_bounds__(128, LBM_H2_MINB) k_step_h2(const __grid_const
 #pragma unroll
     for (int i = 0; i < Q; i++) {
       if (LOAD == 0) {
-        h[i] = *reinterpret_cast<const uint32_t*>(plane_ptr<S>(p, i) + cell);
+        h[i] = ld32(p, plane_ptr<S>(p, i) + cell);
       } else {
         const S* base = static_cast<const S*>(LOAD == 2 ? p.gb[i] : p.ga[i]);
         if (cx(i) == 0) {
-          h[i] = *reinterpret_cast<const uint32_t*>(base + cell);
+          h[i] = ld32(p, base + cell);
         } else {
           int a, b;
           xsrc(cx(i), p, x, cell, a, b);
-          const uint32_t lo = *reinterpret_cast<const unsigned short*>(base + a);
-          const uint32_t hi = *reinterpret_cast<const unsigned short*>(base + b);
+          const uint32_t lo = ld16(p, base + a);
+          const uint32_t hi = ld16(p, base + b);
           h[i] = lo | (hi << 16);
         }
       }
@@ -201,19 +215,19 @@ __global__ void __launch_bounds__(128, LBM_H2_MINB) k_step_h2(const __grid_const
 #pragma unroll
     for (int i = 0; i < Q; i++) {
       if (STORE == 0) {
-        *reinterpret_cast<uint32_t*>(plane_ptr<S>(p, opp(i)) + cell) = h[i];
+        st32(p, plane_ptr<S>(p, opp(i)) + cell, h[i]);
       } else if (STORE == 2) {
-        *reinterpret_cast<uint32_t*>(static_cast<S*>(p.fq[i]) + cell) = h[i];
+        st32(p, static_cast<S*>(p.fq[i]) + cell, h[i]);
       } else {  // back into the slots the gather of direction i read: f*_opp(i)
         S* base = static_cast<S*>(p.ga[i]);
         const uint32_t w = h[opp(i)];
         if (cx(i) == 0) {
-          *reinterpret_cast<uint32_t*>(base + cell) = w;
+          st32(p, base + cell, w);
         } else {
           int a, b;
           xsrc(cx(i), p, x, cell, a, b);
-          *reinterpret_cast<unsigned short*>(base + a) = (unsigned short)(w & 0xffffu);
-          *reinterpret_cast<unsigned short*>(base + b) = (unsigned short)(w >> 16);
+          st16(p, base + a, w & 0xffffu);
+          st16(p, base + b, w >> 16);
         }
       }
     }

@@ -98,7 +98,45 @@ struct KParams {
   float mlp_scale[2];
   float cs2_min;          // lower bound on the learned C_s^2 (0: none)
   float mrt_s[5];         // MRT rates of the e, eps, q, pi and m moment groups
+  // bounds-checked builds (LBM_BOUNDS_CHECK): byte ranges of the population arrays (0, 1),
+  // flags (2), classes (3) and rules (4), and the word that records the first bad access
+  const char* chk_lo[5];
+  const char* chk_hi[5];
+  int* chk_bad;
 };
+
+// ---- checked accesses --------------------------------------------------------------------
+// With LBM_BOUNDS_CHECK every global access of the step, export and set-up kernels checks its
+// address against the array it belongs to; an access outside is skipped (a load gives 0) and
+// the first one is recorded in *chk_bad as 1 + the array index (lbm_sync reports it).  Without
+// it the checks compile away.
+enum : int { CHK_POP = 0, CHK_FLAGS = 2, CHK_CLS = 3, CHK_RULES = 4 };
+
+__device__ __forceinline__ bool chk(const KParams& p, const void* a, int bytes, int kind) {
+#ifdef LBM_BOUNDS_CHECK
+  const char* c = static_cast<const char*>(a);
+  bool ok;
+  if (kind == CHK_POP)
+    ok = (c >= p.chk_lo[0] && c + bytes <= p.chk_hi[0]) || (p.chk_lo[1] && c >= p.chk_lo[1] && c + bytes <= p.chk_hi[1]);
+  else
+    ok = c >= p.chk_lo[kind] && c + bytes <= p.chk_hi[kind];
+  if (!ok) atomicCAS(p.chk_bad, 0, 1 + kind);
+  return ok;
+#else
+  (void)p; (void)a; (void)bytes; (void)kind;
+  return true;
+#endif
+}
+
+__device__ __forceinline__ int cls_at(const KParams& p, long long cell) {
+  return chk(p, p.cls + cell, 1, CHK_CLS) ? p.cls[cell] : CLS_SKIP;
+}
+__device__ __forceinline__ int flag_at(const KParams& p, long long cell) {
+  return chk(p, p.flags + cell, 1, CHK_FLAGS) ? p.flags[cell] : CELL_SOLID;
+}
+__device__ __forceinline__ unsigned long long rule_at(const KParams& p, long long cell) {
+  return chk(p, p.rules + cell, 8, CHK_RULES) ? p.rules[cell] : 0ull;
+}
 
 __device__ __forceinline__ int cidx(const KParams& p, int x, int y, int z) {
   return (z * p.ny + y) * p.nxp + x;
@@ -116,6 +154,16 @@ template <> __device__ __forceinline__ void st<float>(float* a, float v) { *a = 
 template <> __device__ __forceinline__ void st<__half>(__half* a, float v) { *a = __float2half_rn(v); }
 template <> __device__ __forceinline__ void st<__nv_bfloat16>(__nv_bfloat16* a, float v) {
   *a = __float2bfloat16_rn(v);
+}
+
+// Population accesses of global memory (checked in bounds-checked builds).
+template <class S>
+__device__ __forceinline__ float ldp(const KParams& p, const S* a) {
+  return chk(p, a, (int)sizeof(S), CHK_POP) ? ld<S>(a) : 0.f;
+}
+template <class S>
+__device__ __forceinline__ void stp(const KParams& p, S* a, float v) {
+  if (chk(p, a, (int)sizeof(S), CHK_POP)) st<S>(a, v);
 }
 
 // Value after a round trip through the storage precision.
@@ -156,7 +204,7 @@ static __device__ __noinline__ int classify(const KParams& p, int x, int y, int 
   cell = cidx(p, x, y, z);
   if (rank == 4) return K_BB;
   if (rank == 3) return K_INFLOW;
-  if (rank == 2) return p.flags[cidx(p, x - 1, y, z)] == CELL_FLUID ? K_OUTCOPY : K_BB;
+  if (rank == 2) return flag_at(p, cidx(p, x - 1, y, z)) == CELL_FLUID ? K_OUTCOPY : K_BB;
   int d[3];
   for (int a = 0; a < 3; a++) {
     d[a] = c[a];
@@ -170,7 +218,7 @@ static __device__ __noinline__ int classify(const KParams& p, int x, int y, int 
     }
   }
   const int src = cidx(p, s[0], s[1], s[2]);
-  const int fl = p.flags[src];
+  const int fl = flag_at(p, src);
   if (fl == CELL_SOLID) return K_BB;
   if (fl == CELL_INFLOW) return K_INFLOW;
   plane = opp(dir_index(d[0], d[1], d[2]));
@@ -254,11 +302,11 @@ __device__ __forceinline__ void load_state(const KParams& p, int x, int y, int z
   if (cls == CLS_SKIP) return;
   if (PAR == 0) {
 #pragma unroll
-    for (int i = 0; i < Q; i++) f[i] = ld<S>(plane_ptr<S>(p, i) + cell);
+    for (int i = 0; i < Q; i++) f[i] = ldp<S>(p, plane_ptr<S>(p, i) + cell);
     // after a streaming step the outflow slots of x = nx-1 were not written (they are
     // copies of the upstream cell); after an import they hold the imported values
     if (cls == CLS_BOUNDARY && p.outflow && !p.nat_valid && x == p.nx - 1) {
-      const unsigned long long r = p.rules[cell];
+      const unsigned long long r = rule_at(p, cell);
 #pragma unroll
       for (int i = 0; i < Q; i++)
         if (cx(i) == -1 && ((r >> (2 * i)) & 3) == R_SPECIAL) outmask |= 1u << i;
@@ -270,16 +318,16 @@ __device__ __forceinline__ void load_state(const KParams& p, int x, int y, int z
 #pragma unroll
     for (int i = 0; i < Q; i++) {
       const S* base = static_cast<const S*>(PAR == 2 ? p.gb[i] : p.ga[i]);
-      f[i] = ld<S>(base + (cx(i) > 0 ? cp : cx(i) < 0 ? cm : cell));
+      f[i] = ldp<S>(p, base + (cx(i) > 0 ? cp : cx(i) < 0 ? cm : cell));
     }
   } else if (cls == CLS_WRAP) {
     Nbr nb;
     nb.init(p, x, y, z);
 #pragma unroll
-    for (int i = 0; i < Q; i++) f[i] = ld<S>(plane_ptr<S>(p, PAR == 2 ? i : opp(i)) + nb.src(p, i));
+    for (int i = 0; i < Q; i++) f[i] = ldp<S>(p, plane_ptr<S>(p, PAR == 2 ? i : opp(i)) + nb.src(p, i));
   } else {
     // boundary cell: the precomputed rules make every load independent of the others
-    const unsigned long long r = p.rules[cell];
+    const unsigned long long r = rule_at(p, cell);
     Nbr nb;
     nb.init(p, x, y, z);
     unsigned special = 0;
@@ -292,7 +340,7 @@ __device__ __forceinline__ void load_state(const KParams& p, int x, int y, int z
       }
       const S* a = k == R_STREAM ? plane_ptr<S>(p, PAR == 2 ? i : opp(i)) + nb.src(p, i)
                                  : plane_ptr<S>(p, PAR == 2 ? opp(i) : i) + cell;
-      float v = ld<S>(a);
+      float v = ldp<S>(p, a);
       // moving-wall value rounded like the natural-layout slot that holds it
       if (k == R_INFLOW) v = rnd<S>(v + p.inflow_term[i]);
       f[i] = v;
@@ -303,7 +351,7 @@ __device__ __forceinline__ void load_state(const KParams& p, int x, int y, int z
         if (!(special & (1u << i))) continue;
         int pl, ce;
         if (resolve_special(p, x, y, z, i, pl, ce) == K_OUTCOPY) outmask |= 1u << i;
-        else f[i] = ld<S>(plane_ptr<S>(p, PAR == 2 ? opp(pl) : pl) + ce);
+        else f[i] = ldp<S>(p, plane_ptr<S>(p, PAR == 2 ? opp(pl) : pl) + ce);
       }
     }
   }
@@ -333,23 +381,23 @@ __device__ __forceinline__ void store_state(const KParams& p, int x, int y, int 
                                             const float (&fs)[Q]) {
   if (PAR == 2) {
 #pragma unroll
-    for (int i = 0; i < Q; i++) st<S>(static_cast<S*>(p.fq[i]) + cell, fs[i]);
+    for (int i = 0; i < Q; i++) stp<S>(p, static_cast<S*>(p.fq[i]) + cell, fs[i]);
   } else if (PAR == 0) {
 #pragma unroll
-    for (int i = 0; i < Q; i++) st<S>(plane_ptr<S>(p, opp(i)) + cell, fs[i]);
+    for (int i = 0; i < Q; i++) stp<S>(p, plane_ptr<S>(p, opp(i)) + cell, fs[i]);
   } else if (cls == CLS_INTERIOR) {
     const int cp = cell + (x == 0 ? p.nx : 0);
     const int cm = cell - (x == p.nx - 1 ? p.nx : 0);
 #pragma unroll
     for (int i = 0; i < Q; i++)
-      st<S>(static_cast<S*>(p.ga[i]) + (cx(i) > 0 ? cp : cx(i) < 0 ? cm : cell), fs[opp(i)]);
+      stp<S>(p, static_cast<S*>(p.ga[i]) + (cx(i) > 0 ? cp : cx(i) < 0 ? cm : cell), fs[opp(i)]);
   } else if (cls == CLS_WRAP) {
     Nbr nb;
     nb.init(p, x, y, z);
 #pragma unroll
-    for (int i = 0; i < Q; i++) st<S>(plane_ptr<S>(p, opp(i)) + nb.src(p, i), fs[opp(i)]);
+    for (int i = 0; i < Q; i++) stp<S>(p, plane_ptr<S>(p, opp(i)) + nb.src(p, i), fs[opp(i)]);
   } else {
-    const unsigned long long r = p.rules[cell];
+    const unsigned long long r = rule_at(p, cell);
     Nbr nb;
     nb.init(p, x, y, z);
 #pragma unroll
@@ -364,7 +412,7 @@ __device__ __forceinline__ void store_state(const KParams& p, int x, int y, int 
       }
       float v = fs[opp(i)];
       if (k == R_INFLOW) v = rnd<S>(v) + p.inflow_term[i];  // same rounding as the swapped path
-      st<S>(plane_ptr<S>(p, pl) + ce, v);
+      stp<S>(p, plane_ptr<S>(p, pl) + ce, v);
     }
   }
 }
@@ -913,7 +961,7 @@ __device__ __forceinline__ V collide(const KParams& p, V (&f)[Q], Macro<V>* mout
   const int z = blockIdx.z;                               \
   if (y >= p.ny) return; /* whole warp */                 \
   const int cell = cidx(p, x, y, z);                      \
-  const int cls = x < p.nx ? p.cls[cell] : CLS_SKIP;
+  const int cls = x < p.nx ? cls_at(p, cell) : CLS_SKIP;
 
 // LOAD / STORE modes as in load_state / store_state: AA even (0, 0), AA odd (1, 1), first
 // pull step after an import (0, 2), pull step (2, 2).
@@ -1017,7 +1065,7 @@ __global__ void __launch_bounds__(128, 5) k_step_zp(const __grid_constant__ KPar
   float f[Q], g[Q];
   unsigned outmask, outmask_g = 0;
   int cell = cidx(p, x, y, z0);
-  int cls = x < p.nx ? p.cls[cell] : CLS_SKIP;
+  int cls = x < p.nx ? cls_at(p, cell) : CLS_SKIP;
   load_state<Q, S, PAR>(p, x, y, z0, cell, cls, f, outmask);
 #pragma unroll 1
   for (int z = z0; z < zend; z++) {
@@ -1025,7 +1073,7 @@ __global__ void __launch_bounds__(128, 5) k_step_zp(const __grid_constant__ KPar
     int celln = 0, clsn = CLS_SKIP;
     if (zn < zend) {
       celln = cidx(p, x, y, zn);
-      clsn = x < p.nx ? p.cls[celln] : CLS_SKIP;
+      clsn = x < p.nx ? cls_at(p, celln) : CLS_SKIP;
       load_state<Q, S, PAR>(p, x, y, zn, celln, clsn, g, outmask_g);
     }
     outflow_fix<Q>(p, x, f, outmask);
@@ -1114,7 +1162,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_row_sums(const __grid_constant_
     if (xb + warp * 32 >= p.nxp) break;  // warp-uniform (nxp is a multiple of 32)
     const int x = xb + threadIdx.x;
     const int cell = cidx(p, x, y, z);
-    const int cls = x < p.nx ? p.cls[cell] : CLS_SKIP;
+    const int cls = x < p.nx ? cls_at(p, cell) : CLS_SKIP;
     float f[Q];
     unsigned outmask;
     load_state<Q, S, PAR>(p, x, y, z, cell, cls, f, outmask);
@@ -1209,7 +1257,7 @@ __global__ void __launch_bounds__(128) k_init_eq(const __grid_constant__ KParams
   for (int i = 0; i < Q; i++) {
     const float cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
     const float v = wgt<Q>(i) * (drho + rho * (3.f * cu + 4.5f * cu * cu - 1.5f * usq));
-    st<S>(plane_ptr<S>(p, i) + cell, fluid ? v : 0.f);
+    stp<S>(p, plane_ptr<S>(p, i) + cell, fluid ? v : 0.f);
   }
 }
 
@@ -1222,7 +1270,7 @@ __global__ void __launch_bounds__(128) k_set_pop(const __grid_constant__ KParams
   const long long N = (long long)p.nx * p.ny * p.nz;
   const bool fluid = cls != CLS_SKIP;
 #pragma unroll
-  for (int i = 0; i < Q; i++) st<S>(plane_ptr<S>(p, i) + cell, fluid ? df[i * N + dense] : 0.f);
+  for (int i = 0; i < Q; i++) stp<S>(p, plane_ptr<S>(p, i) + cell, fluid ? df[i * N + dense] : 0.f);
 }
 
 }  // namespace lbm

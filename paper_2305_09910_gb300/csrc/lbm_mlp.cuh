@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(128 * MLP_NG, 1) k_step_mlp(const __grid_const
     const int y = by * 4 + (warp & 3);
     const bool row = y < p.ny;  // warp-uniform
     const int cell = row ? cidx(p, x, y, z) : 0;
-    const int cls = (row && x < p.nx) ? p.cls[cell] : CLS_SKIP;
+    const int cls = (row && x < p.nx) ? cls_at(p, cell) : CLS_SKIP;
     float f[Q];
     unsigned outmask;
     load_state<Q, S, LOAD>(p, x, y, z, cell, cls, f, outmask);
