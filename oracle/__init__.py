@@ -88,6 +88,7 @@ def lib():
             L.ora_check.argtypes = [P]
             L.ora_step.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int]
             L.ora_stream.argtypes = [P, P, P, ctypes.c_int]
+            L.ora_collide_all.argtypes = [P, P, P, ctypes.c_int]
             L.ora_init_equilibrium.argtypes = [P, P, P, P]
             L.ora_moments.argtypes = [P, P, P, P]
             L.ora_mass_momentum.argtypes = [P, P, P]
@@ -249,6 +250,14 @@ class Oracle:
         fstar = np.ascontiguousarray(fstar, dtype=np.float64).reshape(self.f.shape)
         if lib().ora_stream(ctypes.byref(self.cfg), _ptr(fstar), _ptr(self.f), int(threads)) != 0:
             raise RuntimeError("oracle stream failed")
+
+    def collide_all(self, f=None, threads=1):
+        """Eq. LBCollision alone on every fluid cell of f (default: the state); returns f*."""
+        f = self.f if f is None else np.ascontiguousarray(f, dtype=np.float64).reshape(self.f.shape)
+        out = np.empty_like(f)
+        if lib().ora_collide_all(ctypes.byref(self.cfg), _ptr(f), _ptr(out), int(threads)) != 0:
+            raise RuntimeError("oracle collision failed")
+        return out
 
     def moments(self):
         rho = np.empty((self.nz, self.ny, self.nx), dtype=np.float64)

@@ -447,27 +447,33 @@ int ora_stream(const ora_cfg* cfg, const double* fstar, double* f, int nthreads)
   return 0;
 }
 
-int ora_step(const ora_cfg* cfg, double* f, double* work, int64_t nsteps, int nthreads) {
+int ora_collide_all(const ora_cfg* cfg, const double* f, double* fstar, int nthreads) {
   if (ora_check(cfg) != 0) return -1;
   const int q = cfg->q;
   const int64_t N = (int64_t)cfg->nx * cfg->ny * cfg->nz;
   if (nthreads < 1) nthreads = 1;
-  for (int64_t t = 0; t < nsteps; t++) {
-    /* Eq. LBCollision on every non-solid cell */
+  /* Eq. LBCollision on every fluid cell */
 #pragma omp parallel for num_threads(nthreads) schedule(static)
-    for (int z = 0; z < cfg->nz; z++)
-      for (int y = 0; y < cfg->ny; y++)
-        for (int x = 0; x < cfg->nx; x++) {
-          int64_t c = cell_index(cfg, x, y, z);
-          double fl[27], fs[27];
-          if (cell_flag(cfg, x, y, z) != ORA_CELL_FLUID) {
-            for (int i = 0; i < q; i++) work[i * N + c] = 0.0;
-            continue;
-          }
-          for (int i = 0; i < q; i++) fl[i] = f[i * N + c];
-          ora_collide(cfg, fl, fs, NULL);
-          for (int i = 0; i < q; i++) work[i * N + c] = fs[i];
+  for (int z = 0; z < cfg->nz; z++)
+    for (int y = 0; y < cfg->ny; y++)
+      for (int x = 0; x < cfg->nx; x++) {
+        int64_t c = cell_index(cfg, x, y, z);
+        double fl[27], fs[27];
+        if (cell_flag(cfg, x, y, z) != ORA_CELL_FLUID) {
+          for (int i = 0; i < q; i++) fstar[i * N + c] = 0.0;
+          continue;
         }
+        for (int i = 0; i < q; i++) fl[i] = f[i * N + c];
+        ora_collide(cfg, fl, fs, NULL);
+        for (int i = 0; i < q; i++) fstar[i * N + c] = fs[i];
+      }
+  return 0;
+}
+
+int ora_step(const ora_cfg* cfg, double* f, double* work, int64_t nsteps, int nthreads) {
+  if (ora_check(cfg) != 0) return -1;
+  for (int64_t t = 0; t < nsteps; t++) {
+    ora_collide_all(cfg, f, work, nthreads);
     ora_stream(cfg, work, f, nthreads);
   }
   return 0;

@@ -102,6 +102,9 @@ int ora_check(const ora_cfg* cfg);
 /* Eq. LBStreaming alone: f = streamed fstar with the boundary rules (solid cells get w). */
 int ora_stream(const ora_cfg* cfg, const double* fstar, double* f, int nthreads);
 
+/* Eq. LBCollision alone on every fluid cell: fstar = collided f (0 on other cells). */
+int ora_collide_all(const ora_cfg* cfg, const double* f, double* fstar, int nthreads);
+
 /* nsteps full steps in place on f (q*N); work is a q*N scratch array. */
 int ora_step(const ora_cfg* cfg, double* f, double* work, int64_t nsteps, int nthreads);
 
