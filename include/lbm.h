@@ -161,6 +161,38 @@ size_t lbm_halo_bytes(lbm_handle h, int face);
 lbm_status lbm_halo_pack(lbm_handle h, int face, void* buf);
 lbm_status lbm_halo_unpack(lbm_handle h, int face, const void* buf);
 
+/* 2:1 static grid refinement across a z face (Sec. 3 and Fig. 2: blocks of the forest are
+ * refined 2:1, and interpolation kernels carry the populations across a coarse-fine
+ * transition; Sec. 5.2 runs them between the levels).  The paper leaves the transfer
+ * undefined; these calls implement the volumetric, mass-conserving scheme of Rohde, Kandhai,
+ * Derksen and van den Akker (2006), used by waLBerla (Schornbaum and Ruede 2016), in pull form.
+ * A refined z slab is its own fine lattice (2 nx x 2 ny x 2 nz_slab cells, relaxation time
+ * tau_f = 1/2 + 2 (tau_c - 1/2), body force F_c / 2: acoustic scaling) beside coarse lattices
+ * that end at the slab; the faces that meet are LBM_FACE_HALO faces, coarse +z with fine -z or
+ * coarse -z with fine +z.  Both lattices: two-grid pull, same stencil and precision, periodic
+ * x and y faces, stepped at least once since their last import (else LBM_ESTATE); other
+ * mismatches give LBM_EINVAL (LBM_EUNSUPPORTED for non-periodic x or y faces).
+ * One coarse step, from post-collision states C*(t) and F*(t):
+ *   lbm_refine_explode(coarse, cf, fine, ff, 0); lbm_step(fine, 1);
+ *   lbm_refine_coalesce(fine, ff, coarse, cf);
+ *   lbm_refine_explode(coarse, cf, fine, ff, 1); lbm_step(fine, 1); lbm_step(coarse, 1);
+ * (for every interface), which leaves C*(t+1) and F*(t+1).
+ *   lbm_refine_explode: writes the fine ghost plane beyond face ff, for the directions entering
+ *     the fine lattice, from the post-collision populations of the coarse plane next to face
+ *     cf: fine cell (x, y) of the ghost plane gets coarse cell ((x - s c_x)/2, (y - s c_y)/2)
+ *     (floor, periodic), s = substep (0 before the first fine step, 1 before the second).
+ *   lbm_refine_coalesce: writes the coarse ghost plane beyond face cf, for the directions
+ *     entering the coarse lattice, with the mean of the 8 fine populations that reach the
+ *     receiving coarse cell's volume in the two fine steps just taken (post-collision states
+ *     F*(t+1/2) and F*(t) of the fine plane next to face ff; float32 sum).  Needs two fine
+ *     steps since the fine lattice's last import (LBM_ESTATE).
+ * One kernel per call on the destination handle's stream; when the handles use different
+ * streams the call waits for the source's queued work and the source's later work waits for
+ * the kernel.  Pure copies for explode (bit-exact); round-to-nearest-even into the storage
+ * precision for coalesce. */
+lbm_status lbm_refine_explode(lbm_handle coarse, int coarse_face, lbm_handle fine, int fine_face, int substep);
+lbm_status lbm_refine_coalesce(lbm_handle fine, int fine_face, lbm_handle coarse, int coarse_face);
+
 /* Fills p with the defaults listed above. */
 void lbm_params_default(lbm_params* p);
 
@@ -212,6 +244,11 @@ lbm_status lbm_moments(lbm_handle h, float* rho, float* u, int on_device);
 /* Current populations as shifted float32 df_i = f_i - w_i, [q][nz][ny][nx]; 0 on non-fluid
  * cells.  Exact for F32 storage; exact widening for F16/BF16 storage. */
 lbm_status lbm_get_populations(lbm_handle h, float* df, int on_device);
+
+/* The stored post-collision populations f*_i(x, t) of the last step of a two-grid pull
+ * lattice (natural slots, not streamed), as shifted float32 [q][nz][ny][nx]; 0 on non-fluid
+ * cells.  LBM_ESTATE for an AA lattice or before the first step after an import. */
+lbm_status lbm_get_post_collision(lbm_handle h, float* df, int on_device);
 
 /* Replaces the state by the given shifted populations (rounded to the storage precision
  * with round-to-nearest-even).  Clears the instability flag. */

@@ -53,6 +53,7 @@ struct lbm_s {
   // import), 1 AA swapped post-collision (odd number of steps), 2 pull post-collision
   int parity = 0;
   int nat_valid = 1;          // natural layout came from an import (outflow slots hold values)
+  int prev_post = 0;          // pull: the other array holds the post-collision state before the current one
   int nsm = 0;                // multiprocessors of the device (persistent grid size)
   std::string err;
 };
@@ -250,12 +251,12 @@ static cudaError_t dispatch_step(const lbm_s* h, const KParams& p, int closure, 
 }
 
 template <int Q>
-static cudaError_t dispatch_export(const lbm_s* h, const KParams& p, int mode, const ExportArgs& a) {
+static cudaError_t dispatch_export(const lbm_s* h, const KParams& p, int mode, const ExportArgs& a, int parity) {
   const Launch L = launch_cfg(h);
   switch (h->prm.precision) {
-    case LBM_F32: return launch_export<Q, float>(p, h->parity, mode, a, L);
-    case LBM_F16_SHIFTED: return launch_export<Q, __half>(p, h->parity, mode, a, L);
-    default: return launch_export<Q, __nv_bfloat16>(p, h->parity, mode, a, L);
+    case LBM_F32: return launch_export<Q, float>(p, parity, mode, a, L);
+    case LBM_F16_SHIFTED: return launch_export<Q, __half>(p, parity, mode, a, L);
+    default: return launch_export<Q, __nv_bfloat16>(p, parity, mode, a, L);
   }
 }
 
@@ -352,6 +353,56 @@ int lbm_internal_info(lbm_handle h, int* q, int* precision, int* parity, int* cl
 lbm_status lbm_internal_fail(lbm_handle h, lbm_status s, const char* msg) { return fail(h, s, "%s", msg); }
 
 // ---- C ABI ----------------------------------------------------------------------------------
+
+// ---- refinement transfer kernels (2:1 across a z face; see lbm_refine_explode below) ----
+struct RefPlanes {
+  void* dst[9];        // destination plane of each transferred direction
+  const void* src[9];  // source plane (explode: coarse state; coalesce: fine F*(t+1/2))
+  const void* old[9];  // coalesce: fine F*(t)
+  int cx[9], cy[9];
+};
+
+__device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+template <class E>
+__global__ void __launch_bounds__(256) k_refine_explode(RefPlanes rp, int nd, int nxf, int nyf, int nxpf,
+                                                        int nxpc, int s) {
+  const long long plane = (long long)nyf * nxf;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nd * plane;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(t / plane);
+    const int r = (int)(t - k * plane);
+    const int y = r / nxf, x = r - y * nxf;
+    const int xs = wrap1(x - s * rp.cx[k], nxf), ys = wrap1(y - s * rp.cy[k], nyf);
+    static_cast<E*>(rp.dst[k])[(long long)y * nxpf + x] =
+        static_cast<const E*>(rp.src[k])[(long long)(ys >> 1) * nxpc + (xs >> 1)];
+  }
+}
+
+template <class S>
+__global__ void __launch_bounds__(256) k_refine_coalesce(RefPlanes rp, int nd, int nxc, int nyc, int nxpc,
+                                                         int nxpf) {
+  const long long plane = (long long)nyc * nxc;
+  const int nxf = 2 * nxc, nyf = 2 * nyc;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nd * plane;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(t / plane);
+    const int r = (int)(t - k * plane);
+    const int Y = r / nxc, X = r - Y * nxc;
+    const int cx = rp.cx[k], cy = rp.cy[k];
+    const int xv = 2 * wrap1(X + cx, nxc), yv = 2 * wrap1(Y + cy, nyc);  // the receiving cell's volume
+    const S* a = static_cast<const S*>(rp.src[k]);
+    const S* b = static_cast<const S*>(rp.old[k]);
+    float sum = 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const int xf = xv + (j & 1), yf = yv + (j >> 1);
+      sum += ld<S>(a + (long long)wrap1(yf - cy, nyf) * nxpf + wrap1(xf - cx, nxf));
+      sum += ld<S>(b + (long long)wrap1(yf - 2 * cy, nyf) * nxpf + wrap1(xf - 2 * cx, nxf));
+    }
+    st<S>(static_cast<S*>(rp.dst[k]) + (long long)Y * nxpc + X, sum * 0.125f);
+  }
+}
 
 extern "C" {
 
@@ -610,6 +661,7 @@ lbm_status lbm_init_equilibrium(lbm_handle h, const float* rho, const float* u, 
   if (tu) cudaFreeAsync(tu, h->stream);
   CUDA_TRY(h, e);
   h->parity = 0;
+  h->prev_post = 0;
   h->nat_valid = 1;
   return reset_status(h);
 }
@@ -626,11 +678,13 @@ lbm_status lbm_set_populations(lbm_handle h, const float* df, int on_device) {
   if (t) cudaFreeAsync(t, h->stream);
   CUDA_TRY(h, e);
   h->parity = 0;
+  h->prev_post = 0;
   h->nat_valid = 1;
   return reset_status(h);
 }
 
-static lbm_status run_export(lbm_handle h, int mode, const ExportArgs& a);
+static lbm_status run_export(lbm_handle h, int mode, const ExportArgs& a, bool raw = false);
+static void advance_state(lbm_handle h);
 
 // n steps; with every > 0 the plane statistics of the state each step k (k % every == 0)
 // starts from are added to the accumulated sums, inside that step's kernel where it can.
@@ -664,14 +718,8 @@ static lbm_status run_steps(lbm_handle h, int64_t n, int64_t every) {
       CUDA_TRY(h, cudaGetLastError());
     }
     if (sample) h->nsamples++;
-    if (h->prm.streaming == LBM_PULL) {  // the destination array holds the new state
-      h->cur ^= 1;
-      h->parity = 2;
-      p = kparams(h);
-    } else {
-      if (h->parity == 1) h->nat_valid = 0;  // an odd step leaves the outflow slots unwritten
-      h->parity ^= 1;
-    }
+    advance_state(h);  // pull: the destination array holds the new state
+    if (h->prm.streaming == LBM_PULL) p = kparams(h);
   }
   return LBM_OK;
 }
@@ -687,10 +735,11 @@ constexpr int GRAPH_STEPS = 8;
 
 static void advance_state(lbm_handle h) {
   if (h->prm.streaming == LBM_PULL) {
+    h->prev_post = h->parity == 2;  // the array just read keeps the state it held
     h->cur ^= 1;
     h->parity = 2;
   } else {
-    if (h->parity == 1) h->nat_valid = 0;
+    if (h->parity == 1) h->nat_valid = 0;  // an odd step leaves the outflow slots unwritten
     h->parity ^= 1;
   }
 }
@@ -712,7 +761,7 @@ static bool graph_ready(lbm_handle h) {
     h->graphs_off = true;
     return false;
   }
-  const int saved[3] = {h->parity, h->cur, h->nat_valid};
+  const int saved[4] = {h->parity, h->cur, h->nat_valid, h->prev_post};
   cudaStream_t user = h->stream;
   h->stream = h->cap;
   cudaGraph_t graph = nullptr;
@@ -729,6 +778,7 @@ static bool graph_ready(lbm_handle h) {
   h->parity = saved[0];
   h->cur = saved[1];
   h->nat_valid = saved[2];
+  h->prev_post = saved[3];
   ok = ok && ended && graph && cudaGraphInstantiate(&h->gexec, graph, 0) == cudaSuccess;
   if (graph) cudaGraphDestroy(graph);
   cudaGetLastError();  // a failed capture leaves no sticky error; fall back to launches
@@ -845,6 +895,122 @@ lbm_status lbm_halo_unpack(lbm_handle h, int face, const void* buf) {
   return halo_copy(h, face, const_cast<void*>(buf), false);
 }
 
+// ---- 2:1 grid refinement across a z face ---------------------------------------------------
+// Volumetric transfer of Rohde et al. (2006) in pull form.  A fine cell (x, y) of the slab's
+// boundary plane pulls a population entering through the face from the ghost plane at
+// (x - c_x, y - c_y); in the scheme's push form the fine ghost region is two fine planes deep,
+// filled from the coarse interface cell whose volume each ghost cell lies in and streamed (not
+// collided) with the fine cells, so the ghost value seen in fine substep s (0, 1) is the coarse
+// population of the cell over (x - s c_x, y - s c_y).  Leaving the slab, the 8 fine values that
+// end in a coarse cell's volume after both substeps are F*(t+1/2) of (x - c_x, y - c_y) and
+// F*(t) of (x - 2 c_x, y - 2 c_y) for the 2x2 fine cells (x, y) above the coarse cell; their mean
+// is what the coarse cell receives, i.e. what its pull reads from the coarse ghost cell one
+// coarse step back along c_i.
+// The pair (coarse face, fine face) of one interface: the coarse lattice's +z face meets the
+// fine lattice's -z face or the other way round; both halo faces of two-grid pull lattices of
+// the same stencil and precision, periodic in x and y, the fine one twice as wide and deep.
+// Errors are recorded on the destination handle e (fine for explode, coarse for coalesce).
+static lbm_status refine_check(lbm_handle coarse, int cface, lbm_handle fine, int fface, lbm_handle e) {
+  if (!coarse || !fine) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (coarse == fine) return fail(e, LBM_EINVAL, "coarse and fine must be different lattices");
+  if ((cface != 4 && cface != 5) || fface != 9 - cface)
+    return fail(e, LBM_EINVAL, "faces must be (coarse 5, fine 4) or (coarse 4, fine 5)");
+  if (coarse->prm.face_bc[cface] != LBM_FACE_HALO || fine->prm.face_bc[fface] != LBM_FACE_HALO)
+    return fail(e, LBM_EINVAL, "both faces must be halo faces");
+  if (coarse->q != fine->q || coarse->prm.precision != fine->prm.precision)
+    return fail(e, LBM_EINVAL, "coarse and fine lattices need the same stencil and precision");
+  if (fine->nx != 2 * coarse->nx || fine->ny != 2 * coarse->ny)
+    return fail(e, LBM_EINVAL, "the fine lattice must be 2 nx x 2 ny of the coarse one");
+  for (int f = 0; f < 4; f++)
+    if (coarse->prm.face_bc[f] != LBM_FACE_PERIODIC || fine->prm.face_bc[f] != LBM_FACE_PERIODIC)
+      return fail(e, LBM_EUNSUPPORTED, "refinement interfaces need periodic x and y faces");
+  if (coarse->parity != 2 || fine->parity != 2)
+    return fail(e, LBM_ESTATE, "both lattices must have stepped since their last import");
+  return LBM_OK;
+}
+
+// Orders the transfer after the source handle's work and the destination handle's later
+// work after the transfer when the two handles use different streams.
+static lbm_status stream_join(lbm_handle from, lbm_handle to, lbm_handle err) {
+  if (from->stream == to->stream) return LBM_OK;
+  cudaEvent_t ev;
+  CUDA_TRY(err, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaError_t e = cudaEventRecord(ev, from->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(to->stream, ev, 0);
+  cudaEventDestroy(ev);
+  CUDA_TRY(err, e);
+  return LBM_OK;
+}
+
+static int refine_planes(lbm_handle dst_h, long long dst_z, lbm_handle src_h, long long src_z, int sign,
+                         RefPlanes& rp) {
+  int dirs[27], c[81];
+  const int nd = halo_dirs(src_h, sign, dirs);
+  lbm_stencil(src_h->q, c, nullptr);
+  const KParams pd = kparams(dst_h), ps = kparams(src_h);
+  const size_t sb = store_bytes(src_h->prm.precision);
+  const size_t pbd = (size_t)dst_h->nxp * dst_h->ny * sb, pbs = (size_t)src_h->nxp * src_h->ny * sb;
+  for (int k = 0; k < nd; k++) {
+    const int i = dirs[k];
+    rp.dst[k] = (char*)pd.fp[i] + dst_z * (long long)pbd;
+    rp.src[k] = (const char*)ps.fp[i] + src_z * (long long)pbs;
+    rp.old[k] = ps.fq[i] ? (const char*)ps.fq[i] + src_z * (long long)pbs : nullptr;
+    rp.cx[k] = c[3 * i];
+    rp.cy[k] = c[3 * i + 1];
+  }
+  return nd;
+}
+
+lbm_status lbm_refine_explode(lbm_handle coarse, int coarse_face, lbm_handle fine, int fine_face, int substep) {
+  lbm_status st = refine_check(coarse, coarse_face, fine, fine_face, fine);
+  if (st != LBM_OK) return st;
+  if (substep != 0 && substep != 1) return fail(fine, LBM_EINVAL, "substep must be 0 or 1");
+  // populations leaving the coarse lattice through its face = entering the fine one through its face
+  RefPlanes rp{};
+  const int sign = coarse_face == 5 ? 1 : -1;
+  const int nd = refine_planes(fine, fine_face == 4 ? -1 : fine->nz, coarse, coarse_face == 5 ? coarse->nz - 1 : 0,
+                               sign, rp);
+  st = stream_join(coarse, fine, fine);
+  if (st != LBM_OK) return st;
+  const long long n = (long long)nd * fine->nx * fine->ny;
+  const int blocks = (int)std::min<long long>((n + 255) / 256, (long long)fine->nsm * 8);
+  if (fine->prm.precision == LBM_F32)
+    k_refine_explode<uint32_t><<<blocks, 256, 0, fine->stream>>>(rp, nd, fine->nx, fine->ny, fine->nxp, coarse->nxp, substep);
+  else
+    k_refine_explode<uint16_t><<<blocks, 256, 0, fine->stream>>>(rp, nd, fine->nx, fine->ny, fine->nxp, coarse->nxp, substep);
+  CUDA_TRY(fine, cudaGetLastError());
+  return stream_join(fine, coarse, fine);
+}
+
+lbm_status lbm_refine_coalesce(lbm_handle fine, int fine_face, lbm_handle coarse, int coarse_face) {
+  lbm_status st = refine_check(coarse, coarse_face, fine, fine_face, coarse);
+  if (st != LBM_OK) return st;
+  if (!fine->prev_post)
+    return fail(coarse, LBM_ESTATE, "the fine lattice needs two steps since its last import");
+  RefPlanes rp{};
+  const int sign = fine_face == 5 ? 1 : -1;  // leaving the fine lattice through its face
+  const int nd = refine_planes(coarse, coarse_face == 4 ? -1 : coarse->nz, fine, fine_face == 5 ? fine->nz - 1 : 0,
+                               sign, rp);
+  st = stream_join(fine, coarse, coarse);
+  if (st != LBM_OK) return st;
+  const long long n = (long long)nd * coarse->nx * coarse->ny;
+  const int blocks = (int)std::min<long long>((n + 255) / 256, (long long)coarse->nsm * 8);
+  switch (coarse->prm.precision) {
+    case LBM_F32:
+      k_refine_coalesce<float><<<blocks, 256, 0, coarse->stream>>>(rp, nd, coarse->nx, coarse->ny, coarse->nxp, fine->nxp);
+      break;
+    case LBM_F16_SHIFTED:
+      k_refine_coalesce<__half><<<blocks, 256, 0, coarse->stream>>>(rp, nd, coarse->nx, coarse->ny, coarse->nxp, fine->nxp);
+      break;
+    default:
+      k_refine_coalesce<__nv_bfloat16><<<blocks, 256, 0, coarse->stream>>>(rp, nd, coarse->nx, coarse->ny, coarse->nxp,
+                                                                          fine->nxp);
+      break;
+  }
+  CUDA_TRY(coarse, cudaGetLastError());
+  return stream_join(coarse, fine, coarse);
+}
+
 lbm_status lbm_sync(lbm_handle h) {
   if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
   CUDA_TRY(h, cudaMemcpyAsync(h->status_host, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -864,9 +1030,12 @@ lbm_status lbm_sync(lbm_handle h) {
   return LBM_OK;
 }
 
-static lbm_status run_export(lbm_handle h, int mode, const ExportArgs& a) {
+// raw: the values stored in the state array's own slots (layout 0), whatever the state
+static lbm_status run_export(lbm_handle h, int mode, const ExportArgs& a, bool raw) {
   KParams p = kparams(h);
-  cudaError_t e = h->q == 19 ? dispatch_export<19>(h, p, mode, a) : dispatch_export<27>(h, p, mode, a);
+  if (raw) p.nat_valid = 1;
+  const int par = raw ? 0 : h->parity;
+  cudaError_t e = h->q == 19 ? dispatch_export<19>(h, p, mode, a, par) : dispatch_export<27>(h, p, mode, a, par);
   CUDA_TRY(h, e);
   return LBM_OK;
 }
@@ -898,7 +1067,19 @@ lbm_status lbm_moments(lbm_handle h, float* rho, float* u, int on_device) {
   return LBM_OK;
 }
 
+static lbm_status get_pop(lbm_handle h, float* df, int on_device, bool raw);
+
 lbm_status lbm_get_populations(lbm_handle h, float* df, int on_device) {
+  return get_pop(h, df, on_device, false);
+}
+
+lbm_status lbm_get_post_collision(lbm_handle h, float* df, int on_device) {
+  if (h && (h->prm.streaming != LBM_PULL || h->parity != 2))
+    return fail(h, LBM_ESTATE, "no post-collision state: a two-grid pull lattice that has stepped is needed");
+  return get_pop(h, df, on_device, true);
+}
+
+static lbm_status get_pop(lbm_handle h, float* df, int on_device, bool raw) {
   if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
   if (!df) return fail(h, LBM_EINVAL, "df is NULL");
   const size_t count = (size_t)ncell(h) * h->q;
@@ -910,7 +1091,7 @@ lbm_status lbm_get_populations(lbm_handle h, float* df, int on_device) {
     CUDA_TRY(h, cudaMallocAsync((void**)&t, count * sizeof(float), h->stream));
     a.df = t;
   }
-  lbm_status s = run_export(h, EX_POP, a);
+  lbm_status s = run_export(h, EX_POP, a, raw);
   if (s != LBM_OK) return s;
   if (!on_device) {
     CUDA_TRY(h, cudaMemcpyAsync(df, t, count * sizeof(float), cudaMemcpyDeviceToHost, h->stream));

@@ -101,6 +101,9 @@ def load():
             "lbm_halo_bytes": (ctypes.c_size_t, [H, I]),
             "lbm_halo_pack": (I, [H, I, P]),
             "lbm_halo_unpack": (I, [H, I, P]),
+            "lbm_refine_explode": (I, [H, I, H, I, I]),
+            "lbm_refine_coalesce": (I, [H, I, H, I]),
+            "lbm_get_post_collision": (I, [H, P, I]),
             "lbm_reduce_noalloc": (I, [P, P, I, I, I, I, P, P, P]),
             "lbm_set_closure_f32": (I, [H, P, I, D, D]),
             "lbm_set_closure_floor": (I, [H, D]),
@@ -246,6 +249,19 @@ def lbm_moments(h, rho=None, u=None):
 def lbm_get_populations(h, df):
     p, dev = _buf(df, np.float32, True)
     _check(load().lbm_get_populations(h, p, dev), h)
+
+
+def lbm_get_post_collision(h, df):
+    p, dev = _buf(df, np.float32, True)
+    _check(load().lbm_get_post_collision(h, p, dev), h)
+
+
+def lbm_refine_explode(coarse, coarse_face: int, fine, fine_face: int, substep: int):
+    _check(load().lbm_refine_explode(coarse, int(coarse_face), fine, int(fine_face), int(substep)), fine)
+
+
+def lbm_refine_coalesce(fine, fine_face: int, coarse, coarse_face: int):
+    _check(load().lbm_refine_coalesce(fine, int(fine_face), coarse, int(coarse_face)), coarse)
 
 
 def lbm_set_populations(h, df):
@@ -449,6 +465,11 @@ class Lattice:
     def get_populations(self):
         df = np.zeros((self.q, self.nz, self.ny, self.nx), dtype=np.float32)
         lbm_get_populations(self.h, df)
+        return df
+
+    def get_post_collision(self):
+        df = np.zeros((self.q, self.nz, self.ny, self.nx), dtype=np.float32)
+        lbm_get_post_collision(self.h, df)
         return df
 
     def set_populations(self, df):
