@@ -355,6 +355,42 @@ def _slab_form(nslab, nsteps, warmup, peak, peak_kind):
                          "bytes_per_update": 153.0, "ms_per_step": round(ms, 4)}}
 
 
+def _refined_form(nsteps, warmup, peak, peak_kind, precision="f32"):
+    """A 256x128x128 coarse box (periodic, body force along x, TRT + Smagorinsky) whose planes
+    z = 32..95 are refined 2:1 into a 512x256x128 fine lattice: per coarse step every coarse
+    cell is updated once and every fine cell twice, plus the explosion and coalescence of the
+    two interfaces.  Throughput counts cell updates of both levels."""
+    import torch
+
+    from paper_2305_09910_gb300 import inputs, refine
+
+    par = inputs.channel_parameters(128)
+    rs = refine.RefinedSlab(256, 128, 128, 32, 96, stencil=19, tau=par["tau"], force=(par["force"], 0.0, 0.0),
+                            closure="smag", cs_smag=0.1, precision=precision)
+    rs.init_equilibrium()
+    rs.step(warmup)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    rs.step(nsteps)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    rs.sync()
+    ms = t0.elapsed_time(t1) / nsteps
+    upd = rs.updates_per_step
+    bpu = float(rs.fine.bytes_per_update)
+    launches = 3 * len(rs.interfaces) + 2 + len(rs.coarse)  # explode x2, coalesce per interface; steps
+    rs.close()
+    achieved = upd * bpu / (ms * 1e-3) / 1e9
+    return {"MLUPS": round(upd / (ms * 1e-3) / 1e6, 1), "updates_per_coarse_step": upd,
+            "launches_per_coarse_step": launches,
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": None,
+                         "bytes_per_update": bpu, "ms_per_coarse_step": round(ms, 4)}}
+
+
 def _cpu_baseline(target_s=12.0):
     """The FP64 oracle on this host's cores, on a 128x64x64 sub-lattice of the channel."""
     import numpy as np
@@ -527,6 +563,9 @@ def main():
             torch.cuda.empty_cache()
         forms.update(_extra_forms(nsteps, args.warmup, peak, peak_kind))
         forms["channel512_f32_2slabs_halo"] = _slab_form(2, nsteps, args.warmup, peak, peak_kind)
+        for prec in ("f32", "f16"):
+            forms[f"box256_refined2to1_{prec}"] = _refined_form(nsteps // 2, args.warmup, peak, peak_kind, prec)
+            torch.cuda.empty_cache()
         fl, _ = _channel_lattice(nx, ny, nz, "f32", collision="mrt")
         forms[f"channel{nx}_f32_mrt"] = _form_line(fl, nsteps, args.warmup, peak, peak_kind)
         fl.close()
