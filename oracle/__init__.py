@@ -202,7 +202,7 @@ class Oracle:
         c.mlp = None if self._mlp is None else self._mlp.ctypes.data
         c.mlp_scale[0], c.mlp_scale[1] = float(mlp_scale[0]), float(mlp_scale[1])
         c.mlp_cs_min = float(mlp_cs_min)
-        c.collision = {"trt": 0, "mrt": 1}[collision]
+        c.collision = {"trt": 0, "mrt": 1, "reg": 2}[collision]
         for k in range(5):
             c.mrt_s[k] = float(mrt_s[k])
         self.cfg = c

@@ -318,6 +318,25 @@ void ora_collide(const ora_cfg* cfg, const double* f, double* fstar, double* tau
     mrt_collide(cfg, f, feq, fi, tau, fstar);
     return;
   }
+  if (cfg->collision == ORA_COLL_REG) {
+    /* BGK with Guo forcing reads f* = f^eq + (1 - w) g + F_i/2 with g = f - f^eq + F_i/2;
+     * the regularised operator keeps only the projection of g on the Hermite polynomials
+     * H_i = c_i c_i - I/3: g_i -> (9/2) w_i H_i : P, P = sum_j c_j c_j g_j (sum_j g_j = 0) */
+    double P[3][3] = {{0.0}};
+    for (int i = 0; i < q; i++) {
+      double g = f[i] - feq[i] + 0.5 * fi[i];
+      for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) P[a][b] += C27[i][a] * C27[i][b] * g;
+    }
+    double tr = P[0][0] + P[1][1] + P[2][2];
+    for (int i = 0; i < q; i++) {
+      double h = -tr / 3.0;
+      for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) h += C27[i][a] * C27[i][b] * P[a][b];
+      fstar[i] = feq[i] + 0.5 * fi[i] + (1.0 - wp) * 4.5 * W_(q, i) * h;
+    }
+    return;
+  }
   for (int i = 0; i < q; i++) {
     int j = OPP[i];
     double fp = 0.5 * (f[i] + f[j]), fm = 0.5 * (f[i] - f[j]);
@@ -407,7 +426,8 @@ int ora_check(const ora_cfg* cfg) {
   }
   if (cfg->face[1] == ORA_FACE_OUTFLOW && cfg->nx < 2) return -7;
   if (cfg->closure == ORA_CLOSURE_MLP && !cfg->mlp) return -8;
-  if (cfg->collision != ORA_COLL_TRT && cfg->collision != ORA_COLL_MRT) return -9;
+  if (cfg->collision != ORA_COLL_TRT && cfg->collision != ORA_COLL_MRT && cfg->collision != ORA_COLL_REG)
+    return -9;
   if (cfg->collision == ORA_COLL_MRT) {
     if (cfg->q != 19) return -10;
     for (int k = 0; k < 5; k++)

@@ -41,7 +41,10 @@ enum { ORA_CLOSURE_NONE = 0, ORA_CLOSURE_SMAG = 1, ORA_CLOSURE_MLP = 2 };
 /* collision operator: TRT, or D3Q19 multiple-relaxation-time (MRT) in the orthogonal moment
  * basis of d'Humieres, Ginzburg, Krafczyk, Lallemand & Luo (2002), the operator the paper's
  * LAGOON runs use (Sec. 5.2) */
-enum { ORA_COLL_TRT = 0, ORA_COLL_MRT = 1 };
+/* or projected regularisation (Latt & Chopard 2006): the non-equilibrium part, with the half
+ * force of the forcing scheme, is replaced by its projection on the second-order Hermite
+ * polynomials before it relaxes with 1/tau_eff (D3Q19 and D3Q27) */
+enum { ORA_COLL_TRT = 0, ORA_COLL_MRT = 1, ORA_COLL_REG = 2 };
 
 /* MLP closure: 7 -> 32 -> 32 -> 1, parameters packed as
  * W1[32][7], b1[32], W2[32][32], b2[32], W3[32], b3[1]. */
