@@ -566,9 +566,11 @@ def main():
         for prec in ("f32", "f16"):
             forms[f"box256_refined2to1_{prec}"] = _refined_form(nsteps // 2, args.warmup, peak, peak_kind, prec)
             torch.cuda.empty_cache()
-        fl, _ = _channel_lattice(nx, ny, nz, "f32", collision="mrt")
-        forms[f"channel{nx}_f32_mrt"] = _form_line(fl, nsteps, args.warmup, peak, peak_kind)
-        fl.close()
+        for coll in ("mrt", "reg"):
+            fl, _ = _channel_lattice(nx, ny, nz, "f32", collision=coll)
+            forms[f"channel{nx}_f32_{coll}"] = _form_line(fl, nsteps, args.warmup, peak, peak_kind)
+            fl.close()
+            torch.cuda.empty_cache()
 
     if (nx, ny, nz, args.form, args.streaming, args.closure, channel) == (512, 256, 256, "f32", "pull", "smag", True):
         workload = WORKLOAD

@@ -121,7 +121,8 @@ typedef struct {
   double rho_inflow;    /* density used by moving-wall bounce-back, default 1 */
   void* stream;         /* cudaStream_t for all work, default NULL */
   int32_t pipeline;     /* load pipeline of the AA step kernels (LBM_PIPE_*), default DIRECT */
-  int32_t collision;    /* LBM_COLL_TRT (default) | LBM_COLL_MRT (D3Q19, no learned closure) */
+  int32_t collision;    /* LBM_COLL_TRT (default) | LBM_COLL_MRT (D3Q19) | LBM_COLL_REG;
+                         * MRT and REG without the learned closure */
   double mrt_rates[5];  /* MRT rates of the moment groups e, eps, q, pi, m; default
                          * 1.19, 1.4, 1.2, 1.4, 1.98; the stress moments relax with 1/tau_eff */
 } lbm_params;
@@ -130,9 +131,13 @@ typedef struct {
  * relaxation-time operator of d'Humieres, Ginzburg, Krafczyk, Lallemand & Luo (2002) in its
  * orthogonal moment basis (rho, e, eps, j, q, 3p_xx, 3pi_xx, p_ww, pi_ww, p_xy, p_yz, p_xz, m),
  * relaxing the moments of f - f^eq (the same second-order equilibrium) with Guo's force in
- * moment space; the collision of the paper's LAGOON runs (Sec. 5.2).  Every pipeline runs the
- * MRT step as the direct one-cell kernel. */
-enum { LBM_COLL_TRT = 0, LBM_COLL_MRT = 1 };
+ * moment space; the collision of the paper's LAGOON runs (Sec. 5.2).  REG: projected
+ * regularisation (Latt & Chopard 2006), the non-hybrid member of the family of LaBS's
+ * D3Q19HRR scheme (Sec. 4 and 5.1 name it without a definition; its finite-difference
+ * blend is not built): with g = f - f^eq + F_i/2,
+ * f*_i = f^eq_i + F_i/2 + (1 - 1/tau_eff) (9/2) w_i H_i : sum_j H_j g_j, H_i = c_i c_i - I/3
+ * (D3Q19 and D3Q27).  Every pipeline runs the MRT and REG steps as the direct one-cell kernel. */
+enum { LBM_COLL_TRT = 0, LBM_COLL_MRT = 1, LBM_COLL_REG = 2 };
 
 /* load pipeline of the step kernels:
  * DIRECT (default) = every thread loads its cell from global memory;

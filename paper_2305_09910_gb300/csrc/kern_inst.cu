@@ -15,7 +15,8 @@
 namespace lbm {
 
 // stats: also write the warp-slot plane statistics of the starting state (p.stats_w); *nws
-// receives the number of warp slots per row.  coll: 0 TRT, 1 MRT (D3Q19, one cell per thread).
+// receives the number of warp slots per row.  coll: 0 TRT, 1 MRT (D3Q19, one cell per thread),
+// 2 regularised (one cell per thread).
 template <int Q, class S, int LOAD, int STORE, bool STATS>
 static void step_mode_s(const KParams& p, int closure, const Launch& L, int coll, int* nws) {
   if constexpr (Q == 19) {
@@ -25,6 +26,12 @@ static void step_mode_s(const KParams& p, int closure, const Launch& L, int coll
       else k_step<Q, S, CL_SMAG, LOAD, STORE, STATS, 1><<<L.grid, L.block, 0, L.stream>>>(p);
       return;
     }
+  }
+  if (coll == 2) {  // regularised collision: one cell per thread, every stencil and storage
+    if (nws) *nws = p.nxp / 32;
+    if (closure == CL_NONE) k_step<Q, S, CL_NONE, LOAD, STORE, STATS, 2><<<L.grid, L.block, 0, L.stream>>>(p);
+    else k_step<Q, S, CL_SMAG, LOAD, STORE, STATS, 2><<<L.grid, L.block, 0, L.stream>>>(p);
+    return;
   }
   // half storage, D3Q19: x-pairs, 64 x per warp (for D3Q27 the pair kernel needs more
   // registers than it saves, and on the bluff body the warps at the inflow and outflow faces

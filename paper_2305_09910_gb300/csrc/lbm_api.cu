@@ -176,7 +176,7 @@ static KParams kparams(const lbm_s* h) {
 // True when the step kernel of this handle can sample the statistics itself (direct loads,
 // no learned closure); the other forms sample them in a separate pass before the step.
 static bool fused_stats(const lbm_s* h) {
-  return (h->prm.pipeline == LBM_PIPE_DIRECT || h->prm.collision == LBM_COLL_MRT) &&
+  return (h->prm.pipeline == LBM_PIPE_DIRECT || h->prm.collision != LBM_COLL_TRT) &&
          h->prm.closure != LBM_CLOSURE_MLP;
 }
 
@@ -184,12 +184,13 @@ template <int Q>
 static cudaError_t dispatch_step(const lbm_s* h, const KParams& p, int closure, int parity, bool stats = false,
                                  int* nws = nullptr) {
   const Launch L = launch_cfg(h);
-  if (h->prm.collision == LBM_COLL_MRT) {  // one kernel for every pipeline: the direct MRT step
+  if (h->prm.collision != LBM_COLL_TRT) {  // one kernel for every pipeline: the direct MRT / regularised step
     const int mode = h->prm.streaming == LBM_PULL ? (parity == 0 ? 2 : 3) : parity;
+    const int coll = h->prm.collision;
     switch (h->prm.precision) {
-      case LBM_F32: return launch_step<Q, float>(p, closure, mode, L, stats, nws, 1);
-      case LBM_F16_SHIFTED: return launch_step<Q, __half>(p, closure, mode, L, stats, nws, 1);
-      default: return launch_step<Q, __nv_bfloat16>(p, closure, mode, L, stats, nws, 1);
+      case LBM_F32: return launch_step<Q, float>(p, closure, mode, L, stats, nws, coll);
+      case LBM_F16_SHIFTED: return launch_step<Q, __half>(p, closure, mode, L, stats, nws, coll);
+      default: return launch_step<Q, __nv_bfloat16>(p, closure, mode, L, stats, nws, coll);
     }
   }
   if (closure == CL_MLP) {  // one kernel for every pipeline: the tensor-core closure step
@@ -499,8 +500,10 @@ lbm_status lbm_create(int nx, int ny, int nz, int stencil, double tau, const lbm
   if (p.pipeline < LBM_PIPE_TMA || p.pipeline > LBM_PIPE_ASYNC)
     return fail(nullptr, LBM_EINVAL, "unknown pipeline %d", p.pipeline);
   if (!(p.cs_smag >= 0.0)) return fail(nullptr, LBM_EINVAL, "cs_smag must be >= 0");
-  if (p.collision != LBM_COLL_TRT && p.collision != LBM_COLL_MRT)
+  if (p.collision != LBM_COLL_TRT && p.collision != LBM_COLL_MRT && p.collision != LBM_COLL_REG)
     return fail(nullptr, LBM_EINVAL, "unknown collision %d", p.collision);
+  if (p.collision == LBM_COLL_REG && p.closure == LBM_CLOSURE_MLP)
+    return fail(nullptr, LBM_EUNSUPPORTED, "the learned closure runs with the TRT collision");
   if (p.collision == LBM_COLL_MRT) {
     if (stencil != 19) return fail(nullptr, LBM_EUNSUPPORTED, "the MRT collision is defined for D3Q19");
     if (p.closure == LBM_CLOSURE_MLP)

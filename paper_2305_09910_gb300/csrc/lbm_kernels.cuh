@@ -853,6 +853,73 @@ __device__ __forceinline__ void mrt_pairs_back(float (&f)[19], const float (&dm)
   (mrt_pair_back<P>(f, dm), ...);
 }
 
+// ---- regularised collision (projected regularisation, Latt & Chopard 2006) ---------------
+// BGK with Guo forcing reads f* = f^eq + (1 - w) g + F_i/2 with g = f - f^eq + F_i/2; the
+// regularised operator keeps only the part of g on the second-order Hermite polynomials
+// H_i = c_i c_i - I/3:  f*_i = f^eq_i + F_i/2 + (1 - w) (9/2) w_i H_i : P  with
+// P = sum_j H_j g_j = Pi^neq + (u F + F u)/2 (the second moment of Guo's term is u F + F u).
+// Shifted values per pair (i, opp i) with c = c_i: the even part S is common, the odd part A
+// flips sign,
+//   S = w_i [drho - 1.5 j.u - 1.5 u.F + 4.5 (c.j)(c.u) + 4.5 (c.u)(c.F) + (1 - w) 4.5 H_i:P]
+//   A = w_i [3 c.j + 1.5 c.F].
+struct RegCtx {
+  float B0, a, tr3, Pxx, Pyy, Pzz, Pxy, Pxz, Pyz;
+  float ux, uy, uz, jx, jy, jz, Fx, Fy, Fz;
+};
+
+template <int Q, int I>
+__device__ __forceinline__ void reg_pair(float (&f)[Q], const RegCtx& r) {
+  constexpr int P = prim(I), R = P == I ? I + 1 : I;
+  constexpr int X = cx(P), Y = cy(P), Z = cz(P);
+  constexpr float w = (float)wgt_d<Q>(P);
+  const float cu = cdot<X, Y, Z>(r.ux, r.uy, r.uz);
+  const float cj = cdot<X, Y, Z>(r.jx, r.jy, r.jz);
+  const float cF = cdot<X, Y, Z>(r.Fx, r.Fy, r.Fz);
+  float h = -r.tr3;
+  if (X) h = vadd(h, r.Pxx);
+  if (Y) h = vadd(h, r.Pyy);
+  if (Z) h = vadd(h, r.Pzz);
+  if (X && Y) h = vfma((float)(2 * X * Y), r.Pxy, h);
+  if (X && Z) h = vfma((float)(2 * X * Z), r.Pxz, h);
+  if (Y && Z) h = vfma((float)(2 * Y * Z), r.Pyz, h);
+  const float S = vmul(w, vfma(r.a, h, vfma(vmul(4.5f, cu), vadd(cj, cF), r.B0)));
+  const float A = vmul(w, vfma(3.f, cj, vmul(1.5f, cF)));
+  f[P] = vadd(S, A);
+  f[R] = vsub(S, A);
+}
+
+template <int Q, int... K>
+__device__ __forceinline__ void reg_pairs(float (&f)[Q], const RegCtx& r, std::integer_sequence<int, K...>) {
+  (reg_pair<Q, 2 * K + 1>(f, r), ...);
+}
+
+template <int Q>
+__device__ __forceinline__ void relax_reg(const KParams& p, float (&f)[Q], const Macro<float>& M, float w) {
+  RegCtx r;
+  r.Fx = p.F[0];
+  r.Fy = p.F[1];
+  r.Fz = p.F[2];
+  r.ux = M.ux;
+  r.uy = M.uy;
+  r.uz = M.uz;
+  r.jx = M.jx;
+  r.jy = M.jy;
+  r.jz = M.jz;
+  r.Pxx = vfma(M.ux, r.Fx, M.pi[0]);
+  r.Pyy = vfma(M.uy, r.Fy, M.pi[1]);
+  r.Pzz = vfma(M.uz, r.Fz, M.pi[2]);
+  r.Pxy = vfma(0.5f, vfma(M.ux, r.Fy, vmul(M.uy, r.Fx)), M.pi[3]);
+  r.Pxz = vfma(0.5f, vfma(M.ux, r.Fz, vmul(M.uz, r.Fx)), M.pi[4]);
+  r.Pyz = vfma(0.5f, vfma(M.uy, r.Fz, vmul(M.uz, r.Fy)), M.pi[5]);
+  r.tr3 = vmul(vadd(vadd(r.Pxx, r.Pyy), r.Pzz), 1.f / 3.f);
+  r.a = vmul(vsub(1.f, w), 4.5f);
+  const float ju = vfma(M.jz, M.uz, vfma(M.jy, M.uy, vmul(M.jx, M.ux)));
+  const float uF = vfma(M.uz, r.Fz, vfma(M.uy, r.Fy, vmul(M.ux, r.Fx)));
+  r.B0 = vfma(-1.5f, vadd(ju, uF), M.drho);
+  f[0] = vmul((float)wgt_d<Q>(0), vfma(r.a, -r.tr3, r.B0));
+  reg_pairs<Q>(f, r, std::make_integer_sequence<int, (Q - 1) / 2>{});
+}
+
 // With shifted populations df = f - w: m(df) = M f - M w, and the equilibrium and force
 // moments in closed form (the polynomial equilibrium and Guo's force on this lattice):
 //   rho: drho, 0;  e: -11 drho + 19 rho u^2, 38 u.F;  eps: 3 drho - 11/2 rho u^2, -11 u.F;
@@ -932,7 +999,7 @@ template <int Q, int CL, class V, bool ACC = true, int COLL = 0>
 __device__ __forceinline__ V collide(const KParams& p, V (&f)[Q], Macro<V>* mout = nullptr) {
   static_assert(CL != CL_MLP, "the learned closure has its own kernel");
   using L = Lanes<V>;
-  const Macro<V> M = macro<Q, CL != CL_NONE, V>(p, f);
+  const Macro<V> M = macro<Q, CL != CL_NONE || COLL == 2, V>(p, f);
   if (mout) *mout = M;
   V wp = vset<V>(p.omega_p), wm = vset<V>(p.omega_m);
   if (CL != CL_NONE) {
@@ -947,6 +1014,9 @@ __device__ __forceinline__ V collide(const KParams& p, V (&f)[Q], Macro<V>* mout
   if constexpr (COLL == 1) {
     static_assert(Q == 19 && std::is_same<V, float>::value, "MRT: D3Q19, one cell per thread");
     relax_mrt(p, f, M, wp);
+  } else if constexpr (COLL == 2) {
+    static_assert(std::is_same<V, float>::value, "regularised: one cell per thread");
+    relax_reg<Q>(p, f, M, wp);
   } else {
     relax<Q, V, ACC>(p, f, M, wp, wm);
   }

@@ -27,7 +27,7 @@ LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ESTATE, LBM_EUNSUP
 PRECISION = {"f32": 0, "f16": 1, "bf16": 2}
 STREAMING = {"aa": 0, "pull": 1}
 PIPELINE = {"tma": 0, "direct": 1, "prefetch": 2, "async": 3}
-COLLISION = {"trt": 0, "mrt": 1}
+COLLISION = {"trt": 0, "mrt": 1, "reg": 2}
 CLOSURE = {"none": 0, "smag": 1, "mlp": 2}
 FACE = {"periodic": 0, "wall": 1, "freeslip": 2, "inflow": 3, "outflow": 4, "halo": 5}
 CELL = {"fluid": 0, "solid": 1, "inflow": 2}

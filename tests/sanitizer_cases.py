@@ -32,7 +32,7 @@ def run():
         for prec in ("f32", "f16", "bf16"):
             for streaming in ("aa", "pull"):
                 for faces, fl in ((CHANNEL, None), (TUNNEL, flags)):
-                    for coll in (("trt", "mrt") if q == 19 else ("trt",)):
+                    for coll in (("trt", "mrt", "reg") if q == 19 else ("trt", "reg")):
                         lat = lbm.Lattice(nx, ny, nz, stencil=q, tau=0.6, precision=prec, closure="smag",
                                           cs_smag=0.12, faces=faces, u_inflow=(0.04, 0, 0), streaming=streaming,
                                           collision=coll)
