@@ -1098,10 +1098,22 @@ static __global__ void __launch_bounds__(256) k_stats_total(const float* stats_w
   }
 }
 
+// Resident blocks per SM the step is compiled for (registers per thread = 65536 / (128 x
+// this)): more resident warps keep more loads in flight.  D3Q19 TRT and regularised: 10 (48
+// registers; the pull step spills nothing and measured 10 % faster than at 8); D3Q27: 9 (56
+// registers, no spill; pull 5 % faster); MRT: 8, above which it spills.
+#ifndef LBM_STEP_MINB19
+#define LBM_STEP_MINB19 10
+#endif
+#ifndef LBM_STEP_MINB27
+#define LBM_STEP_MINB27 9
+#endif
+
 // STATS: also write the plane statistics of the state this step starts from (warp slot
 // blockIdx.x of each row, nxp/32 slots per row).
 template <int Q, class S, int CL, int LOAD, int STORE, bool STATS = false, int COLL = 0>
-__global__ void __launch_bounds__(128, 8) k_step(const __grid_constant__ KParams p) {
+__global__ void __launch_bounds__(128, Q == 19 ? (COLL == 1 ? 8 : LBM_STEP_MINB19) : LBM_STEP_MINB27)
+    k_step(const __grid_constant__ KParams p) {
   LBM_CELL_COORDS
   float f[Q];
   unsigned outmask;
