@@ -48,7 +48,11 @@
  * scratch), allocated on the handle's stream.  The caller owns every pointer it passes in.
  * All device work is ordered on the handle's stream (lbm_params.stream, a cudaStream_t;
  * NULL = legacy default stream).  Calls that return data to host memory synchronise that
- * stream before returning.  A handle must not be used from two threads at once.
+ * stream before returning.  Host arrays (on_device = 0) in pinned (page-locked) or managed
+ * memory are read or written by the kernels in place; an input array there must stay
+ * unchanged until the stream has passed the call (as for any asynchronous copy from pinned
+ * memory).  Pageable host arrays are staged through device copies.  A handle must not be
+ * used from two threads at once.
  *
  * Errors: every call returns an lbm_status; lbm_last_error() gives a message for the last
  * failing call on a handle.  A status of LBM_EUNSTABLE (a non-finite or non-positive

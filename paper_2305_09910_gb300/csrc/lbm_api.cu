@@ -634,11 +634,27 @@ lbm_status lbm_set_force(lbm_handle h, double fx, double fy, double fz) {
 }
 
 // Stages a host array on the device (or passes a device pointer through).
+// The device address of host memory the GPU can reach directly (pinned or registered host
+// memory, managed memory), else nullptr (pageable memory, which is staged through a copy).
+static void* host_alias(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the query's error state
+    return nullptr;
+  }
+  if (a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeManaged) return a.devicePointer;
+  return nullptr;
+}
+
 static lbm_status stage_in(lbm_handle h, const float* src, size_t count, int on_device, const float** dev,
                            float** tmp) {
   *tmp = nullptr;
   *dev = src;
   if (!src || on_device) return LBM_OK;
+  if (const void* alias = host_alias(src)) {  // pinned: the kernel reads it in place
+    *dev = static_cast<const float*>(alias);
+    return LBM_OK;
+  }
   CUDA_TRY(h, cudaMallocAsync((void**)tmp, count * sizeof(float), h->stream));
   CUDA_TRY(h, cudaMemcpyAsync(*tmp, src, count * sizeof(float), cudaMemcpyHostToDevice, h->stream));
   *dev = *tmp;
@@ -1052,17 +1068,19 @@ lbm_status lbm_moments(lbm_handle h, float* rho, float* u, int on_device) {
   if (on_device) {
     a.rho = rho;
     a.u = u;
-  } else {
-    if (rho) CUDA_TRY(h, cudaMallocAsync((void**)&trho, (size_t)n * sizeof(float), h->stream));
-    if (u) CUDA_TRY(h, cudaMallocAsync((void**)&tu, (size_t)n * 3 * sizeof(float), h->stream));
-    a.rho = trho;
-    a.u = tu;
+  } else {  // pinned host arrays are written in place, pageable ones through a device copy
+    float* arho = rho ? static_cast<float*>(host_alias(rho)) : nullptr;
+    float* au = u ? static_cast<float*>(host_alias(u)) : nullptr;
+    if (rho && !arho) CUDA_TRY(h, cudaMallocAsync((void**)&trho, (size_t)n * sizeof(float), h->stream));
+    if (u && !au) CUDA_TRY(h, cudaMallocAsync((void**)&tu, (size_t)n * 3 * sizeof(float), h->stream));
+    a.rho = arho ? arho : trho;
+    a.u = au ? au : tu;
   }
   lbm_status s = run_export(h, EX_MOM, a);
   if (s != LBM_OK) return s;
   if (!on_device) {
-    if (rho) CUDA_TRY(h, cudaMemcpyAsync(rho, trho, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
-    if (u) CUDA_TRY(h, cudaMemcpyAsync(u, tu, (size_t)n * 3 * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    if (trho) CUDA_TRY(h, cudaMemcpyAsync(rho, trho, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    if (tu) CUDA_TRY(h, cudaMemcpyAsync(u, tu, (size_t)n * 3 * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
     if (trho) cudaFreeAsync(trho, h->stream);
     if (tu) cudaFreeAsync(tu, h->stream);
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
@@ -1090,6 +1108,8 @@ static lbm_status get_pop(lbm_handle h, float* df, int on_device, bool raw) {
   float* t = nullptr;
   if (on_device) {
     a.df = df;
+  } else if (float* alias = static_cast<float*>(host_alias(df))) {  // pinned: written in place
+    a.df = alias;
   } else {
     CUDA_TRY(h, cudaMallocAsync((void**)&t, count * sizeof(float), h->stream));
     a.df = t;
@@ -1097,8 +1117,10 @@ static lbm_status get_pop(lbm_handle h, float* df, int on_device, bool raw) {
   lbm_status s = run_export(h, EX_POP, a, raw);
   if (s != LBM_OK) return s;
   if (!on_device) {
-    CUDA_TRY(h, cudaMemcpyAsync(df, t, count * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
-    cudaFreeAsync(t, h->stream);
+    if (t) {
+      CUDA_TRY(h, cudaMemcpyAsync(df, t, count * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+      cudaFreeAsync(t, h->stream);
+    }
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   }
   return LBM_OK;
