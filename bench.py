@@ -50,7 +50,7 @@ def _peak_hbm():
 
 def _profile_traffic(kernel_tag):
     """Per-launch DRAM bytes from the committed ncu summary of this kernel, if it was taken
-    on the library build that is running now (same source hash); else None."""
+    on step kernels identical to the ones running now (same kernel-source hash); else None."""
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
     if not os.path.exists(path):
         return None
@@ -60,10 +60,10 @@ def _profile_traffic(kernel_tag):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
     try:
-        stamp = open(os.path.join(ROOT, "paper_2305_09910_gb300", "liblbm.so.sha256")).read().strip()
+        stamp = open(os.path.join(ROOT, "paper_2305_09910_gb300", "liblbm.so.kernel.sha256")).read().strip()
     except OSError:
         return None
-    if vals.get("library_sha256") != stamp:
+    if vals.get("kernel_sha256") != stamp:
         return None
     try:
         return float(vals["dram_bytes_per_launch"])

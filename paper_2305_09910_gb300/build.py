@@ -52,6 +52,23 @@ def _digest(extra) -> str:
     return h.hexdigest()
 
 
+def _kernel_sources():
+    """The sources of the step-kernel translation units (kern_inst.cu and the headers it includes)."""
+    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")) + \
+        [os.path.join(CSRC, "kern_inst.cu")]
+
+
+def kernel_digest(extra=()) -> str:
+    """Hash of the step kernels' sources and flags: ncu summaries taken on one build stay valid
+    for another with the same kernels (host-side API changes do not touch them)."""
+    h = hashlib.sha256()
+    for path in _kernel_sources():
+        with open(path, "rb") as fh:
+            h.update(os.path.relpath(path, ROOT).encode() + b"\0" + fh.read())
+    h.update(" ".join(ARCH + NVFLAGS + list(extra)).replace(ROOT, ".").encode())
+    return h.hexdigest()
+
+
 def build(force: bool = False, verbose: bool = False, extra_flags=(), variant=None) -> str:
     """Compiles (if needed) and returns the path of liblbm.so (or of a variant's library)."""
     name, bdir, vflags = VARIANTS[variant]
@@ -63,6 +80,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=(), variant=No
     if not force and os.path.exists(lib_path) and os.path.exists(stamp):
         with open(stamp) as fh:
             if fh.read().strip() == digest:
+                with open(lib_path + ".kernel.sha256", "w") as kfh:
+                    kfh.write(kernel_digest(extra) + "\n")
                 return lib_path
     nvcc = _nvcc()
     os.makedirs(build_dir, exist_ok=True)
@@ -96,6 +115,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=(), variant=No
     os.replace(tmp, lib_path)
     with open(stamp, "w") as fh:
         fh.write(digest + "\n")
+    with open(lib_path + ".kernel.sha256", "w") as fh:
+        fh.write(kernel_digest(extra) + "\n")
     return lib_path
 
 
