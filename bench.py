@@ -355,6 +355,34 @@ def _slab_form(nslab, nsteps, warmup, peak, peak_kind):
                          "bytes_per_update": 153.0, "ms_per_step": round(ms, 4)}}
 
 
+def _small_form(streaming, nsteps=2000):
+    """The 64x32x32 Poiseuille lattice (walls as solid rows, body force), launch-bound: time
+    per step of lbm_step(n), which runs several steps per launch (multi-step cooperative
+    launches or graph replays)."""
+    import torch
+
+    from paper_2305_09910_gb300 import inputs, lbm
+
+    nx, ny, nz = 64, 32, 32
+    lat = lbm.Lattice(nx, ny, nz, stencil=19, tau=0.8, streaming=streaming)
+    lat.set_flags(inputs.poiseuille_flags(nx, ny, nz))
+    lat.set_force(1e-6)
+    lat.init_equilibrium()
+    lat.step(20)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    lat.step(nsteps)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    lat.sync()
+    us = t0.elapsed_time(t1) * 1e3 / nsteps
+    lat.close()
+    return {"MLUPS": round(nx * ny * nz / us, 1), "us_per_step": round(us, 2), "steps": nsteps}
+
+
 def _refined_form(nsteps, warmup, peak, peak_kind, precision="f32"):
     """A 256x128x128 coarse box (periodic, body force along x, TRT + Smagorinsky) whose planes
     z = 32..95 are refined 2:1 into a 512x256x128 fine lattice: per coarse step every coarse
@@ -563,6 +591,8 @@ def main():
             torch.cuda.empty_cache()
         forms.update(_extra_forms(nsteps, args.warmup, peak, peak_kind))
         forms["channel512_f32_2slabs_halo"] = _slab_form(2, nsteps, args.warmup, peak, peak_kind)
+        for streaming in ("pull", "aa"):
+            forms[f"poiseuille64_f32_{streaming}"] = _small_form(streaming)
         for prec in ("f32", "f16"):
             forms[f"box256_refined2to1_{prec}"] = _refined_form(nsteps // 2, args.warmup, peak, peak_kind, prec)
             torch.cuda.empty_cache()

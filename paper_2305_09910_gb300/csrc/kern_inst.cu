@@ -67,6 +67,49 @@ cudaError_t launch_step(const KParams& p, int closure, int mode, const Launch& L
   return cudaGetLastError();
 }
 
+// nsteps plain steps in one cooperative launch (k_step_multi): pull alternates p0 and p1, AA
+// alternates the even and odd forms on p0 starting with `odd0`.  The grid is what fits on
+// the device at once (a cooperative launch refuses more, it never waits).
+template <int Q, class S, int CL, int COLL, bool AA>
+static cudaError_t multi_one(const KParams2& pp, int nsteps, int odd0, cudaStream_t stream, int nsm) {
+  auto kern = k_step_multi<Q, S, CL, COLL, AA>;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+  const KParams& p = pp.p[0];
+  const long long ntiles = (long long)(p.nxp / 32) * ((p.ny + 3) / 4) * p.nz;
+  const int blocks = (int)std::min<long long>(ntiles, (long long)per_sm * nsm);
+  void* args[] = {(void*)&pp, (void*)&nsteps, (void*)&odd0};
+  return cudaLaunchCooperativeKernel((const void*)kern, dim3(blocks), dim3(32, 4), args, 0, stream);
+}
+
+template <int Q, class S, int COLL, bool AA>
+static cudaError_t multi_cl(const KParams2& pp, int closure, int nsteps, int odd0, cudaStream_t st, int nsm) {
+  return closure == CL_NONE ? multi_one<Q, S, CL_NONE, COLL, AA>(pp, nsteps, odd0, st, nsm)
+                            : multi_one<Q, S, CL_SMAG, COLL, AA>(pp, nsteps, odd0, st, nsm);
+}
+
+template <int Q, class S, bool AA>
+static cudaError_t multi_coll(const KParams2& pp, int closure, int coll, int nsteps, int odd0, cudaStream_t st,
+                              int nsm) {
+  if constexpr (Q == 19) {
+    if (coll == 1) return multi_cl<Q, S, 1, AA>(pp, closure, nsteps, odd0, st, nsm);
+  }
+  if (coll == 2) return multi_cl<Q, S, 2, AA>(pp, closure, nsteps, odd0, st, nsm);
+  return multi_cl<Q, S, 0, AA>(pp, closure, nsteps, odd0, st, nsm);
+}
+
+template <int Q, class S>
+cudaError_t launch_step_multi(const KParams& p0, const KParams& p1, int closure, int coll, bool aa, int odd0,
+                              int nsteps, cudaStream_t stream, int nsm) {
+  KParams2 pp;
+  pp.p[0] = p0;
+  pp.p[1] = p1;
+  return aa ? multi_coll<Q, S, true>(pp, closure, coll, nsteps, odd0, stream, nsm)
+            : multi_coll<Q, S, false>(pp, closure, coll, nsteps, odd0, stream, nsm);
+}
+
 #ifndef LBM_ASYNC_ZC
 #define LBM_ASYNC_ZC 8
 #endif
@@ -225,5 +268,7 @@ template cudaError_t launch_step_mlp<LBM_Q, LBM_S>(const KParams&, int, cudaStre
 template cudaError_t launch_export<LBM_Q, LBM_S>(const KParams&, int, int, const ExportArgs&, const Launch&);
 template cudaError_t launch_init_eq<LBM_Q, LBM_S>(const KParams&, const float*, const float*, const Launch&);
 template cudaError_t launch_set_pop<LBM_Q, LBM_S>(const KParams&, const float*, const Launch&);
+template cudaError_t launch_step_multi<LBM_Q, LBM_S>(const KParams&, const KParams&, int, int, bool, int, int,
+                                                     cudaStream_t, int);
 
 }  // namespace lbm

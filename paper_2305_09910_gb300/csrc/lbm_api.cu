@@ -42,6 +42,7 @@ struct lbm_s {
   KParams gkey{};
   int gkey_state[3] = {-1, -1, -1};  // parity, cur, nat_valid
   bool graphs_off = false;
+  bool multi_off = false;     // cooperative multi-step launches unavailable (refused once)
   double* stats = nullptr;    // ny * LBM_STATS_K doubles
   float* mlp = nullptr;       // MLP parameters widened to float
   float mlp_scale[2] = {0.f, 0.f};
@@ -354,6 +355,19 @@ int lbm_internal_info(lbm_handle h, int* q, int* precision, int* parity, int* cl
 lbm_status lbm_internal_fail(lbm_handle h, lbm_status s, const char* msg) { return fail(h, s, "%s", msg); }
 
 // ---- C ABI ----------------------------------------------------------------------------------
+
+// cooperative multi-step launch of k_step_multi for lbm_step (see run_multi)
+template <int Q>
+static cudaError_t dispatch_multi(const lbm_s* h, const KParams& p0, const KParams& p1, int nsteps) {
+  const bool aa = h->prm.streaming != LBM_PULL;
+  const int odd0 = aa ? h->parity : 0;
+  const int cl = h->prm.closure, coll = h->prm.collision;
+  switch (h->prm.precision) {
+    case LBM_F32: return launch_step_multi<Q, float>(p0, p1, cl, coll, aa, odd0, nsteps, h->stream, h->nsm);
+    case LBM_F16_SHIFTED: return launch_step_multi<Q, __half>(p0, p1, cl, coll, aa, odd0, nsteps, h->stream, h->nsm);
+    default: return launch_step_multi<Q, __nv_bfloat16>(p0, p1, cl, coll, aa, odd0, nsteps, h->stream, h->nsm);
+  }
+}
 
 // ---- refinement transfer kernels (2:1 across a z face; see lbm_refine_explode below) ----
 struct RefPlanes {
@@ -811,11 +825,66 @@ static bool graph_ready(lbm_handle h) {
   return true;
 }
 
+// ---- several steps per launch on small lattices ---------------------------------------------
+// On small lattices the steps are launch-bound even as graph replays: lbm_step runs them as
+// cooperative launches of k_step_multi, MULTI_CHUNK steps at most each, once the state is
+// steady (as for the graphs).  Measured on GB300 (FP32 D3Q19, us per step, multi / graph):
+// pull 32^3 3.8 / 6.7, 64x32x32 4.6 / 7.7, 64^3 11.1 / 11.3, 128x64x64 17.6 / 16.9; AA 32^3
+// 5.1 / 5.6, 64x32x32 6.1 / 6.2, 64^3 14.2 / 10.0 (the AA graph keeps the one array in L2).
+// Hence the limits in padded cells below.  A device that refuses the cooperative launch falls
+// back to the graphs.
+#ifndef LBM_MULTI_MAX_CELLS
+#define LBM_MULTI_MAX_CELLS (1ll << 17)
+#endif
+#ifndef LBM_MULTI_MAX_CELLS_AA
+#define LBM_MULTI_MAX_CELLS_AA (1ll << 15)
+#endif
+constexpr int64_t MULTI_CHUNK = 4096;
+
+static bool steady_state(const lbm_s* h) {
+  return h->prm.streaming == LBM_PULL ? h->parity == 2
+                                      : !(h->prm.face_bc[1] == LBM_FACE_OUTFLOW && h->nat_valid);
+}
+
+// Runs what it can of n steps as multi-step launches; returns the steps left.
+static int64_t run_multi(lbm_handle h, int64_t n) {
+  while (n >= 2) {
+    const int chunk = (int)std::min<int64_t>(n, MULTI_CHUNK);
+    KParams p0 = kparams(h), p1 = p0;
+    p0.nat_valid = p1.nat_valid = h->nat_valid;
+    if (h->prm.streaming == LBM_PULL) {  // the second array's view
+      h->cur ^= 1;
+      p1 = kparams(h);
+      h->cur ^= 1;
+      p1.nat_valid = h->nat_valid;
+    }
+    const cudaError_t e = h->q == 19 ? dispatch_multi<19>(h, p0, p1, chunk) : dispatch_multi<27>(h, p0, p1, chunk);
+    if (e != cudaSuccess) {  // refused before anything ran: use the graphs from now on
+      cudaGetLastError();
+      h->multi_off = true;
+      return n;
+    }
+    for (int k = 0; k < chunk; k++) advance_state(h);
+    n -= chunk;
+  }
+  return n;
+}
+
 lbm_status lbm_step(lbm_handle h, int64_t n) {
   if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
   if (n < 0) return fail(h, LBM_EINVAL, "n must be >= 0");
   if (h->prm.closure == LBM_CLOSURE_MLP && !h->mlp_set)
     return fail(h, LBM_ESTATE, "MLP closure selected but lbm_set_closure was not called");
+  const long long multi_max = h->prm.streaming == LBM_PULL ? LBM_MULTI_MAX_CELLS : LBM_MULTI_MAX_CELLS_AA;
+  if (n >= 2 && !h->multi_off && h->prm.pipeline == LBM_PIPE_DIRECT && h->prm.closure != LBM_CLOSURE_MLP &&
+      (long long)h->nxp * h->ny * h->nz <= multi_max) {
+    while (n > 0 && !steady_state(h)) {  // settle with single launches
+      lbm_status s = run_steps(h, 1, 0);
+      if (s != LBM_OK) return s;
+      n--;
+    }
+    n = run_multi(h, n);
+  }
   // settle the state with single launches first (the first pull step, the AA outflow import)
   while (n > 0 && n >= 2 * GRAPH_STEPS && !graph_ready(h) && !h->graphs_off &&
          (h->prm.streaming == LBM_PULL ? h->parity != 2 : h->nat_valid != 0) &&

@@ -26,6 +26,7 @@
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -1131,6 +1132,57 @@ __global__ void __launch_bounds__(128, Q == 19 ? (COLL == 1 ? 8 : LBM_STEP_MINB1
     if (STATS) stat_values(M, v);
   }
   if (STATS) stat_warp_store(p, y, z, blockIdx.x, p.nxp / 32, v);
+}
+
+// ---- several steps in one launch --------------------------------------------------------
+// Small lattices are launch-bound: k_step_multi runs nsteps plain steps in one cooperative
+// launch, the steps separated by grid-wide barriers (cooperative groups), each block taking
+// the (32 x 4)-cell tiles of k_step's grid in turn.  Two-grid pull alternates the two arrays
+// (pp.p[s & 1]); AA alternates the even and odd forms on one array, starting with the form
+// `odd0`.  Every cell gets the bits of the single-launch step.
+struct KParams2 {
+  KParams p[2];
+};
+
+template <int Q, class S, int CL, int LOAD, int STORE, int COLL>
+__device__ __forceinline__ void step_tile(const KParams& p, int tile) {
+  const int tx = p.nxp / 32, ty = (p.ny + 3) / 4;
+  const int bz = tile / (tx * ty);
+  const int r = tile - bz * tx * ty;
+  const int by = r / tx, bx = r - by * tx;
+  const int x = bx * 32 + threadIdx.x;
+  const int y = by * 4 + threadIdx.y;
+  const int z = bz;
+  if (y >= p.ny) return;  // whole warp
+  const int cell = cidx(p, x, y, z);
+  const int cls = x < p.nx ? cls_at(p, cell) : CLS_SKIP;
+  float f[Q];
+  unsigned outmask;
+  load_state<Q, S, LOAD>(p, x, y, z, cell, cls, f, outmask);
+  outflow_fix<Q>(p, x, f, outmask);
+  if (cls == CLS_SKIP) return;
+  const float rho = collide<Q, CL, float, acc_form<S>, COLL>(p, f, nullptr);
+  if (!(rho > 0.f && rho < 3.0e38f)) atomicOr(p.status, 1);
+  store_state<Q, S, STORE>(p, x, y, z, cell, cls, f);
+}
+
+template <int Q, class S, int CL, int COLL, bool AA>
+__global__ void __launch_bounds__(128, Q == 19 ? 8 : 6) k_step_multi(const __grid_constant__ KParams2 pp, int nsteps, int odd0) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  const KParams& p0 = pp.p[0];
+  const int ntiles = (p0.nxp / 32) * ((p0.ny + 3) / 4) * p0.nz;
+  for (int s = 0; s < nsteps; s++) {
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      if (AA) {
+        if ((s + odd0) & 1) step_tile<Q, S, CL, 1, 1, COLL>(p0, t);
+        else step_tile<Q, S, CL, 0, 0, COLL>(p0, t);
+      } else {
+        step_tile<Q, S, CL, 2, 2, COLL>(pp.p[s & 1], t);
+      }
+    }
+    if (s + 1 < nsteps) grid.sync();
+  }
 }
 
 // The same step with register double-buffering along z: each thread updates ZC cells

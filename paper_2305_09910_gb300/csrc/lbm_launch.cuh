@@ -32,6 +32,9 @@ template <int Q, class S>
 cudaError_t launch_init_eq(const KParams& p, const float* rho, const float* u, const Launch& L);
 template <int Q, class S>
 cudaError_t launch_set_pop(const KParams& p, const float* df, const Launch& L);
+template <int Q, class S>
+cudaError_t launch_step_multi(const KParams& p0, const KParams& p1, int closure, int coll, bool aa, int odd0,
+                              int nsteps, cudaStream_t stream, int nsm);
 
 #define LBM_DECLARE_INSTANCE(Q, S)                                                                 \
   extern template cudaError_t launch_step<Q, S>(const KParams&, int, int, const Launch&, bool, int*, int); \
@@ -43,7 +46,9 @@ cudaError_t launch_set_pop(const KParams& p, const float* df, const Launch& L);
                                                   const Launch&);                                  \
   extern template cudaError_t launch_init_eq<Q, S>(const KParams&, const float*, const float*,     \
                                                    const Launch&);                                 \
-  extern template cudaError_t launch_set_pop<Q, S>(const KParams&, const float*, const Launch&);
+  extern template cudaError_t launch_set_pop<Q, S>(const KParams&, const float*, const Launch&);     \
+  extern template cudaError_t launch_step_multi<Q, S>(const KParams&, const KParams&, int, int, bool, int, \
+                                                      int, cudaStream_t, int);
 
 LBM_DECLARE_INSTANCE(19, float)
 LBM_DECLARE_INSTANCE(19, __half)

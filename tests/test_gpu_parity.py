@@ -526,8 +526,9 @@ def test_step_stats_rejects_bad_arguments():
 @pytest.mark.parametrize("name,streaming,precision", [("tunnel19", "aa", "f32"), ("channel19", "pull", "f32"),
                                                       ("channel27", "aa", "f16"), ("mixed19", "pull", "bf16")])
 def test_graph_replayed_steps_match_single_launches(name, streaming, precision):
-    """lbm_step(n) replays a CUDA graph of 8 steps on a steady state; the bits equal n single
-    launches, also across a change of the force between calls (the graph is re-captured)."""
+    """lbm_step(n) on a steady state runs several steps per launch (on these small lattices as
+    cooperative multi-step launches); the bits equal n single launches, also across a change
+    of the force between calls."""
     from paper_2305_09910_gb300 import lbm
 
     case = dict(CASES[name])
