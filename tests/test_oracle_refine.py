@@ -11,6 +11,9 @@ the scheme's published properties fix, not against itself:
   the viscosity, tau_f - 1/2 = 2 (tau_c - 1/2));
 * the analytic Poiseuille profile across a refined slab between no-slip walls (viscosity and
   body-force scaling F_f = F_c / 2);
+* with several refined slabs, and slabs on the no-slip walls (halfway bounce-back on the
+  fine level): exact mass conservation, the Poiseuille parabola with both walls refined (the
+  channel case), the shear-wave rate across four interfaces;
 * planted mistakes in the oracle (wrong viscosity scaling, an unshifted coalescence) fail
   these pins.
 """
@@ -204,3 +207,87 @@ def test_planted_unshifted_coalescence_fails_transport_pin():
     coal_wrong = r.coalesce(np.concatenate([ext[:, 2:4], ext[:, 2:]], axis=1))[r.lo][i]
     coal_right = r.coalesce(r.fine_stream(r.fine_stream(ext)))[r.lo][i]
     assert coal_right[1, 2] == 1.0 and coal_wrong[1, 2] != 1.0
+
+
+# ---- several slabs, slabs on the walls -------------------------------------------------------
+def _smooth_multi(r, seed=9):
+    nz, ny, nx = r.nz, r.ny, r.nx
+    rc = 1.0 + inputs.uniform_field(seed, 1, (nz, ny, nx), -0.01, 0.01)
+    uc = inputs.uniform_field(seed, 2, (3, nz, ny, nx), -0.02, 0.02)
+    rf, uf = [], []
+    for k, s in enumerate(r.slabs):
+        shp = (s.nzf, 2 * ny, 2 * nx)
+        rf.append(1.0 + inputs.uniform_field(seed, 10 + k, shp, -0.01, 0.01))
+        uf.append(inputs.uniform_field(seed, 20 + k, (3,) + shp, -0.02, 0.02))
+    r.init_equilibrium(rc, uc, rf, uf)
+
+
+@pytest.mark.parametrize("walls,slabs", [(False, [(1, 3), (5, 8)]), (True, [(0, 2), (6, 9)]),
+                                         (True, [(0, 3)]), (True, [(3, 5), (7, 9)])])
+def test_several_slabs_conserve_mass(walls, slabs):
+    r = RefinedOracle(4, 2, 9, q=19, tau=0.7, walls=walls, slabs=slabs)
+    _smooth_multi(r)
+    m0, j0 = r.mass(), r.momentum()
+    r.step(15)
+    assert abs(r.mass() - m0) <= 1e-13 * m0
+    if not walls:
+        assert np.abs(r.momentum() - j0).max() <= 1e-13 * m0
+    assert not any(np.isnan(f).any() for f in r.ffs) and not np.isnan(r.fc[:, ~r.covered]).any()
+
+
+def test_poiseuille_with_refined_wall_slabs():
+    """The channel case: both walls inside fine slabs, a coarse core; the analytic parabola
+    on both levels (walls half a fine cell beyond the first fine cell centres)."""
+    nz, tau, F = 16, 1.0, 1e-6
+    nu = (tau - 0.5) / 3
+    r = RefinedOracle(2, 2, nz, q=19, tau=tau, force=(F, 0, 0), walls=True, slabs=[(0, 4), (12, 16)])
+    r.init_equilibrium(1.0, np.zeros(3), [1.0, 1.0], [np.zeros(3), np.zeros(3)])
+    r.step(3000)
+    cxd = r.c[:, 0].astype(float)
+
+    def ux(f, fx):
+        return ((np.tensordot(cxd, f, axes=(0, 0)) + fx / 2) / f.sum(0)).mean(axis=(1, 2))
+
+    ana = lambda z: F / (2 * nu) * (z + 0.5) * (nz - z - 0.5)
+    umax = ana(nz / 2 - 0.5)
+    m = ~r.covered
+    err = np.abs(ux(r.fc[:, m], F) - ana(np.arange(nz, dtype=float)[m])).max() / umax
+    for s, f in zip(r.slabs, r.ffs):
+        zf = s.z0 + (np.arange(s.nzf) + 0.5) / 2 - 0.5
+        err = max(err, np.abs(ux(f, F / 2) - ana(zf)).max() / umax)
+    assert err <= 1e-6, err
+
+
+def test_shear_wave_with_two_slabs_decays_at_the_viscous_rate():
+    nz, tau, U = 32, 0.8, 1e-3
+    k = 2 * np.pi / nz
+    r = RefinedOracle(2, 2, nz, q=19, tau=tau, slabs=[(4, 10), (18, 26)])
+    zc = np.arange(nz, dtype=float)
+    uc = np.zeros((3, nz, 2, 2))
+    uc[0] = U * np.sin(k * zc)[:, None, None]
+    zfs = [s.z0 + (np.arange(s.nzf) + 0.5) / 2 - 0.5 for s in r.slabs]
+    ufs = []
+    for s, zf in zip(r.slabs, zfs):
+        u = np.zeros((3, s.nzf, 4, 4))
+        u[0] = U * np.sin(k * zf)[:, None, None]
+        ufs.append(u)
+    r.init_equilibrium(1.0, uc, [1.0, 1.0], ufs)
+    cxd = r.c[:, 0].astype(float)
+    m = ~r.covered
+
+    def amp():
+        f = np.where(np.isnan(r.fc), 0.0, r.fc)
+        with np.errstate(invalid="ignore"):
+            uxc = (np.tensordot(cxd, f, axes=(0, 0)) / f.sum(0)).mean(axis=(1, 2))
+        num = (uxc[m] * np.sin(k * zc[m])).sum()
+        den = (np.sin(k * zc[m]) ** 2).sum()
+        for ff, zf in zip(r.ffs, zfs):
+            uxf = (np.tensordot(cxd, ff, axes=(0, 0)) / ff.sum(0)).mean(axis=(1, 2))
+            num += 0.5 * (uxf * np.sin(k * zf)).sum()
+            den += 0.5 * (np.sin(k * zf) ** 2).sum()
+        return num / den
+
+    a0 = amp()
+    r.step(400)
+    rate = -np.log(amp() / a0) / 400
+    assert abs(rate / ((tau - 0.5) / 3 * k * k) - 1.0) <= 5e-3
