@@ -409,7 +409,7 @@ def _refined_form(nsteps, warmup, peak, peak_kind, precision="f32"):
     ms = t0.elapsed_time(t1) / nsteps
     upd = rs.updates_per_step
     bpu = float(rs.fine.bytes_per_update)
-    launches = 3 * len(rs.interfaces) + 2 + len(rs.coarse)  # explode x2, coalesce per interface; steps
+    launches = 3 * len(rs.interfaces) + 2 * len(rs.fines) + len(rs.coarse)  # transfers; steps
     rs.close()
     achieved = upd * bpu / (ms * 1e-3) / 1e9
     return {"MLUPS": round(upd / (ms * 1e-3) / 1e6, 1), "updates_per_coarse_step": upd,

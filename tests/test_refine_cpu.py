@@ -8,20 +8,35 @@ from paper_2305_09910_gb300 import refine
 
 
 def test_plan_periodic_wraps_one_coarse_piece():
-    pieces, inter = refine.plan(10, 3, 7, walls=False)
-    assert pieces == [([7, 8, 9, 0, 1, 2], ("halo", "halo"))]
-    # the piece's -z face (global plane 7) meets the slab's +z face, its +z face (plane 2) the slab's -z face
-    assert inter == [(0, 4, 5), (0, 5, 4)]
+    coarse, fine, inter = refine.plan(10, [(3, 7)], walls=False)
+    assert coarse == [([7, 8, 9, 0, 1, 2], ("halo", "halo"))]
+    assert fine == [((3, 7), ("halo", "halo"))]
+    # the slab's -z face meets the piece's +z face (plane 2), its +z face the piece's -z face (plane 7)
+    assert sorted(inter) == [(0, 4, 0, 5), (0, 5, 0, 4)]
 
 
 def test_plan_walls_two_coarse_pieces():
-    pieces, inter = refine.plan(9, 2, 6, walls=True)
-    assert pieces == [([0, 1], ("wall", "halo")), ([6, 7, 8], ("halo", "wall"))]
-    assert inter == [(0, 5, 4), (1, 4, 5)]
+    coarse, fine, inter = refine.plan(9, [(2, 6)], walls=True)
+    assert coarse == [([0, 1], ("wall", "halo")), ([6, 7, 8], ("halo", "wall"))]
+    assert inter == [(0, 5, 0, 4), (1, 4, 0, 5)]
 
 
-@pytest.mark.parametrize("args", [(8, 3, 3, False), (8, 0, 7, False), (8, 0, 4, True), (8, 2, 8, True),
-                                  (8, 5, 3, False)])
+def test_plan_refined_walls_of_a_channel():
+    coarse, fine, inter = refine.plan(16, [(12, 16), (0, 4)], walls=True)
+    assert coarse == [(list(range(4, 12)), ("halo", "halo"))]
+    assert fine == [((0, 4), ("wall", "halo")), ((12, 16), ("halo", "wall"))]
+    assert inter == [(0, 4, 0, 5), (0, 5, 1, 4)]
+
+
+def test_plan_two_periodic_slabs():
+    coarse, fine, inter = refine.plan(12, [(1, 3), (6, 9)], walls=False)
+    assert coarse == [([9, 10, 11, 0], ("halo", "halo")), ([3, 4, 5], ("halo", "halo"))]
+    assert sorted(inter) == [(0, 4, 1, 5), (0, 5, 0, 4), (1, 4, 0, 5), (1, 5, 1, 4)]
+
+
+@pytest.mark.parametrize("args", [(8, [(3, 3)], False), (8, [(0, 7)], False), (8, [(2, 9)], True),
+                                  (8, [(5, 3)], False), (8, [(1, 3), (3, 5)], True), (8, [(0, 2), (6, 8)], False),
+                                  (8, [(0, 8)], True), (8, [], True)])
 def test_plan_rejects_bad_ranges(args):
     with pytest.raises(ValueError):
         refine.plan(*args)
