@@ -146,9 +146,17 @@ class RefinedSlab:
         self._primed = False
 
     def _per_slab(self, a):
+        """One entry per slab: a list as given, None for every slab, or a single array for a
+        single slab."""
         if isinstance(a, (list, tuple)):
+            if len(a) != len(self.fines):
+                raise ValueError(f"expected {len(self.fines)} fine-level arrays, got {len(a)}")
             return list(a)
-        return [a] * len(self.fines) if a is None else [a]
+        if a is None:
+            return [None] * len(self.fines)
+        if len(self.fines) != 1:
+            raise ValueError("several refined slabs: pass one fine-level array per slab (a list)")
+        return [a]
 
     def set_populations(self, dfc, dff):
         """Shifted populations df = f - w (pre-collision): dfc (q, nz, ny, nx), dff one

@@ -45,3 +45,16 @@ def test_plan_rejects_bad_ranges(args):
 def test_fine_tau_doubles_the_lattice_viscosity():
     for tau in (0.51, 0.8, 1.3):
         assert (refine.fine_tau(tau) - 0.5) / 3 == pytest.approx(2 * (tau - 0.5) / 3)
+
+
+def test_per_slab_arrays_must_match_the_slabs():
+    rs = refine.RefinedSlab.__new__(refine.RefinedSlab)  # host logic only, no lattices
+    rs.fines = [object(), object()]
+    assert rs._per_slab(None) == [None, None]
+    assert rs._per_slab([1, 2]) == [1, 2]
+    with pytest.raises(ValueError):
+        rs._per_slab([1])
+    with pytest.raises(ValueError):
+        rs._per_slab(1)
+    rs.fines = [object()]
+    assert rs._per_slab(3) == [3]
