@@ -237,7 +237,10 @@ lbm_status lbm_set_force(lbm_handle h, double fx, double fy, double fz);
 lbm_status lbm_init_equilibrium(lbm_handle h, const float* rho, const float* u, int on_device);
 
 /* Advances n >= 0 time steps (collision then streaming, Sec. 2).  Asynchronous: returns
- * after enqueuing; instability is reported by lbm_sync. */
+ * after enqueuing; instability is reported by lbm_sync.  Once the state is steady, several
+ * steps go into one launch: on small lattices (up to 2^17 padded cells for two-grid pull,
+ * 2^15 for AA) cooperative launches of up to 4096 steps separated by grid-wide barriers,
+ * above that replays of a CUDA graph of 8 steps; the result has the bits of n single steps. */
 lbm_status lbm_step(lbm_handle h, int64_t n);
 
 /* Waits for the handle's stream.  LBM_EUNSTABLE if any step since the last state reset saw a
