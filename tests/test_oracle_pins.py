@@ -552,3 +552,24 @@ def test_stats_sample_matches_moments(O):
     assert np.allclose(acc[:, 0], 24)
     assert np.allclose(acc[:, 1], u[0].sum(axis=(0, 2)), rtol=0, atol=1e-15)
     assert np.allclose(acc[:, 7], (u[0] * u[1]).sum(axis=(0, 2)), rtol=0, atol=1e-15)
+
+
+def test_velocity_set_weights_match_the_published_tables(O):
+    """tests/golden/velocity_set_weights.txt: the D3Q19 and D3Q27 weights by squared speed
+    (Qian, d'Humieres & Lallemand 1992) and c_s^2 = 1/3."""
+    import os
+    from fractions import Fraction
+
+    path = os.path.join(os.path.dirname(__file__), "golden", "velocity_set_weights.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    for q in (19, 27):
+        c, w, _ = O.stencil(q)
+        c2 = (c * c).sum(axis=1)
+        for st, speed, count, frac in rows:
+            if int(st) != q:
+                continue
+            sel = c2 == int(speed)
+            assert sel.sum() == int(count)
+            assert np.all(np.abs(w[sel] - float(Fraction(frac))) <= 1e-17)
+        # c_s^2 = sum_i w_i c_ix^2
+        assert abs((w * c[:, 0] ** 2).sum() - 1.0 / 3.0) <= 1e-16
