@@ -30,6 +30,7 @@ FACE = {"periodic": 0, "wall": 1, "freeslip": 2, "inflow": 3, "outflow": 4}
 CELL = {"fluid": 0, "solid": 1, "inflow": 2}
 CLOSURE = {"none": 0, "smag": 1, "mlp": 2}
 MLP_NPARAM = 32 * 7 + 32 + 32 * 32 + 32 + 32 + 1
+CFLAGS = ["-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared", "-D_GNU_SOURCE"]
 
 
 def build(force: bool = False) -> str:
@@ -38,8 +39,7 @@ def build(force: bool = False) -> str:
             os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "lbm_oracle.h"))):
         return _SO
     tmp = _SO + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
-           "-D_GNU_SOURCE", "-o", tmp, _SRC, "-lm"]
+    cmd = ["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _SO)
     return _SO
@@ -70,41 +70,46 @@ class _Cfg(ctypes.Structure):
     ]
 
 
+def load(path: str):
+    """Loads a compiled copy of the oracle from ``path`` and declares its functions."""
+    L = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    L.ora_stencil.argtypes = [ctypes.c_int, P, P, P]
+    L.ora_equilibrium.argtypes = [ctypes.c_int, ctypes.c_double, P, P]
+    L.ora_smag_tau.argtypes = [ctypes.c_double] * 4
+    L.ora_smag_tau.restype = ctypes.c_double
+    L.ora_collide.argtypes = [P, P, P, P]
+    L.ora_mrt_row.argtypes = [ctypes.c_int, ctypes.c_int]
+    L.ora_mrt_row.restype = ctypes.c_double
+    L.ora_moments_cell.argtypes = [P, P, P, P]
+    L.ora_check.argtypes = [P]
+    L.ora_step.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int]
+    L.ora_stream.argtypes = [P, P, P, ctypes.c_int]
+    L.ora_collide_all.argtypes = [P, P, P, ctypes.c_int]
+    L.ora_init_equilibrium.argtypes = [P, P, P, P]
+    L.ora_moments.argtypes = [P, P, P, P]
+    L.ora_mass_momentum.argtypes = [P, P, P]
+    L.ora_step_sampled.argtypes = [P, P, P, P, ctypes.c_int64, P]
+    L.ora_stats_sample.argtypes = [P, P, P]
+    L.ora_mlp_forward.argtypes = [P, P, P, P, P, P]
+    L.ora_mlp_forward.restype = ctypes.c_double
+    L.ora_mlp_backward.argtypes = [P, P, ctypes.c_double, P]
+    L.ora_mlp_features.argtypes = [P, P, P]
+    L.ora_closure_samples.argtypes = [P, P, ctypes.c_double, ctypes.c_double, P, P, P, P, P]
+    L.ora_closure_loss.argtypes = [P, P, P, P, P, ctypes.c_int64, ctypes.c_double, P]
+    L.ora_closure_loss.restype = ctypes.c_double
+    L.ora_filter2.argtypes = [P, P, P, P]
+    L.ora_adam.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                           ctypes.c_double, ctypes.c_double, ctypes.c_int64]
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            L = ctypes.CDLL(_SO)
-            P = ctypes.c_void_p
-            L.ora_stencil.argtypes = [ctypes.c_int, P, P, P]
-            L.ora_equilibrium.argtypes = [ctypes.c_int, ctypes.c_double, P, P]
-            L.ora_smag_tau.argtypes = [ctypes.c_double] * 4
-            L.ora_smag_tau.restype = ctypes.c_double
-            L.ora_collide.argtypes = [P, P, P, P]
-            L.ora_mrt_row.argtypes = [ctypes.c_int, ctypes.c_int]
-            L.ora_mrt_row.restype = ctypes.c_double
-            L.ora_moments_cell.argtypes = [P, P, P, P]
-            L.ora_check.argtypes = [P]
-            L.ora_step.argtypes = [P, P, P, ctypes.c_int64, ctypes.c_int]
-            L.ora_stream.argtypes = [P, P, P, ctypes.c_int]
-            L.ora_collide_all.argtypes = [P, P, P, ctypes.c_int]
-            L.ora_init_equilibrium.argtypes = [P, P, P, P]
-            L.ora_moments.argtypes = [P, P, P, P]
-            L.ora_mass_momentum.argtypes = [P, P, P]
-            L.ora_step_sampled.argtypes = [P, P, P, P, ctypes.c_int64, P]
-            L.ora_stats_sample.argtypes = [P, P, P]
-            L.ora_mlp_forward.argtypes = [P, P, P, P, P, P]
-            L.ora_mlp_forward.restype = ctypes.c_double
-            L.ora_mlp_backward.argtypes = [P, P, ctypes.c_double, P]
-            L.ora_mlp_features.argtypes = [P, P, P]
-            L.ora_closure_samples.argtypes = [P, P, ctypes.c_double, ctypes.c_double, P, P, P, P, P]
-            L.ora_closure_loss.argtypes = [P, P, P, P, P, ctypes.c_int64, ctypes.c_double, P]
-            L.ora_closure_loss.restype = ctypes.c_double
-            L.ora_filter2.argtypes = [P, P, P, P]
-            L.ora_adam.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
-                                   ctypes.c_double, ctypes.c_double, ctypes.c_int64]
-            _lib = L
+            _lib = load(_SO)
     return _lib
 
 
