@@ -90,6 +90,7 @@ def load(path: str):
     L.ora_moments.argtypes = [P, P, P, P]
     L.ora_mass_momentum.argtypes = [P, P, P]
     L.ora_step_sampled.argtypes = [P, P, P, P, ctypes.c_int64, P]
+    L.ora_step_sampled_pop.argtypes = [P, P, P, ctypes.c_int64, P]
     L.ora_stats_sample.argtypes = [P, P, P]
     L.ora_mlp_forward.argtypes = [P, P, P, P, P, P]
     L.ora_mlp_forward.restype = ctypes.c_double
@@ -325,4 +326,14 @@ class Oracle:
         out = np.zeros((cells.size, self.q), dtype=np.float64)
         lib().ora_step_sampled(ctypes.byref(self.cfg), _ptr(rho_in), _ptr(u_in), _ptr(cells),
                                cells.size, _ptr(out))
+        return out
+
+    def step_sampled_pop(self, df, cells):
+        """One step from f = w + df (df: shifted float32 populations of every cell, shaped like
+        f), at the listed linear cells.  Returns an array (len(cells), q) of plain f_i(x, t+1)."""
+        df = np.ascontiguousarray(df, dtype=np.float32)
+        assert df.size == self.q * self.N
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        out = np.zeros((cells.size, self.q), dtype=np.float64)
+        lib().ora_step_sampled_pop(ctypes.byref(self.cfg), _ptr(df), _ptr(cells), cells.size, _ptr(out))
         return out

@@ -585,6 +585,43 @@ void ora_step_sampled(const ora_cfg* cfg, const float* rho_in, const float* u_in
   }
 }
 
+/* On-demand post-collision values for ora_step_sampled_pop: f(t) = w + df (shifted float32
+ * populations given for every cell, [q][N]). */
+typedef struct {
+  const ora_cfg* cfg;
+  const float* df;
+  int64_t ncell;
+  int64_t cached_cell;
+  double cached[27];
+} pop_ctx;
+
+static double pop_lookup(void* vctx, int64_t cell, int dir) {
+  pop_ctx* e = (pop_ctx*)vctx;
+  if (e->cached_cell != cell) {
+    double f[27];
+    for (int i = 0; i < e->cfg->q; i++) f[i] = W_(e->cfg->q, i) + (double)e->df[(int64_t)i * e->ncell + cell];
+    ora_collide(e->cfg, f, e->cached, NULL);
+    e->cached_cell = cell;
+  }
+  return e->cached[dir];
+}
+
+void ora_step_sampled_pop(const ora_cfg* cfg, const float* df, const int64_t* cells, int64_t n, double* out) {
+  const int64_t N = (int64_t)cfg->nx * cfg->ny * cfg->nz;
+  for (int64_t k = 0; k < n; k++) {
+    int64_t c = cells[k];
+    int x = (int)(c % cfg->nx), y = (int)((c / cfg->nx) % cfg->ny), z = (int)(c / ((int64_t)cfg->nx * cfg->ny));
+    pop_ctx e = {cfg, df, N, -1, {0}};
+    for (int i = 0; i < cfg->q; i++) {
+      if (cfg->flags && cfg->flags[c] != ORA_CELL_FLUID) {
+        out[k * cfg->q + i] = 0.0;
+        continue;
+      }
+      out[k * cfg->q + i] = ora_pull(cfg, x, y, z, i, pop_lookup, &e);
+    }
+  }
+}
+
 void ora_stats_sample(const ora_cfg* cfg, const double* f, double* acc) {
   const int q = cfg->q;
   const int64_t N = (int64_t)cfg->nx * cfg->ny * cfg->nz;

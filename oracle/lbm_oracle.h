@@ -125,6 +125,10 @@ void ora_mass_momentum(const ora_cfg* cfg, const double* f, double* out);
 void ora_step_sampled(const ora_cfg* cfg, const float* rho_in, const float* u_in,
                       const int64_t* cells, int64_t n, double* out);
 
+/* One step from f(t) = w + df, df the shifted float32 populations of every cell ([q][N], e.g.
+ * a GPU state), evaluated only at the listed cells.  out is n*q (cell-major), plain f. */
+void ora_step_sampled_pop(const ora_cfg* cfg, const float* df, const int64_t* cells, int64_t n, double* out);
+
 /* Adds one sample of per-y-plane velocity sums to acc (ny*10):
  * count, Su_x, Su_y, Su_z, Su_x^2, Su_y^2, Su_z^2, Su_xu_y, Su_xu_z, Su_yu_z. */
 void ora_stats_sample(const ora_cfg* cfg, const double* f, double* acc);

@@ -4,6 +4,8 @@
   full-size sampled parity) equals the pinned whole-lattice step ``ora_step`` from the same
   state at every cell of channel, wind-tunnel and mixed-face lattices, both stencils, to
   1e-15 (Eq. LBCollision then Eq. LBStreaming, Sec. 2).
+* ``ora_step_sampled_pop`` (the same from arbitrary shifted float32 populations, used to
+  check a step of the bench's gather kernel at full size) equals ``ora_step`` likewise.
 * ``ora_filter2`` (width-2 box filter with Favre velocity, the closure's training data)
   returns, for linear density and momentum fields, the closed form: the box mean is the
   value at the box centre, the Favre velocity the centre momentum over the centre density;
@@ -75,14 +77,48 @@ def test_step_sampled_equals_whole_lattice_step(oracle_mod, q, name, faces, kw):
 
 @pytest.mark.parametrize("edit", [
     # the cached post-collision values are the equilibrium itself (the collision is skipped)
-    ("    ora_collide(e->cfg, f, e->cached, NULL);\n", "    memcpy(e->cached, f, sizeof f);\n"),
+    ("uc, f);\n    ora_collide(e->cfg, f, e->cached, NULL);\n", "uc, f);\n    memcpy(e->cached, f, sizeof f);\n"),
     # the one-cell cache is never refreshed: every source reads the first cell looked up
-    ("  if (e->cached_cell != cell) {\n", "  if (e->cached_cell < 0) {\n"),
+    ("  if (e->cached_cell != cell) {\n    double f[27], uc[3]", "  if (e->cached_cell < 0) {\n    double f[27], uc[3]"),
 ], ids=["no_collision", "stale_cache"])
 def test_planted_mistakes_in_step_sampled_fail_the_pin(oracle_mod, edit):
     with mutant([edit]):
         err, _ = _sampled_vs_step(oracle_mod, 19, FACES_CHANNEL, CASES[0][2])
     assert err > 1e-6, err
+
+
+def _sampled_pop_vs_step(O, q, faces, kw, seed=4):
+    """The sampled step from arbitrary populations (a developed, non-equilibrium state)."""
+    nx, ny, nz = 13, 9, 7
+    flags = _flags(nx, ny, nz, seed, inflow_cells=faces[0] != "inflow" or q == 27)
+    o = O.Oracle(nx, ny, nz, q=q, tau=0.57, faces=faces, flags=flags, **kw)
+    rho, u = _fields(nx, ny, nz, seed)
+    o.init_equilibrium(rho.astype(np.float64), u.astype(np.float64))
+    o.step(2, threads=1)
+    df = o.shifted().astype(np.float32)
+    o.set_shifted(df)  # both sides start from the same float32 values
+    o.step(1, threads=1)
+    cells = np.arange(nx * ny * nz)
+    got = o.step_sampled_pop(df, cells)
+    ref = o.f.reshape(q, -1).T
+    fluid = flags.reshape(-1) == 0
+    return float(np.abs(got[fluid] - ref[fluid]).max()), float(np.abs(got[~fluid]).max(initial=0.0))
+
+
+@pytest.mark.parametrize("q", [19, 27])
+@pytest.mark.parametrize("name,faces,kw", CASES, ids=[c[0] for c in CASES])
+def test_step_sampled_from_populations_equals_whole_lattice_step(oracle_mod, q, name, faces, kw):
+    err, solid = _sampled_pop_vs_step(oracle_mod, q, faces, kw)
+    assert err <= 1e-15, err
+    assert solid == 0.0
+
+
+def test_planted_mistake_in_step_sampled_from_populations_fails_the_pin(oracle_mod):
+    # the populations are unshifted with the D3Q19 weights whatever the stencil
+    with mutant([("for (int i = 0; i < e->cfg->q; i++) f[i] = W_(e->cfg->q, i) + (double)e->df",
+                  "for (int i = 0; i < e->cfg->q; i++) f[i] = W_(19, i) + (double)e->df")]):
+        err, _ = _sampled_pop_vs_step(oracle_mod, 27, FACES_TUNNEL, CASES[1][2])
+    assert err > 1e-3, err
 
 
 # ---- box filter --------------------------------------------------------------------------
