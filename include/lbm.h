@@ -124,7 +124,7 @@ typedef struct {
   double u_inflow[3];   /* velocity of INFLOW faces and cells, default 0 */
   double rho_inflow;    /* density used by moving-wall bounce-back, default 1 */
   void* stream;         /* cudaStream_t for all work, default NULL */
-  int32_t pipeline;     /* load pipeline of the AA step kernels (LBM_PIPE_*), default DIRECT */
+  int32_t pipeline;     /* load pipeline (LBM_PIPE_*): DIRECT, the default, is the only one built */
   int32_t collision;    /* LBM_COLL_TRT (default) | LBM_COLL_MRT (D3Q19) | LBM_COLL_REG;
                          * MRT and REG without the learned closure */
   double mrt_rates[5];  /* MRT rates of the moment groups e, eps, q, pi, m; default
@@ -140,16 +140,14 @@ typedef struct {
  * D3Q19HRR scheme (Sec. 4 and 5.1 name it without a definition; its finite-difference
  * blend is not built): with g = f - f^eq + F_i/2,
  * f*_i = f^eq_i + F_i/2 + (1 - 1/tau_eff) (9/2) w_i H_i : sum_j H_j g_j, H_i = c_i c_i - I/3
- * (D3Q19 and D3Q27).  Every pipeline runs the MRT and REG steps as the direct one-cell kernel. */
+ * (D3Q19 and D3Q27). */
 enum { LBM_COLL_TRT = 0, LBM_COLL_MRT = 1, LBM_COLL_REG = 2 };
 
-/* load pipeline of the step kernels:
- * DIRECT (default) = every thread loads its cell from global memory;
- * TMA = AA loads staged in shared memory by 1-D bulk copies in a 3-stage mbarrier pipeline
- *   of persistent CTAs; PREFETCH = AA loads double-buffered in registers along z;
- * ASYNC = loads staged in shared memory by per-lane asynchronous copies (cp.async) a few
- *   cells ahead along z (FP32 storage; AA and two-grid pull; half storage loads directly).
- * All compute bit-identical updates. */
+/* load pipeline of the step kernels.  DIRECT (the default and the only one built): every thread
+ * loads its cell's populations straight from global memory.  The staged forms (TMA bulk copies
+ * into shared memory, register prefetch along z, per-lane cp.async) were measured slower than
+ * direct loads on GB300, whose loads already move exactly the algorithmic bytes; their values
+ * stay reserved and lbm_create answers them with LBM_EUNSUPPORTED. */
 enum { LBM_PIPE_TMA = 0, LBM_PIPE_DIRECT = 1, LBM_PIPE_PREFETCH = 2, LBM_PIPE_ASYNC = 3 };
 
 /* Halo exchange of z slabs (Sec. 3: a block's communication kernels pack and unpack the
@@ -202,107 +200,146 @@ lbm_status lbm_halo_unpack(lbm_handle h, int face, const void* buf);
 lbm_status lbm_refine_explode(lbm_handle coarse, int coarse_face, lbm_handle fine, int fine_face, int substep);
 lbm_status lbm_refine_coalesce(lbm_handle fine, int fine_face, lbm_handle coarse, int coarse_face);
 
-/* Fills p with the defaults listed above. */
+/* Fills p with the defaults listed above.  The parameter block holds the free parameters that
+ * Sec. 3 passes to every generated kernel beside its raw pointers and shapes. */
 void lbm_params_default(lbm_params* p);
 
-/* Host-only: the library's velocity set.  c: q*3 ints, w: q doubles (either may be NULL).
- * Returns q, or 0 if q is not 19 or 27. */
+/* Host-only: the library's velocity set, the c_i of Eq. LBStreaming (Sec. 2): D3Q19, the
+ * stencil of Sec. 4 and 5.2, or D3Q27 (the 27-velocity extension; the paper names only D3Q19).
+ * c: q*3 ints, w: q doubles (either may be NULL).  Returns q, or 0 if q is not 19 or 27. */
 int lbm_stencil(int q, int* c, double* w);
 
 /* Creates a lattice of nx*ny*nz cells (all fluid, populations at rest equilibrium rho = 1)
  * with stencil 19 or 27 and molecular relaxation time tau (> 1/2; nu = (tau - 1/2)/3).
- * p may be NULL for the defaults.  Sec. 2 (problem statement).  Errors: EINVAL for bad
- * sizes, stencil, tau, Lambda or face combination (periodic faces come in pairs); ENOMEM;
- * EUNSUPPORTED for an outflow face the kernels cannot serve. */
+ * p may be NULL for the defaults.  Sec. 2 (the lattice Boltzmann equation on a lattice of
+ * cells) and Sec. 3 (a kernel takes raw pointers, shapes and free parameters).  Errors: EINVAL
+ * for bad sizes, stencil, tau, Lambda, face combination (periodic faces come in pairs) or an
+ * unknown enum value; ENOMEM; EUNSUPPORTED for an outflow face the kernels cannot serve, a
+ * collision/closure/stencil combination that is not built, or a pipeline other than DIRECT.
+ * *out is NULL on every error. */
 lbm_status lbm_create(int nx, int ny, int nz, int stencil, double tau, const lbm_params* p,
                       lbm_handle* out);
 
-/* Frees all device memory of h (after its stream's work).  NULL is accepted. */
+/* Frees all device memory of h (after its stream's work).  NULL is accepted.  Memory
+ * management only: the paper has no counterpart. */
 lbm_status lbm_destroy(lbm_handle h);
 
 /* Cell flags, nx*ny*nz uint8 (LBM_CELL_*), x fastest; on_device != 0 if flags is a device
- * pointer.  Other values give EINVAL.  Cells that become fluid keep whatever populations
+ * pointer.  The geometry that the boundary kernels of Sec. 3 act on: solid cells (halfway
+ * bounce-back) and the moving-wall cells of an inflow (Sec. 5.2, the wind tunnel's inflow);
+ * the boundary rules are precomputed here, once per call.  Other values give EINVAL.  Cells that become fluid keep whatever populations
  * they held; call lbm_init_equilibrium or lbm_set_populations afterwards.  With a
  * LBM_FACE_HALO z face the array holds nz + 2 planes, z = -1 .. nz: the ghost planes carry
  * the flags of the neighbouring slabs' cells (so bounce-back against a solid cell across the
  * face is resolved here). */
 lbm_status lbm_set_flags(lbm_handle h, const uint8_t* flags, int on_device);
 
-/* Constant body-force density F (lattice units), used by every later step. */
+/* Constant body-force density F (lattice units), used by every later step: the pressure
+ * gradient that drives the turbulent channel of Sec. 5.1, entering the collision of Eq.
+ * LBCollision as Guo's forcing term. */
 lbm_status lbm_set_force(lbm_handle h, double fx, double fy, double fz);
 
-/* Sets every fluid cell to f_i^eq(rho, u) (second-order equilibrium).  rho: N floats or
- * NULL (rho = 1); u: 3*N floats [3][nz][ny][nx] or NULL (u = 0).  The reported velocity of
- * the new state is u + F/(2 rho).  Clears the instability flag. */
+/* Sets every fluid cell to f_i^eq(rho, u) (second-order equilibrium, the f^eq of Eq.
+ * LBCollision, Sec. 2).  rho: N floats or NULL (rho = 1); u: 3*N floats [3][nz][ny][nx] or
+ * NULL (u = 0).  The reported velocity of the new state is u + F/(2 rho).  Clears the status
+ * word (instability, closure wait).  Host arrays: see "Ownership" above. */
 lbm_status lbm_init_equilibrium(lbm_handle h, const float* rho, const float* u, int on_device);
 
-/* Advances n >= 0 time steps (collision then streaming, Sec. 2).  Asynchronous: returns
+/* Advances n >= 0 time steps: Eq. LBCollision then Eq. LBStreaming (Sec. 2) with the boundary
+ * rules, fused into one sweep over the lattice per step (the stream-collide kernel of Sec. 3
+ * and 5.2, bounded by memory bandwidth).  Asynchronous: returns
  * after enqueuing; instability is reported by lbm_sync.  Once the state is steady, several
  * steps go into one launch: on small lattices (up to 2^17 padded cells for two-grid pull,
  * 2^15 for AA) cooperative launches of up to 4096 steps separated by grid-wide barriers,
- * above that replays of a CUDA graph of 8 steps; the result has the bits of n single steps. */
+ * above that replays of a CUDA graph of 8 steps; the result has the bits of n single steps.
+ * LBM_ECUDA on a handle that lbm_sync has declared unusable. */
 lbm_status lbm_step(lbm_handle h, int64_t n);
 
-/* Waits for the handle's stream.  LBM_EUNSTABLE if any step since the last state reset saw a
- * non-finite or non-positive density; LBM_ECUDA if a pipelined step gave up waiting for its
- * staged loads (a bounded wait that should never expire), or, in a library built with
- * LBM_BOUNDS_CHECK (liblbm_check.so), if a kernel skipped an access outside its array. */
+/* Waits for the handle's stream and reports what the steps since the last state reset saw
+ * (failure detection; the paper has no counterpart).  LBM_EUNSTABLE: a non-finite or
+ * non-positive density (the state is kept for inspection).  LBM_ECUDA: a learned-closure step
+ * gave up its bounded wait for a tile's tensor-core result (an event that should not occur;
+ * the step stopped early and the state is incomplete, but the device is usable once the
+ * state is set again); or that step's second, draining wait gave up as well, after which the
+ * tensor-core work may still have been running when the kernel left: the handle is then marked
+ * unusable and every later step returns LBM_ECUDA; or, in a library built with
+ * LBM_BOUNDS_CHECK (liblbm_check.so), a kernel skipped an access outside its array. */
 lbm_status lbm_sync(lbm_handle h);
 
-/* Moments of the current state: rho (N floats) and u (3*N floats, includes +F/(2 rho)).
- * Either pointer may be NULL.  Non-fluid cells report 0. */
+/* Diagnostic: the number of polls (each a try-wait that may suspend the thread) the learned-
+ * closure step makes in its first wait for each tile's tensor-core result before it gives up;
+ * default 2^22 (far longer than any MMA takes), polls = -1 restores it, 0 makes every first
+ * wait give up at once, which drives the timeout path of lbm_sync without a device fault
+ * (the step still waits, with the full bound, for the tensor core to finish before its
+ * kernel leaves).  EINVAL outside [-1, 2^22].  Failure detection; the paper has no
+ * counterpart. */
+lbm_status lbm_debug_set_wait_polls(lbm_handle h, int64_t polls);
+
+/* Moments of the current state: rho (N floats) and u (3*N floats, includes +F/(2 rho)), the
+ * local fluid properties on which f^eq of Eq. LBCollision depends (Sec. 2).  Either pointer
+ * may be NULL.  Non-fluid cells report 0.  Host arrays: synchronises before returning. */
 lbm_status lbm_moments(lbm_handle h, float* rho, float* u, int on_device);
 
-/* Current populations as shifted float32 df_i = f_i - w_i, [q][nz][ny][nx]; 0 on non-fluid
- * cells.  Exact for F32 storage; exact widening for F16/BF16 storage. */
+/* Current populations (the PDFs f_i of Sec. 2) as shifted float32 df_i = f_i - w_i,
+ * [q][nz][ny][nx]; 0 on non-fluid cells.  Exact for F32 storage; exact widening for F16/BF16
+ * storage.  For checkpoints and parity checks. */
 lbm_status lbm_get_populations(lbm_handle h, float* df, int on_device);
 
-/* The stored post-collision populations f*_i(x, t) of the last step of a two-grid pull
- * lattice (natural slots, not streamed), as shifted float32 [q][nz][ny][nx]; 0 on non-fluid
- * cells.  LBM_ESTATE for an AA lattice or before the first step after an import. */
+/* The stored post-collision populations f*_i(x, t) (Eq. LBCollision, Sec. 2) of the last step
+ * of a two-grid pull lattice (natural slots, not streamed), as shifted float32
+ * [q][nz][ny][nx]; 0 on non-fluid cells.  The values the refinement transfers move between
+ * levels.  LBM_ESTATE for an AA lattice or before the first step after an import. */
 lbm_status lbm_get_post_collision(lbm_handle h, float* df, int on_device);
 
-/* Replaces the state by the given shifted populations (rounded to the storage precision
- * with round-to-nearest-even).  Clears the instability flag. */
+/* Replaces the state by the given shifted populations (the PDFs f_i of Sec. 2, rounded to the
+ * storage precision with round-to-nearest-even); restarts from a checkpoint.  Clears the
+ * status word. */
 lbm_status lbm_set_populations(lbm_handle h, const float* df, int on_device);
 
-/* FP64 sums over fluid cells: out[0] = sum rho, out[1..3] = sum rho u.  Synchronises. */
+/* FP64 sums over fluid cells: out[0] = sum rho, out[1..3] = sum rho u.  Synchronises.  Mass
+ * conservation is what the channel of Sec. 5.1 assesses first. */
 lbm_status lbm_reduce(lbm_handle h, double out[4]);
 
 /* Turbulence statistics in FP64, per y plane (LBM_STATS_K values each, see above):
  * reset, add one sample of the current state, read ny*LBM_STATS_K doubles (host).  What the
- * channel assesses (Sec. 4.1): mean and fluctuation profiles over the homogeneous x-z planes.
- * Per-cell values are float32 (the moments of lbm_moments); sums are FP64. */
+ * turbulent channel of Sec. 5.1 assesses: the symmetry and regularity of the solution and the
+ * shear stresses along the wall normal, i.e. mean and fluctuation profiles over the
+ * homogeneous x-z planes.  Per-cell values are float32 (the moments of lbm_moments); sums are
+ * FP64. */
 lbm_status lbm_stats_reset(lbm_handle h);
 lbm_status lbm_stats_sample(lbm_handle h);
 lbm_status lbm_stats_get(lbm_handle h, double* out, int64_t* nsamples);
 
-/* Advances n >= 0 steps like lbm_step and adds one statistics sample of the state that each
+/* Advances n >= 0 steps like lbm_step (Sec. 2 equations) and adds one statistics sample (the
+ * channel profiles of Sec. 5.1) of the state that each
  * step k = 0, every, 2 every, ... (k counted from this call, every >= 1) starts from, i.e.
- * ceil(n / every) samples.  With the direct pipeline and no learned closure the sample is
+ * ceil(n / every) samples.  Without the learned closure the sample is
  * taken by that step's own kernel (per-warp float32 sums of 32 or 64 cells, then FP64 plane
- * sums), so sampling adds no pass over the populations; otherwise a separate pass runs
- * before the step.  Per-warp partial sums live in a scratch array allocated on the first
+ * sums), so sampling adds no pass over the populations; with the learned closure a separate
+ * pass runs before the step.  Per-warp partial sums live in a scratch array allocated on the first
  * call (10 floats per warp slot, about 1.25 bytes per cell).  EINVAL for n < 0 or every < 1. */
 lbm_status lbm_step_stats(lbm_handle h, int64_t n, int64_t every);
 
 /* MLP closure parameters (host, bfloat16 bit patterns, n == LBM_MLP_NPARAM) and feature
- * scales.  Needed before stepping with closure LBM_CLOSURE_MLP. */
+ * scales.  Needed before stepping with closure LBM_CLOSURE_MLP.  The learned closure has no
+ * counterpart in the paper (whose LES closures, Sec. 4, are fixed models): a per-cell network
+ * gives the Smagorinsky coefficient inside the collision of Eq. LBCollision. */
 lbm_status lbm_set_closure(lbm_handle h, const uint16_t* bf16_params, int n, double scale_pi,
                            double scale_rho);
 
 /* As lbm_set_closure, from float32 parameters (host or device), rounded to bfloat16 with
- * round-to-nearest-even. */
+ * round-to-nearest-even.  No counterpart in the paper (learned closure). */
 lbm_status lbm_set_closure_f32(lbm_handle h, const float* params, int on_device, double scale_pi,
                                double scale_rho);
 
 /* Lower bound on the learned coefficient: C_s^2(x) = max(network value, cs_min^2) (default
- * cs_min = 0, no bound).  A safeguard for coarse runs near tau = 1/2, where a learned eddy
+ * cs_min = 0, no bound).  No counterpart in the paper (learned closure).  A safeguard for coarse runs near tau = 1/2, where a learned eddy
  * viscosity below the Smagorinsky one can leave too little dissipation. */
 lbm_status lbm_set_closure_floor(lbm_handle h, double cs_min);
 
 /* ---- learned-closure training (all array arguments are caller-owned DEVICE pointers) ----
- * The closure's network is trained on pairs the solver generates: a fine lattice is
+ * No counterpart in the paper: it compares LES closures (Sec. 4) but trains none.  The
+ * closure's network is trained on pairs the solver generates: a fine lattice is
  * box-filtered (width 2) onto the coarse grid.  Per coarse cell (8 fine cells) the fine
  * solver's density, momentum, rho u u, strain rate S_f = -3 Pi^neq / (2 rho tau_eff) and
  * Smagorinsky stress -2 nu_t S_f are averaged; the unresolved stress is
@@ -318,32 +355,37 @@ lbm_status lbm_set_closure_floor(lbm_handle h, double cs_min);
 lbm_status lbm_closure_samples(lbm_handle fine, double tau0_c, double cs0, const double scale[2],
                                float* x, float* target, float* smag, float* weight);
 
-/* Box filter of width 2 of the fine state (device outputs, nc coarse cells as above):
+/* Box filter of width 2 of the fine state (device outputs, nc coarse cells as above); the
+ * coarse-from-fine averaging of a 2:1 grid transition (Sec. 3, Fig. 2), here for the
+ * closure's reference fields:
  * rho_bar = mean density of the 8 fine cells, u_bar = <rho u> / <rho> (Favre, [3][nc]).
  * Needs even sizes and no outflow face.  Asynchronous on the fine handle's stream. */
 lbm_status lbm_filter2(lbm_handle fine, float* rho_bar, float* u_bar);
 
-/* Network output y for n samples x[n][7] (parameters: LBM_MLP_NPARAM floats). */
+/* Network output y for n samples x[n][7] (parameters: LBM_MLP_NPARAM floats).  No counterpart
+ * in the paper (learned closure). */
 lbm_status lbm_mlp_forward(const float* params, const float* x, int64_t n, float* y, void* stream);
 
-/* grad = sum_s dy[s] d y_s / d params (overwritten). */
+/* grad = sum_s dy[s] d y_s / d params (overwritten).  No counterpart in the paper. */
 lbm_status lbm_mlp_backward(const float* params, const float* x, const float* dy, int64_t n,
                             float* grad, void* stream);
 
 /* Weighted mean-square error of the predicted eddy viscosity over the batch of samples
  * offset + s * stride (s < n):  nu = softplus(y) cs0^2/ln 2 * smag,
  * L = sum w (nu - target)^2 / sum w.  grad (overwritten) = dL/dparams; *loss (host or
- * device double) = L.  Synchronises the stream. */
+ * device double) = L.  Synchronises the stream.  No counterpart in the paper. */
 lbm_status lbm_closure_loss_grad(const float* params, const float* x, const float* target,
                                  const float* smag, const float* weight, int64_t n, int64_t offset,
                                  int64_t stride, double cs0, float* grad, double* loss, void* stream);
 
-/* One Adam step (Kingma and Ba) on n parameters; t is the 1-based step count. */
+/* One Adam step (Kingma and Ba 2015) on n parameters; t is the 1-based step count.  No
+ * counterpart in the paper. */
 lbm_status lbm_adam_step(float* params, const float* grad, float* m, float* v, int n, double lr,
                          double beta1, double beta2, double eps, int64_t t, void* stream);
 
 /* Sizes of the handle: padded row length nxp, bytes of one stored population, algorithmic
- * bytes moved per lattice update of the stepping kernel (2 q s + 1 flag byte). */
+ * bytes moved per lattice update of the stepping kernel (2 q s + 1 class byte): the n_b of
+ * Eq. roofline (Sec. 5.2, 304 bytes for D3Q19 in double precision there). */
 lbm_status lbm_info(lbm_handle h, int* nxp, int* bytes_per_pop, double* bytes_per_update);
 
 /* lbm_reduce_noalloc: the sums of lbm_reduce (out[0] = sum rho, out[1..3] = sum rho u over
@@ -357,20 +399,22 @@ lbm_status lbm_info(lbm_handle h, int* nxp, int* bytes_per_pop, double* bytes_pe
  *   flags   device pointer to nx*ny*nz uint8 cell flags, or NULL for all fluid.
  *   force   body-force density (3 doubles, host) used for rho u = sum c f + F/2, or NULL.
  *   out     4 doubles, host or device memory; written before the call returns.
- *   stream  cudaStream_t the work is ordered on (NULL = legacy default stream); the call
- *           synchronises it before returning.
+ *   stream  cudaStream_t the work is ordered on (NULL = legacy default stream).  Every call
+ *           synchronises this stream before it returns, so out holds the sums on return.
  * Scratch: a static device array of LBM_NOALLOC_MAX_PARTIALS * 4 + 4 doubles (512 KiB) that
  * every GPU loading the library keeps until exit.  Lattices of more than
  * LBM_NOALLOC_MAX_PARTIALS * 16384 cells (2^28) are rejected with LBM_EINVAL and a message in
  * lbm_last_error(NULL).  The first call on a device (with that device current) looks up the
  * array's device address; make that first call before any stream capture.  All calls share
  * the array, so calls whose GPU work overlaps race with each other.  No cudaMalloc, cudaFree
- * or allocating library call is made. */
+ * or allocating library call is made.  The caller must pass arrays of the stated sizes: the
+ * call can only trust the pointers (the Python binding checks sizes and devices). */
 #define LBM_NOALLOC_MAX_PARTIALS 16384
 lbm_status lbm_reduce_noalloc(const float* df, const uint8_t* flags, int nx, int ny, int nz,
                               int stencil, const double force[3], double out[4], void* stream);
 
-/* Message for the last failing call on h (or on creation when h is NULL). */
+/* Message for the last failing call on h (or on creation, and on calls without a handle, when
+ * h is NULL).  Error reporting; the paper has no counterpart. */
 const char* lbm_last_error(lbm_handle h);
 
 #ifdef __cplusplus

@@ -219,21 +219,25 @@ def split(samples, frac):
 
 
 def experiment(nx, ny, nz, re_tau=180.0, u_bulk=0.05, spin=60000, nsnap=20, every=500, epochs=6,
-               coarse_steps=20000, cs0=0.1, cs_min=0.1, seed=0, log=None, amp=0.1):
+               coarse_steps=20000, cs0=0.1, cs_min=0.1, seed=0, log=None, amp=0.1, flow_seed=None):
     """The learned-closure experiment on a fine channel of nx x ny x nz cells.
 
     1. spin the fine Smagorinsky channel up; 2. collect nsnap box-filtered sample sets;
     3. train on the first 3/4 (earlier snapshots), score on the last 1/4 against Smagorinsky
     (the zero output layer); 4. from the filtered final fine state, run the coarse channel
     with Smagorinsky and with the learned closure (bounded below by cs_min) and compare
-    their mean and RMS velocity profiles with the filtered fine run over the same time."""
+    their mean and RMS velocity profiles with the filtered fine run over the same time.
+    `seed` seeds the network's initial weights and the minibatch order, `flow_seed` (default
+    the inputs' default seed) the perturbations of the initial channel state."""
     import torch
 
     t0 = time.time()
     rep = {"fine": [nx, ny, nz], "coarse": [nx // 2, ny // 2, nz // 2], "re_tau": re_tau,
            "u_bulk": u_bulk, "spin_steps": spin, "snapshots": nsnap, "every": every,
            "epochs": epochs, "coarse_steps": coarse_steps, "cs0": cs0, "cs_min": cs_min}
-    fine = channel(nx, ny, nz, closure="smag", cs0=cs0, re_tau=re_tau, u_bulk=u_bulk, amp=amp)
+    flow_seed = inputs.DEFAULT_SEED if flow_seed is None else flow_seed
+    rep["flow_seed"] = flow_seed
+    fine = channel(nx, ny, nz, closure="smag", cs0=cs0, re_tau=re_tau, u_bulk=u_bulk, amp=amp, seed=flow_seed)
     fine.step(spin)
     fine.sync()
     lbm.lbm_stats_reset(fine.h)

@@ -110,60 +110,6 @@ cudaError_t launch_step_multi(const KParams& p0, const KParams& p1, int closure,
             : multi_coll<Q, S, false>(pp, closure, coll, nsteps, odd0, stream, nsm);
 }
 
-#ifndef LBM_ASYNC_ZC
-#define LBM_ASYNC_ZC 8
-#endif
-#ifndef LBM_ASYNC_NST
-#define LBM_ASYNC_NST 2
-#endif
-
-template <int Q, int CL, int LOAD, int STORE>
-static cudaError_t async_one(const KParams& p, const Launch& L0) {
-  constexpr int ZC = LBM_ASYNC_ZC, NST = LBM_ASYNC_NST;
-  constexpr int smem = NST * Q * 128 * (int)sizeof(float);
-  static_assert(smem <= 48 * 1024, "stage buffers above the default dynamic shared memory limit");
-  Launch L = L0;
-  L.grid.z = (p.nz + ZC - 1) / ZC;
-  k_step_async<Q, CL, LOAD, STORE, ZC, NST><<<L.grid, L.block, smem, L.stream>>>(p);
-  return cudaGetLastError();
-}
-
-template <int Q, int LOAD, int STORE>
-static cudaError_t async_mode(const KParams& p, int closure, const Launch& L) {
-  if (closure == CL_NONE) return async_one<Q, CL_NONE, LOAD, STORE>(p, L);
-  return async_one<Q, CL_SMAG, LOAD, STORE>(p, L);
-}
-
-// Staged (cp.async) step; FP32 storage only, the half forms take the direct kernels.
-template <int Q, class S>
-cudaError_t launch_step_async(const KParams& p, int closure, int mode, const Launch& L) {
-  if constexpr (!std::is_same<S, float>::value) {
-    return launch_step<Q, S>(p, closure, mode, L, false, nullptr, 0);
-  } else {
-    switch (mode) {
-      case 0: return async_mode<Q, 0, 0>(p, closure, L);
-      case 1: return async_mode<Q, 1, 1>(p, closure, L);
-      case 2: return async_mode<Q, 0, 2>(p, closure, L);
-      default: return async_mode<Q, 2, 2>(p, closure, L);
-    }
-  }
-}
-
-template <int Q, class S>
-cudaError_t launch_step_zp(const KParams& p, int closure, int parity, const Launch& L0) {
-  constexpr int ZC = 4;
-  Launch L = L0;
-  L.grid.z = (p.nz + ZC - 1) / ZC;
-  if (parity == 0) {
-    if (closure == CL_NONE) k_step_zp<Q, S, CL_NONE, 0, ZC><<<L.grid, L.block, 0, L.stream>>>(p);
-    else k_step_zp<Q, S, CL_SMAG, 0, ZC><<<L.grid, L.block, 0, L.stream>>>(p);
-  } else {
-    if (closure == CL_NONE) k_step_zp<Q, S, CL_NONE, 1, ZC><<<L.grid, L.block, 0, L.stream>>>(p);
-    else k_step_zp<Q, S, CL_SMAG, 1, ZC><<<L.grid, L.block, 0, L.stream>>>(p);
-  }
-  return cudaGetLastError();
-}
-
 template <int Q, class S, int LOAD, int STORE>
 static cudaError_t mlp_one(const KParams& p, cudaStream_t stream, int nsm) {
   constexpr int smem = (int)sizeof(MlpSmem);
@@ -192,35 +138,6 @@ cudaError_t launch_step_mlp(const KParams& p, int mode, cudaStream_t stream, int
     case 2: return mlp_one<Q, S, 0, 2>(p, stream, nsm);
     default: return mlp_one<Q, S, 2, 2>(p, stream, nsm);
   }
-}
-
-template <int Q, class S, int CL, int PAR>
-static cudaError_t tma_one(const KParams& p, cudaStream_t stream, int nsm) {
-  constexpr int smem = TmaGeom<S>::template smem_bytes<Q, PAR>();
-  auto kern = k_step_tma<Q, S, CL, PAR>;
-  static int blocks_per_sm = 0;  // per instantiation, found once
-  if (blocks_per_sm == 0) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, TMA_TX, smem);
-    if (e != cudaSuccess) return e;
-    if (blocks_per_sm < 1) blocks_per_sm = 1;
-  }
-  const int nseg = (p.nxp + TMA_TX - 1) / TMA_TX;
-  const long long ntiles = (long long)nseg * p.ny * p.nz;
-  const long long grid = std::min<long long>(ntiles, (long long)nsm * blocks_per_sm);
-  kern<<<(unsigned)grid, TMA_TX, smem, stream>>>(p, ntiles);
-  return cudaGetLastError();
-}
-
-template <int Q, class S>
-cudaError_t launch_step_tma(const KParams& p, int closure, int parity, cudaStream_t stream, int nsm) {
-  if (parity == 0) {
-    if (closure == CL_NONE) return tma_one<Q, S, CL_NONE, 0>(p, stream, nsm);
-    return tma_one<Q, S, CL_SMAG, 0>(p, stream, nsm);
-  }
-  if (closure == CL_NONE) return tma_one<Q, S, CL_NONE, 1>(p, stream, nsm);
-  return tma_one<Q, S, CL_SMAG, 1>(p, stream, nsm);
 }
 
 template <int Q, class S, int PAR>
@@ -261,9 +178,6 @@ cudaError_t launch_set_pop(const KParams& p, const float* df, const Launch& L) {
 }
 
 template cudaError_t launch_step<LBM_Q, LBM_S>(const KParams&, int, int, const Launch&, bool, int*, int);
-template cudaError_t launch_step_tma<LBM_Q, LBM_S>(const KParams&, int, int, cudaStream_t, int);
-template cudaError_t launch_step_zp<LBM_Q, LBM_S>(const KParams&, int, int, const Launch&);
-template cudaError_t launch_step_async<LBM_Q, LBM_S>(const KParams&, int, int, const Launch&);
 template cudaError_t launch_step_mlp<LBM_Q, LBM_S>(const KParams&, int, cudaStream_t, int);
 template cudaError_t launch_export<LBM_Q, LBM_S>(const KParams&, int, int, const ExportArgs&, const Launch&);
 template cudaError_t launch_init_eq<LBM_Q, LBM_S>(const KParams&, const float*, const float*, const Launch&);

@@ -56,6 +56,8 @@ struct lbm_s {
   int nat_valid = 1;          // natural layout came from an import (outflow slots hold values)
   int prev_post = 0;          // pull: the other array holds the post-collision state before the current one
   int nsm = 0;                // multiprocessors of the device (persistent grid size)
+  int wait_polls = MBAR_POLLS; // polls of the closure step's first wait for each tile's MMA
+  bool broken = false;        // a device wait gave up twice: results and device state undefined
   std::string err;
 };
 
@@ -142,6 +144,7 @@ static KParams kparams(const lbm_s* h) {
   }
   p.mlp = h->mlp;
   p.status = h->status;
+  p.wait_polls = h->wait_polls;
   p.plane = plane_of(h);
   p.nx = h->nx;
   p.ny = h->ny;
@@ -174,81 +177,28 @@ static KParams kparams(const lbm_s* h) {
   return p;
 }
 
-// True when the step kernel of this handle can sample the statistics itself (direct loads,
-// no learned closure); the other forms sample them in a separate pass before the step.
-static bool fused_stats(const lbm_s* h) {
-  return (h->prm.pipeline == LBM_PIPE_DIRECT || h->prm.collision != LBM_COLL_TRT) &&
-         h->prm.closure != LBM_CLOSURE_MLP;
-}
+// True when the step kernel of this handle samples the statistics itself (every form but the
+// learned closure, which samples them in a separate pass before the step).
+static bool fused_stats(const lbm_s* h) { return h->prm.closure != LBM_CLOSURE_MLP; }
 
 template <int Q>
 static cudaError_t dispatch_step(const lbm_s* h, const KParams& p, int closure, int parity, bool stats = false,
                                  int* nws = nullptr) {
-  const Launch L = launch_cfg(h);
-  if (h->prm.collision != LBM_COLL_TRT) {  // one kernel for every pipeline: the direct MRT / regularised step
-    const int mode = h->prm.streaming == LBM_PULL ? (parity == 0 ? 2 : 3) : parity;
-    const int coll = h->prm.collision;
-    switch (h->prm.precision) {
-      case LBM_F32: return launch_step<Q, float>(p, closure, mode, L, stats, nws, coll);
-      case LBM_F16_SHIFTED: return launch_step<Q, __half>(p, closure, mode, L, stats, nws, coll);
-      default: return launch_step<Q, __nv_bfloat16>(p, closure, mode, L, stats, nws, coll);
-    }
-  }
-  if (closure == CL_MLP) {  // one kernel for every pipeline: the tensor-core closure step
-    const int mode = h->prm.streaming == LBM_PULL ? (parity == 0 ? 2 : 3) : parity;
+  // mode of the step kernels: 0 AA even, 1 AA odd, 2 first pull step after an import, 3 pull
+  const int mode = h->prm.streaming == LBM_PULL ? (parity == 0 ? 2 : 3) : parity;
+  if (closure == CL_MLP) {  // the tensor-core closure step
     switch (h->prm.precision) {
       case LBM_F32: return launch_step_mlp<Q, float>(p, mode, h->stream, h->nsm);
       case LBM_F16_SHIFTED: return launch_step_mlp<Q, __half>(p, mode, h->stream, h->nsm);
       default: return launch_step_mlp<Q, __nv_bfloat16>(p, mode, h->stream, h->nsm);
     }
   }
-  if (h->prm.streaming == LBM_PULL) {  // direct or staged loads
-    const int mode = parity == 0 ? 2 : 3;
-    if (stats) {
-      switch (h->prm.precision) {
-        case LBM_F32: return launch_step<Q, float>(p, closure, mode, L, true, nws);
-        case LBM_F16_SHIFTED: return launch_step<Q, __half>(p, closure, mode, L, true, nws);
-        default: return launch_step<Q, __nv_bfloat16>(p, closure, mode, L, true, nws);
-      }
-    }
-    if (h->prm.pipeline == LBM_PIPE_ASYNC) {
-      switch (h->prm.precision) {
-        case LBM_F32: return launch_step_async<Q, float>(p, closure, mode, L);
-        case LBM_F16_SHIFTED: return launch_step_async<Q, __half>(p, closure, mode, L);
-        default: return launch_step_async<Q, __nv_bfloat16>(p, closure, mode, L);
-      }
-    }
-    switch (h->prm.precision) {
-      case LBM_F32: return launch_step<Q, float>(p, closure, mode, L, false, nullptr);
-      case LBM_F16_SHIFTED: return launch_step<Q, __half>(p, closure, mode, L, false, nullptr);
-      default: return launch_step<Q, __nv_bfloat16>(p, closure, mode, L, false, nullptr);
-    }
-  }
-  if (h->prm.pipeline == LBM_PIPE_ASYNC) {
-    switch (h->prm.precision) {
-      case LBM_F32: return launch_step_async<Q, float>(p, closure, parity, L);
-      case LBM_F16_SHIFTED: return launch_step_async<Q, __half>(p, closure, parity, L);
-      default: return launch_step_async<Q, __nv_bfloat16>(p, closure, parity, L);
-    }
-  }
-  if (h->prm.pipeline == LBM_PIPE_PREFETCH) {
-    switch (h->prm.precision) {
-      case LBM_F32: return launch_step_zp<Q, float>(p, closure, parity, L);
-      case LBM_F16_SHIFTED: return launch_step_zp<Q, __half>(p, closure, parity, L);
-      default: return launch_step_zp<Q, __nv_bfloat16>(p, closure, parity, L);
-    }
-  }
-  if (h->prm.pipeline == LBM_PIPE_TMA) {
-    switch (h->prm.precision) {
-      case LBM_F32: return launch_step_tma<Q, float>(p, closure, parity, h->stream, h->nsm);
-      case LBM_F16_SHIFTED: return launch_step_tma<Q, __half>(p, closure, parity, h->stream, h->nsm);
-      default: return launch_step_tma<Q, __nv_bfloat16>(p, closure, parity, h->stream, h->nsm);
-    }
-  }
+  const Launch L = launch_cfg(h);
+  const int coll = h->prm.collision;
   switch (h->prm.precision) {
-    case LBM_F32: return launch_step<Q, float>(p, closure, parity, L, stats, nws);
-    case LBM_F16_SHIFTED: return launch_step<Q, __half>(p, closure, parity, L, stats, nws);
-    default: return launch_step<Q, __nv_bfloat16>(p, closure, parity, L, stats, nws);
+    case LBM_F32: return launch_step<Q, float>(p, closure, mode, L, stats, nws, coll);
+    case LBM_F16_SHIFTED: return launch_step<Q, __half>(p, closure, mode, L, stats, nws, coll);
+    default: return launch_step<Q, __nv_bfloat16>(p, closure, mode, L, stats, nws, coll);
   }
 }
 
@@ -513,6 +463,8 @@ lbm_status lbm_create(int nx, int ny, int nz, int stencil, double tau, const lbm
     return fail(nullptr, LBM_EINVAL, "unknown streaming %d", p.streaming);
   if (p.pipeline < LBM_PIPE_TMA || p.pipeline > LBM_PIPE_ASYNC)
     return fail(nullptr, LBM_EINVAL, "unknown pipeline %d", p.pipeline);
+  if (p.pipeline != LBM_PIPE_DIRECT)
+    return fail(nullptr, LBM_EUNSUPPORTED, "only the direct-load pipeline is built (pipeline %d)", p.pipeline);
   if (!(p.cs_smag >= 0.0)) return fail(nullptr, LBM_EINVAL, "cs_smag must be >= 0");
   if (p.collision != LBM_COLL_TRT && p.collision != LBM_COLL_MRT && p.collision != LBM_COLL_REG)
     return fail(nullptr, LBM_EINVAL, "unknown collision %d", p.collision);
@@ -760,8 +712,8 @@ static lbm_status run_steps(lbm_handle h, int64_t n, int64_t every) {
 // ---- CUDA graph of plain steps ---------------------------------------------------------------
 // Small lattices are launch-bound: lbm_step replays a graph of GRAPH_STEPS steps (an even
 // number, so the streaming state returns to where it started) when the state is steady (pull
-// after its first step; AA once the outflow import state is settled) and the kernels are the
-// direct ones.  The graph is captured on a private stream and re-captured whenever the kernel
+// after its first step; AA once the outflow import state is settled) and the closure is not
+// the learned one (its persistent tensor-core kernel is not captured).  The graph is captured on a private stream and re-captured whenever the kernel
 // parameters of its first step differ (force, closure, flags, parity, arrays); replays give
 // the bits of single launches.
 constexpr int GRAPH_STEPS = 8;
@@ -778,7 +730,7 @@ static void advance_state(lbm_handle h) {
 }
 
 static bool graph_ready(lbm_handle h) {
-  if (h->graphs_off || h->prm.pipeline != LBM_PIPE_DIRECT || h->prm.closure == LBM_CLOSURE_MLP) return false;
+  if (h->graphs_off || h->prm.closure == LBM_CLOSURE_MLP) return false;
   if (h->prm.streaming == LBM_PULL ? h->parity != 2 : (h->prm.face_bc[1] == LBM_FACE_OUTFLOW && h->nat_valid))
     return false;
   KParams p = kparams(h);
@@ -870,13 +822,17 @@ static int64_t run_multi(lbm_handle h, int64_t n) {
   return n;
 }
 
+static const char* const BROKEN_MSG =
+    "the handle is unusable: a learned-closure step gave up waiting for the tensor core twice";
+
 lbm_status lbm_step(lbm_handle h, int64_t n) {
   if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (h->broken) return fail(h, LBM_ECUDA, "%s", BROKEN_MSG);
   if (n < 0) return fail(h, LBM_EINVAL, "n must be >= 0");
   if (h->prm.closure == LBM_CLOSURE_MLP && !h->mlp_set)
     return fail(h, LBM_ESTATE, "MLP closure selected but lbm_set_closure was not called");
   const long long multi_max = h->prm.streaming == LBM_PULL ? LBM_MULTI_MAX_CELLS : LBM_MULTI_MAX_CELLS_AA;
-  if (n >= 2 && !h->multi_off && h->prm.pipeline == LBM_PIPE_DIRECT && h->prm.closure != LBM_CLOSURE_MLP &&
+  if (n >= 2 && !h->multi_off && h->prm.closure != LBM_CLOSURE_MLP &&
       (long long)h->nxp * h->ny * h->nz <= multi_max) {
     while (n > 0 && !steady_state(h)) {  // settle with single launches
       lbm_status s = run_steps(h, 1, 0);
@@ -888,7 +844,7 @@ lbm_status lbm_step(lbm_handle h, int64_t n) {
   // settle the state with single launches first (the first pull step, the AA outflow import)
   while (n > 0 && n >= 2 * GRAPH_STEPS && !graph_ready(h) && !h->graphs_off &&
          (h->prm.streaming == LBM_PULL ? h->parity != 2 : h->nat_valid != 0) &&
-         h->prm.pipeline == LBM_PIPE_DIRECT && h->prm.closure != LBM_CLOSURE_MLP) {
+         h->prm.closure != LBM_CLOSURE_MLP) {
     lbm_status s = run_steps(h, 1, 0);
     if (s != LBM_OK) return s;
     n--;
@@ -903,6 +859,7 @@ lbm_status lbm_step(lbm_handle h, int64_t n) {
 
 lbm_status lbm_step_stats(lbm_handle h, int64_t n, int64_t every) {
   if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (h->broken) return fail(h, LBM_ECUDA, "%s", BROKEN_MSG);
   if (n < 0) return fail(h, LBM_EINVAL, "n must be >= 0");
   if (every < 1) return fail(h, LBM_EINVAL, "every must be >= 1");
   return run_steps(h, n, every);
@@ -1103,8 +1060,13 @@ lbm_status lbm_sync(lbm_handle h) {
   if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
   CUDA_TRY(h, cudaMemcpyAsync(h->status_host, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  if (*h->status_host & 4) {
+    h->broken = true;
+    return fail(h, LBM_ECUDA, "%s", BROKEN_MSG);
+  }
   if (*h->status_host & 2)
-    return fail(h, LBM_ECUDA, "a pipelined step timed out waiting for its staged loads");
+    return fail(h, LBM_ECUDA,
+                "a learned-closure step gave up waiting for its tensor-core result; the state is incomplete");
 #ifdef LBM_BOUNDS_CHECK
   int bad = 0;
   CUDA_TRY(h, cudaMemcpy(&bad, h->chk_bad, sizeof(int), cudaMemcpyDeviceToHost));
@@ -1115,6 +1077,13 @@ lbm_status lbm_sync(lbm_handle h) {
 #endif
   if (*h->status_host & 1)
     return fail(h, LBM_EUNSTABLE, "a step produced a non-finite or non-positive density");
+  return LBM_OK;
+}
+
+lbm_status lbm_debug_set_wait_polls(lbm_handle h, int64_t polls) {
+  if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
+  if (polls < -1 || polls > MBAR_POLLS) return fail(h, LBM_EINVAL, "polls must lie in [-1, %d]", MBAR_POLLS);
+  h->wait_polls = polls < 0 ? MBAR_POLLS : (int)polls;
   return LBM_OK;
 }
 

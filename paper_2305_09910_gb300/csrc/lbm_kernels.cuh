@@ -84,7 +84,9 @@ struct KParams {
   // zero-gradient outflow copy, resolved from the geometry alone)
   const unsigned long long* rules;
   const float* mlp;      // MLP parameters (bf16 values widened to float), device
-  int* status;           // bit 0: non-finite or non-positive density seen
+  int* status;           // bit 0: non-finite or non-positive density seen; bits 1, 2: a
+                         // bounded wait of the learned-closure step gave up (once, twice)
+  int wait_polls;        // polls of the closure step's first wait for each tile's MMA
   float* stats_w;        // sampling steps: per-warp plane sums, [(z ny + y) nws + ws][10]
   long long plane;       // nxp * ny * nz
   int nx, ny, nz, nxp;
@@ -1182,45 +1184,6 @@ __global__ void __launch_bounds__(128, Q == 19 ? 8 : 6) k_step_multi(const __gri
       }
     }
     if (s + 1 < nsteps) grid.sync();
-  }
-}
-
-// The same step with register double-buffering along z: each thread updates ZC cells
-// (x, y, z0 .. z0+ZC-1) and loads the next cell's populations before colliding the current
-// one, so a warp keeps one cell's loads in flight through its arithmetic.  Consecutive
-// cells of a thread own disjoint slots in both AA launches, so the early load is safe.
-template <int Q, class S, int CL, int PAR, int ZC>
-__global__ void __launch_bounds__(128, 5) k_step_zp(const __grid_constant__ KParams p) {
-  const int x = blockIdx.x * 32 + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z0 = blockIdx.z * ZC;
-  if (y >= p.ny) return;  // whole warp
-  const int zend = min(p.nz, z0 + ZC);
-  float f[Q], g[Q];
-  unsigned outmask, outmask_g = 0;
-  int cell = cidx(p, x, y, z0);
-  int cls = x < p.nx ? cls_at(p, cell) : CLS_SKIP;
-  load_state<Q, S, PAR>(p, x, y, z0, cell, cls, f, outmask);
-#pragma unroll 1
-  for (int z = z0; z < zend; z++) {
-    const int zn = z + 1;
-    int celln = 0, clsn = CLS_SKIP;
-    if (zn < zend) {
-      celln = cidx(p, x, y, zn);
-      clsn = x < p.nx ? cls_at(p, celln) : CLS_SKIP;
-      load_state<Q, S, PAR>(p, x, y, zn, celln, clsn, g, outmask_g);
-    }
-    outflow_fix<Q>(p, x, f, outmask);
-    if (cls != CLS_SKIP) {
-      const float rho = collide<Q, CL, float, acc_form<S>>(p, f);
-      if (!(rho > 0.f && rho < 3.0e38f)) atomicOr(p.status, 1);
-      store_state<Q, S, PAR>(p, x, y, z, cell, cls, f);
-    }
-#pragma unroll
-    for (int i = 0; i < Q; i++) f[i] = g[i];
-    outmask = outmask_g;
-    cell = celln;
-    cls = clsn;
   }
 }
 

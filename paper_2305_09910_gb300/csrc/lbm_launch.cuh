@@ -3,8 +3,6 @@
 #pragma once
 
 #include "lbm_kernels.cuh"
-#include "lbm_tma.cuh"
-#include "lbm_async.cuh"
 #include "lbm_h2.cuh"
 #include "lbm_mlp.cuh"
 
@@ -19,13 +17,7 @@ template <int Q, class S>
 cudaError_t launch_step(const KParams& p, int closure, int parity, const Launch& L, bool stats = false,
                         int* nws = nullptr, int coll = 0);
 template <int Q, class S>
-cudaError_t launch_step_tma(const KParams& p, int closure, int parity, cudaStream_t stream, int nsm);
-template <int Q, class S>
 cudaError_t launch_step_mlp(const KParams& p, int mode, cudaStream_t stream, int nsm);
-template <int Q, class S>
-cudaError_t launch_step_async(const KParams& p, int closure, int mode, const Launch& L);
-template <int Q, class S>
-cudaError_t launch_step_zp(const KParams& p, int closure, int parity, const Launch& L);
 template <int Q, class S>
 cudaError_t launch_export(const KParams& p, int parity, int mode, const ExportArgs& a, const Launch& L);
 template <int Q, class S>
@@ -38,9 +30,6 @@ cudaError_t launch_step_multi(const KParams& p0, const KParams& p1, int closure,
 
 #define LBM_DECLARE_INSTANCE(Q, S)                                                                 \
   extern template cudaError_t launch_step<Q, S>(const KParams&, int, int, const Launch&, bool, int*, int); \
-  extern template cudaError_t launch_step_tma<Q, S>(const KParams&, int, int, cudaStream_t, int);  \
-  extern template cudaError_t launch_step_zp<Q, S>(const KParams&, int, int, const Launch&);       \
-  extern template cudaError_t launch_step_async<Q, S>(const KParams&, int, int, const Launch&);    \
   extern template cudaError_t launch_step_mlp<Q, S>(const KParams&, int, cudaStream_t, int);      \
   extern template cudaError_t launch_export<Q, S>(const KParams&, int, int, const ExportArgs&,     \
                                                   const Launch&);                                  \

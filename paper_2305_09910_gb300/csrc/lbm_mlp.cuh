@@ -20,8 +20,12 @@
 // tiles use the no-swizzle K-major layout of 8-row x 16-byte core matrices: element (r, k) of
 // a 4-byte-element tile at (r / 8) * 1024 + (k / 4) * 128 + (r % 8) * 16 + (k % 4) * 4, i.e.
 // leading-dimension byte offset 128 (K-adjacent core matrices), stride byte offset 1024
-// (8-row groups).  Every mbarrier wait is bounded; on a timeout the CTA sets status bit 1,
-// leaves its tile loop, frees its tensor memory and returns.
+// (8-row groups).  Every mbarrier wait is bounded.  When a group's first wait for a tile's MMA
+// gives up (after p.wait_polls polls), the group sets status bit 1, waits again with the full
+// bound so that the tensor core has finished with its accumulator and operand tile, and leaves
+// its tile loop; the CTA then frees its tensor memory and returns.  Should that second wait
+// give up too, status bit 2 records that the MMA may still be running: the launch's results
+// and the tensor memory it held are then undefined.
 #pragma once
 
 #include "lbm_kernels.cuh"
@@ -57,8 +61,11 @@ __device__ __forceinline__ void mbar_init1(uint32_t bar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait_parity(uint32_t bar, uint32_t parity) {
-  for (int it = 0; it < (1 << 22); it++) {
+// polls of a full mbarrier wait (each try_wait may itself suspend the thread for a while)
+constexpr int MBAR_POLLS = 1 << 22;
+
+__device__ __forceinline__ bool mbar_wait_parity(uint32_t bar, uint32_t parity, int polls) {
+  for (int it = 0; it < polls; it++) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -216,12 +223,15 @@ __global__ void __launch_bounds__(128 * MLP_NG, 1) k_step_mlp(const __grid_const
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
     }
-    const bool timed_out = !mbar_wait_parity(bar, phase);
-    phase ^= 1u;
+    const bool timed_out = !mbar_wait_parity(bar, phase, p.wait_polls);
     if (group_any(gbar, timed_out)) {
+      // give up on this launch, but only after the MMA has finished with the accumulator and
+      // the operand tile (the commit still arrives on the barrier)
       if (t == 0) atomicOr(p.status, 2);
+      if (!mbar_wait_parity(bar, phase, MBAR_POLLS)) atomicOr(p.status, 4);
       break;
     }
+    phase ^= 1u;
     tc_fence_after();
     // epilogue: this thread's 32 accumulator columns, bias, GELU, output layer (pairs)
     float2 acc = make_float2(0.f, 0.f);

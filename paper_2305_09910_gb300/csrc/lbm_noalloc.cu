@@ -14,6 +14,7 @@
 // with cudaGetSymbolAddress and caches it; that first call should come before any stream
 // capture.  Every call shares the array: calls whose work overlaps on the GPU race with each
 // other.  Each call overwrites every partial it reads, so nothing carries over between calls.
+// Every call synchronises its stream before it returns (the sums are in out by then).
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -34,6 +35,25 @@ constexpr long long kCellsPerBlock = (long long)kThreads * kCellsPerThread;  // 
 
 static __device__ __align__(256) double g_noalloc_scratch[(LBM_NOALLOC_MAX_PARTIALS + 1) * 4];
 
+#ifdef LBM_BOUNDS_CHECK
+// bounds-checked build: 1 + the array (0 populations, 1 flags) of the first access that fell
+// outside [pointer, pointer + the size the call declares); the access is skipped
+static __device__ int g_noalloc_bad;
+#endif
+
+// Whether the access of `bytes` bytes at a lies inside [lo, hi) (always, unless bounds-checked).
+__device__ __forceinline__ bool noalloc_chk(const void* a, int bytes, const void* lo, const void* hi, int which) {
+#ifdef LBM_BOUNDS_CHECK
+  const char* c = static_cast<const char*>(a);
+  const bool ok = c >= static_cast<const char*>(lo) && c + bytes <= static_cast<const char*>(hi);
+  if (!ok) atomicCAS(&g_noalloc_bad, 0, 1 + which);
+  return ok;
+#else
+  (void)a; (void)bytes; (void)lo; (void)hi; (void)which;
+  return true;
+#endif
+}
+
 // Per-block FP64 sums over a contiguous chunk of cells (fixed order within a thread, fixed
 // tree across threads: the result does not depend on scheduling).
 template <int Q>
@@ -43,15 +63,18 @@ __global__ void __launch_bounds__(kThreads) k_sum_partials(const float* __restri
                                                            double* partials) {
   using namespace lbm;
   const long long first = (long long)blockIdx.x * kCellsPerBlock;
+  const float* const df_end = df + (long long)Q * n;
+  const uint8_t* const fl_end = flags ? flags + n : nullptr;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int k = 0; k < kCellsPerThread; k++) {
     const long long c = first + (long long)k * kThreads + threadIdx.x;
     if (c >= n) break;
-    if (flags && flags[c] != CELL_FLUID) continue;
+    if (flags && (!noalloc_chk(flags + c, 1, flags, fl_end, 1) || flags[c] != CELL_FLUID)) continue;
     float d = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-      const float v = df[(long long)i * n + c];
+      const float* a = df + (long long)i * n + c;
+      const float v = noalloc_chk(a, 4, df, df_end, 0) ? *a : 0.f;
       d += v;
       if (cx(i)) jx += cx(i) > 0 ? v : -v;
       if (cy(i)) jy += cy(i) > 0 ? v : -v;
@@ -136,6 +159,15 @@ extern "C" lbm_status lbm_reduce_noalloc(const float* df, const uint8_t* flags, 
   double* partials = scratch;
   double* total = scratch + (long long)LBM_NOALLOC_MAX_PARTIALS * 4;
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
+#ifdef LBM_BOUNDS_CHECK
+  {
+    const int zero = 0;
+    if (cudaMemcpyToSymbolAsync(g_noalloc_bad, &zero, sizeof zero, 0, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      lbm_internal_set_error("lbm_reduce_noalloc: clearing the bounds-check word failed");
+      return LBM_ECUDA;
+    }
+  }
+#endif
   const float hf[3] = {force ? (float)(0.5 * force[0]) : 0.f, force ? (float)(0.5 * force[1]) : 0.f,
                        force ? (float)(0.5 * force[2]) : 0.f};
   if (stencil == 19)
@@ -155,5 +187,13 @@ extern "C" lbm_status lbm_reduce_noalloc(const float* df, const uint8_t* flags, 
     lbm_internal_set_error(msg);
     return LBM_ECUDA;
   }
+#ifdef LBM_BOUNDS_CHECK
+  int bad = 0;
+  if (cudaMemcpyFromSymbol(&bad, g_noalloc_bad, sizeof bad) != cudaSuccess || bad) {
+    lbm_internal_set_error(bad == 2 ? "lbm_reduce_noalloc: bounds check: an access outside the flags was skipped"
+                                    : "lbm_reduce_noalloc: bounds check: an access outside the populations was skipped");
+    return LBM_ECUDA;
+  }
+#endif
   return LBM_OK;
 }

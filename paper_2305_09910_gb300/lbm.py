@@ -87,6 +87,7 @@ def load():
             "lbm_init_equilibrium": (I, [H, P, P, I]),
             "lbm_step": (I, [H, ctypes.c_int64]),
             "lbm_sync": (I, [H]),
+            "lbm_debug_set_wait_polls": (I, [H, ctypes.c_int64]),
             "lbm_moments": (I, [H, P, P, I]),
             "lbm_get_populations": (I, [H, P, I]),
             "lbm_set_populations": (I, [H, P, I]),
@@ -238,6 +239,10 @@ def lbm_sync(h):
     _check(load().lbm_sync(h), h)
 
 
+def lbm_debug_set_wait_polls(h, polls: int):
+    _check(load().lbm_debug_set_wait_polls(h, int(polls)), h)
+
+
 def lbm_moments(h, rho=None, u=None):
     pr, dr = _buf(rho, np.float32, True)
     pu, du = _buf(u, np.float32, True)
@@ -338,11 +343,24 @@ def lbm_info(h):
 
 def lbm_reduce_noalloc(df, flags, nx, ny, nz, stencil, force=(0.0, 0.0, 0.0), stream=None):
     """FP64 sums of a caller-held population array without any allocation by the library
-    (out is a host array owned here).  df and flags must be CUDA tensors."""
+    (out is a host array owned here).  df (q*nx*ny*nz float32) and flags (nx*ny*nz uint8, or
+    None) must be CUDA tensors on the current device; sizes and devices are checked here,
+    since the C call can only trust the pointers it is given."""
+    import torch
+
     pd, dd = _buf(df, np.float32)
     pf, df_ = _buf(flags, np.uint8) if flags is not None else (None, 1)
     if not dd or not df_:
         raise ValueError("df and flags must be device buffers")
+    n = int(nx) * int(ny) * int(nz)
+    if n > 0 and df.numel() < int(stencil) * n:
+        raise ValueError(f"df holds {df.numel()} values, {int(stencil) * n} needed")
+    if flags is not None and n > 0 and flags.numel() < n:
+        raise ValueError(f"flags holds {flags.numel()} values, {n} needed")
+    dev = torch.cuda.current_device()
+    for name, t in (("df", df), ("flags", flags)):
+        if t is not None and t.device.index != dev:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{dev}")
     fv = np.ascontiguousarray(force, dtype=np.float64)
     out = np.zeros(4, dtype=np.float64)
     st = stream if stream is not None else _current_stream()

@@ -1,7 +1,7 @@
 """Tiny lattices through every step, export and exchange kernel with every boundary type:
 D3Q19/D3Q27, FP32/FP16/BF16, AA and two-grid pull, TRT/MRT/Smagorinsky/learned closure,
 statistics sampled in the step, moments, sums, population export/import, z slabs with halo
-exchange and graph replays.  Run against the bounds-checked library
+exchange, graph replays and the allocation-free sums.  Run against the bounds-checked library
 (``LBM_LIBRARY=.../liblbm_check.so python -m tests.sanitizer_cases``), every global access of
 these kernels is checked against its array and lbm_sync fails on any skipped access.  Not a
 pytest module (no test_ prefix): tests/test_gpu_bounds.py runs it."""
@@ -72,6 +72,18 @@ def run():
         digest.update(sl.get_populations().tobytes())
         sl.close()
         n += 1
+    # the allocation-free sums read the caller's exported populations and flags
+    import torch
+
+    lat = lbm.Lattice(nx, ny, nz, stencil=27, tau=0.6, closure="smag", faces=TUNNEL, u_inflow=(0.04, 0, 0))
+    lat.set_flags(flags)
+    lat.init_equilibrium(rho, u)
+    lat.step(3)
+    df = torch.from_numpy(lat.get_populations()).cuda()
+    sums = lbm.lbm_reduce_noalloc(df, torch.from_numpy(flags).cuda(), nx, ny, nz, 27)
+    digest.update(np.asarray(sums).tobytes())
+    lat.close()
+    n += 1
     print(f"cases: {n} lattices stepped, populations sha256 {digest.hexdigest()}", flush=True)
 
 

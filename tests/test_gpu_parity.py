@@ -146,6 +146,67 @@ def test_poiseuille_1000_steps_matches_oracle():
     assert np.abs(ux - ux[:1, :, :1]).max() <= 1e-9
 
 
+def _steady_channel(q, ny, tau, g, steps):
+    """Quasi-1D force-driven channel (nx = nz = 1, solid rows y = 0 and ny - 1) from rest to
+    `steps` steps on the GPU and on the oracle: (u_x GPU, u_x oracle) over the fluid rows."""
+    import oracle
+    from paper_2305_09910_gb300 import lbm
+
+    flags = np.zeros((1, ny, 1), np.uint8)
+    flags[0, 0, 0] = flags[0, ny - 1, 0] = 1
+    lat = lbm.Lattice(1, ny, 1, stencil=q, tau=tau)
+    lat.set_flags(flags)
+    lat.set_force(g)
+    lat.init_equilibrium()
+    ora = oracle.Oracle(1, ny, 1, q=q, tau=tau, force=(g, 0, 0), flags=flags)
+    ora.init_equilibrium(1.0, np.zeros(3))
+    lat.step(steps)
+    ora.step(steps, threads=1)
+    lat.sync()
+    _, u = lat.moments()
+    _, ur = ora.moments()
+    return u[0, 0, 1:ny - 1, 0].astype(np.float64), ur[0, 0, 1:ny - 1, 0]
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_laminar_steady_state_matches_oracle_1e5(q):
+    """The laminar tolerance (1e-5 relative, max |u_gpu - u_oracle| / max |u_oracle|) at steady
+    state.  In float32 the slowest mode of a laminar run stops decaying once its per-step
+    change falls below half an ulp of the stored populations, i.e. at a relative size of about
+    2^-24 .. 2^-23 times its decay time 1/lambda, lambda = nu pi^2 / H^2 (per step).  This
+    channel (H = 16, tau = 2, lambda = 0.019) keeps that below 6.2e-6, and it is run to 80
+    decay times, where the oracle has converged to round-off."""
+    ny, tau, g = 18, 2.0, 1e-6
+    nu = (tau - 0.5) / 3
+    lam = nu * np.pi ** 2 / (ny - 2) ** 2
+    u, ur = _steady_channel(q, ny, tau, g, int(80 / lam))
+    # the oracle is at the exact TRT parabola (walls halfway, Lambda = 3/16) to FP64 round-off
+    # (about 3e-15 absolute on u_max = 6.4e-5)
+    y = np.arange(1, ny - 1) - 0.5
+    ua = g / (2 * nu) * y * (ny - 2 - y)
+    assert np.abs(ur - ua).max() <= 1e-9 * ua.max()
+    rel = np.abs(u - ur).max() / np.abs(ur).max()
+    print(f"D3Q{q} steady laminar channel H = 16, tau = 2: |u_gpu - u_oracle| / max u = {rel:.2e}")
+    assert rel <= 1e-5, rel
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_poiseuille_config_physics_steady_state_stagnation_bound(q):
+    """The small Poiseuille case's physics (H = 30 between solid rows, tau = 0.8, g = 1e-6) at
+    steady state (25 decay times): its slowest mode decays at lambda = 1.1e-3 per step, so
+    float32 stagnation allows up to about 2^-23 / lambda = 1.1e-4 relative; the measured
+    difference from the oracle is printed and held to twice 2^-24 / lambda (the stagnation of
+    a mode whose populations sit mid-binade)."""
+    ny, tau, g = 32, 0.8, 1e-6
+    nu = (tau - 0.5) / 3
+    lam = nu * np.pi ** 2 / (ny - 2) ** 2
+    u, ur = _steady_channel(q, ny, tau, g, int(25 / lam))
+    rel = np.abs(u - ur).max() / np.abs(ur).max()
+    print(f"D3Q{q} Poiseuille H = 30 steady state: |u_gpu - u_oracle| / max u = {rel:.2e}"
+          f" (2^-24 / lambda = {2.0 ** -24 / lam:.2e})")
+    assert rel <= 2 * 2.0 ** -24 / lam, rel
+
+
 @pytest.mark.parametrize("q", [19, 27])
 def test_poiseuille_steady_closed_form(q):
     """Quasi-1D channel to steady state: the TRT bounce-back parabola with Lambda = 3/16.
@@ -358,74 +419,27 @@ def test_instability_is_reported_not_trapped():
     lat.sync()
 
 
-@pytest.mark.parametrize("pipeline", ["tma", "prefetch", "async"])
-@pytest.mark.parametrize("name", ["channel19", "tunnel27", "mixed19", "periodic27"])
-@pytest.mark.parametrize("precision", ["f32", "f16"])
-def test_staged_and_direct_pipelines_agree_bit_for_bit(name, precision, pipeline):
-    """The staged steps (TMA bulk copies, register prefetch, cp.async) and the direct-load
-    step compute the same update."""
-    from paper_2305_09910_gb300 import lbm
-
-    case = dict(CASES[name])
-    flags = case.pop("flags", None)
-    a, ora = make_pair(precision=precision, flags=flags, pipeline=pipeline, **case)
-    kw = {k: case[k] for k in ("q", "tau", "closure") if k in case}
-    b = lbm.Lattice(case["nx"], case["ny"], case["nz"], stencil=kw.get("q", 19), tau=kw.get("tau", 0.8),
-                    precision=precision, closure=kw.get("closure", "none"), cs_smag=case.get("cs", 0.1),
-                    faces=case.get("faces", ("periodic",) * 6), u_inflow=case.get("u_w", (0, 0, 0)),
-                    pipeline="direct")
-    assert a.params.pipeline == lbm.PIPELINE[pipeline] and b.params.pipeline == lbm.PIPELINE["direct"]
-    if flags is not None:
-        b.set_flags(flags)
-    b.set_force(*case.get("force", (0.0, 0.0, 0.0)))
-    df = _start(a, ora, dict(CASES[name]), seed=5)
-    b.set_populations(df)
-    for n in (1, 2, 3):
-        a.step(n)
-        b.step(n)
-        assert np.array_equal(a.get_populations(), b.get_populations())
-
-
-@pytest.mark.parametrize("pipeline", ["tma", "prefetch", "async"])
+@pytest.mark.parametrize("streaming", ["aa", "pull"])
 @pytest.mark.parametrize("faces", ["periodic", "channel"])
-@pytest.mark.parametrize("precision,nx", [("f32", 300), ("f16", 300), ("bf16", 301)])
-def test_staged_pipelines_large_seams(pipeline, faces, precision, nx):
-    """Several tiles per row, a ragged last tile and z block, seams in x, y and z.  For half
-    storage the direct step updates x-pairs (a ragged last pair when nx is odd) and the staged
-    ones single cells."""
+@pytest.mark.parametrize("nx", [300, 301])
+def test_large_seams_match_oracle(streaming, faces, nx):
+    """Several warps per row and a ragged last one, odd ny and nz (ragged y blocks), seams in
+    x, y and z: 7 steps against the oracle."""
+    import oracle
     from paper_2305_09910_gb300 import inputs, lbm
 
     ny, nz = 7, 21
     fc = ("periodic",) * 6 if faces == "periodic" else FACES_CHANNEL
-    a = lbm.Lattice(nx, ny, nz, tau=0.6, closure="smag", faces=fc, pipeline=pipeline, precision=precision)
-    b = lbm.Lattice(nx, ny, nz, tau=0.6, closure="smag", faces=fc, pipeline="direct", precision=precision)
+    lat = lbm.Lattice(nx, ny, nz, tau=0.6, closure="smag", faces=fc, streaming=streaming)
+    ora = oracle.Oracle(nx, ny, nz, q=19, tau=0.6, closure="smag", cs=0.1, faces=fc, force=(1e-5, 2e-6, 0))
     rho, u = inputs.channel_init(nx, ny, nz, seed=6)
-    for lat in (a, b):
-        lat.set_force(1e-5, 2e-6, 0)
-        lat.init_equilibrium(rho, u)
-        lat.step(7)
-    assert np.array_equal(a.get_populations(), b.get_populations())
-
-
-@pytest.mark.parametrize("precision", ["f32", "f16"])
-def test_async_pull_matches_direct_pull(precision):
-    from paper_2305_09910_gb300 import lbm
-
-    case = dict(CASES["tunnel19"])
-    flags = case.pop("flags")
-    common = dict(stencil=19, tau=case["tau"], closure="smag", cs_smag=case["cs"], faces=case["faces"],
-                  u_inflow=case["u_w"], precision=precision, streaming="pull")
-    a = lbm.Lattice(case["nx"], case["ny"], case["nz"], pipeline="async", **common)
-    b = lbm.Lattice(case["nx"], case["ny"], case["nz"], pipeline="direct", **common)
-    _, ora = make_pair(flags=flags, **case)
-    for lat in (a, b):
-        lat.set_flags(flags)
-    df = _start(a, ora, dict(CASES["tunnel19"]), seed=23)
-    b.set_populations(df)
-    for n in (1, 2, 3):
-        a.step(n)
-        b.step(n)
-        assert np.array_equal(a.get_populations(), b.get_populations())
+    lat.set_force(1e-5, 2e-6, 0)
+    lat.init_equilibrium(rho, u)
+    ora.init_equilibrium(rho.astype(np.float64), u.astype(np.float64))
+    lat.step(7)
+    ora.step(7)
+    lat.sync()
+    assert max_abs_pop_error(lat, ora) <= 1e-6
 
 
 @pytest.mark.parametrize("name", ["channel19", "tunnel27", "mixed19", "periodic27"])

@@ -70,6 +70,24 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib):
         lbm.lbm_create(4, 4, 4, 19, 0.8, p)
 
 
+def test_create_refuses_the_staged_pipelines_before_touching_the_device(lib):
+    """Only the direct-load pipeline is built; the reserved values are refused, unknown ones
+    are invalid."""
+    from paper_2305_09910_gb300 import lbm
+
+    for pipe, status in ((0, lbm.LBM_EUNSUPPORTED), (2, lbm.LBM_EUNSUPPORTED), (3, lbm.LBM_EUNSUPPORTED),
+                         (7, lbm.LBM_EINVAL)):
+        p = lbm.lbm_params_default(stream=ctypes.c_void_p(0))
+        p.pipeline = pipe
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_create(8, 4, 4, 19, 0.8, p)
+        assert e.value.status == status, (pipe, e.value)
+
+
+def test_wait_limit_entry_rejects_bad_arguments(lib):
+    assert lib.lbm_debug_set_wait_polls(None, 0) == -1  # LBM_EINVAL: no handle
+
+
 def test_uniform01_counter_based():
     from paper_2305_09910_gb300 import inputs
 
