@@ -44,12 +44,12 @@ def _params(seed, scale=0.3):
 # small multiple of 2^-24 log2(n) plus the per-sample relative error, times the sum of the
 # magnitudes of its per-sample terms A_j = sum_s |g_sj| (the conditioning of that sum).
 # Every component is held to 4e-6 A_j; components with |g_j| >= A_j / 10 (no strong
-# cancellation) must also agree to 4e-5 relative.
+# cancellation; about half of them) must also agree to 4e-5 relative.
 def _assert_gradient_elementwise(gg, gr, absum):
     err = np.abs(gg - gr)
     assert np.all(err <= 4e-6 * absum + 1e-30), (np.argmax(err / (absum + 1e-30)), (err / (absum + 1e-30)).max())
     well = np.abs(gr) >= 0.1 * absum
-    assert well.sum() > 0.5 * gr.size
+    assert well.sum() > 0.25 * gr.size
     rel = err[well] / np.abs(gr[well])
     assert rel.max() <= 4e-5, rel.max()
     # the bound is far below every layer's gradient, so a wrong or missing layer fails it
@@ -81,10 +81,17 @@ def test_closure_samples_match_oracle(q):
         x, t, sm, w = (o.cpu().numpy().astype(np.float64) for o in out)
         xr, tr, smr, wr = ora.closure_samples(0.52, 0.1, scale)
         assert np.abs(x - xr).max() <= 1e-5 * np.abs(xr).max()
-        assert np.abs(sm - smr).max() <= 1e-5 * smr.max()
-        assert np.abs(w - wr).max() <= 1e-4 * wr.max()
-        assert tr.max() > 0
-        assert np.abs(t - tr).max() <= 1e-3 * tr.max()
+        # |S_c| and its square per sample, each against its own value
+        assert np.all(np.abs(sm - smr) <= 1e-5 * smr + 1e-30)
+        assert np.all(np.abs(w - wr) <= 1e-5 * wr + 1e-30)
+        # the target eddy viscosity per sample: exact zeros (no strain, or a negative
+        # projection clipped) on the same samples; elsewhere 1e-3 of the sample's own value
+        # (measured: 2.1e-4 at most on samples above 1 % of the largest), with a floor of
+        # 1e-5 of the largest target for the samples near zero, whose projection is a
+        # cancelling FP32 dot product (measured: 6.8e-6)
+        assert tr.max() > 0 and (tr > 0).sum() > nc // 3
+        assert np.array_equal(t == 0, tr == 0)
+        assert np.all(np.abs(t - tr) <= 1e-3 * tr + 1e-5 * tr.max())
 
 
 def test_mlp_forward_backward_match_oracle():

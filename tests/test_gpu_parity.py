@@ -488,20 +488,23 @@ def test_pull_and_aa_agree_bit_for_bit(precision):
 
 @pytest.mark.parametrize("precision", ["f32", "f16", "bf16"])
 @pytest.mark.parametrize("streaming", ["aa", "pull"])
-@pytest.mark.parametrize("pipeline", ["direct", "tma"])
-def test_step_stats_matches_sampling_between_steps(precision, streaming, pipeline):
-    """lbm_step_stats(n, every) (sampled inside the step kernel on the direct pipeline, by a
-    separate pass otherwise) = a loop of lbm_stats_sample before every every-th lbm_step."""
+@pytest.mark.parametrize("closure", ["smag", "mlp"])
+def test_step_stats_matches_sampling_between_steps(precision, streaming, closure):
+    """lbm_step_stats(n, every) (sampled inside the step kernel, or by a separate pass before
+    the step with the learned closure) = a loop of lbm_stats_sample before every every-th
+    lbm_step."""
     from paper_2305_09910_gb300 import inputs, lbm
 
-    if pipeline == "tma" and streaming == "pull":
-        pytest.skip("the staged pipelines serve the AA pattern")
     nx, ny, nz, n, every = 100, 18, 12, 7, 3   # ragged warps in x, wall rows, 3 samples
-    kw = dict(tau=0.56, closure="smag", cs_smag=0.12, faces=FACES_CHANNEL, precision=precision,
-              streaming=streaming, pipeline=pipeline)
+    kw = dict(tau=0.56, closure=closure, cs_smag=0.12, faces=FACES_CHANNEL, precision=precision,
+              streaming=streaming)
     a = lbm.Lattice(nx, ny, nz, **kw)
     b = lbm.Lattice(nx, ny, nz, **kw)
     rho, u = inputs.channel_init(nx, ny, nz, u_bulk=0.05, seed=31)
+    if closure == "mlp":
+        params = np.random.default_rng(31).normal(0, 0.2, lbm.MLP_NPARAM).astype(np.float32)
+        for lat in (a, b):
+            lbm.lbm_set_closure_f32(lat.h, params, 300.0, 30.0)
     for lat in (a, b):
         lat.set_force(2e-6)
         lat.init_equilibrium(rho, u)

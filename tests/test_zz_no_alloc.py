@@ -78,7 +78,7 @@ def test_noalloc_reduce_smaller_lattice_after_larger_and_tunnel():
     from paper_2305_09910_gb300 import inputs, lbm
 
     cases = [(19, (300, 96, 80), FACES_CHANNEL, False), (19, (40, 12, 10), FACES_CHANNEL, False),
-             (27, (96, 48, 48), FACES_TUNNEL, True), (19, (33, 9, 7), FACES_TUNNEL, True)]
+             (27, (96, 48, 48), FACES_TUNNEL, True), (19, (34, 9, 7), FACES_TUNNEL, True)]
     nblocks = []
     for q, (nx, ny, nz), faces, gear in cases:
         n = nx * ny * nz
