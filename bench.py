@@ -48,8 +48,8 @@ def _peak_hbm():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def _profile_traffic(kernel_tag):
-    """Per-launch DRAM bytes from the committed ncu summary of this kernel, if it was taken
+def _profile_value(kernel_tag, key):
+    """A value ("- key: `v`" line) of the committed ncu summary of this kernel, if it was taken
     on step kernels identical to the ones running now (same kernel-source hash); else None."""
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
     if not os.path.exists(path):
@@ -66,9 +66,32 @@ def _profile_traffic(kernel_tag):
     if vals.get("kernel_sha256") != stamp:
         return None
     try:
-        return float(vals["dram_bytes_per_launch"])
+        return float(vals[key])
     except (KeyError, ValueError):
         return None
+
+
+def _profile_traffic(kernel_tag):
+    """Per-launch DRAM bytes (read + write) from the committed ncu summary, or None."""
+    return _profile_value(kernel_tag, "dram_bytes_per_launch")
+
+
+SMS, SCHEDULERS = 152, 4  # GB300: 4 warp schedulers per SM, each issuing one warp instruction per clock
+
+
+def _issue_roofline(mlups, inst_per_cell, sm_mhz, hbm):
+    """Instruction-issue roofline of a kernel bound by its arithmetic: achieved thread
+    instructions per second (instructions per cell from the ncu summary of the same kernel x
+    cell updates per second) against SMs x 4 schedulers x 32 lanes x the SM clock."""
+    peak = SMS * SCHEDULERS * 32 * sm_mhz * 1e6 / 1e9
+    if inst_per_cell is None:
+        return {"bound": "issue", "achieved": None, "peak": round(peak, 1), "unit": "Ginst/s", "frac": None,
+                "traffic": None, "inst_per_cell": None, "sm_mhz": sm_mhz,
+                "note": "no ncu instruction count taken on this kernel build", "hbm": hbm}
+    achieved = inst_per_cell * mlups * 1e6 / 1e9
+    return {"bound": "issue", "achieved": round(achieved, 1), "peak": round(peak, 1), "unit": "Ginst/s",
+            "frac": round(achieved / peak, 4), "traffic": None, "inst_per_cell": inst_per_cell, "sm_mhz": sm_mhz,
+            "hbm": hbm}
 
 
 class ClockSampler:
@@ -268,7 +291,7 @@ def _form_line(lat, nsteps, warmup, peak, peak_kind):
             "roofline": _roofline(lat.ncell, lat.bytes_per_update, per, peak, peak_kind, None)}
 
 
-def _extra_forms(nsteps, warmup, peak, peak_kind):
+def _extra_forms(nsteps, warmup, peak, peak_kind, sm_mhz):
     """The other benchmark shapes, timed the same way (state values do not change the cost
     of a step; these start from rest or from uniform flow):
       * precision form: channel 1024x512x512 (268M cells), FP32 and FP16-shifted storage;
@@ -314,8 +337,11 @@ def _extra_forms(nsteps, warmup, peak, peak_kind):
             lbm.lbm_set_closure_f32(lat.h, params, 600.0, 3000.0)
             lbm.lbm_set_closure_floor(lat.h, 0.1)
         line = _form_line(lat, nsteps, warmup, peak, peak_kind)
-        if name == "mlp":
-            line["roofline"]["bound"] = "alu (fused 7-32-32-1 network per cell; 32x32 layer on tcgen05)"
+        if name == "mlp":  # issue-bound: the network's arithmetic, with the HBM fraction beside it
+            inst = _profile_value(f"k_step_q19_f32_mlp_pull_channel{size}", "inst_per_cell")
+            if inst is None:
+                inst = _profile_value("k_step_q19_f32_mlp_pull_channel256", "inst_per_cell")
+            line["roofline"] = _issue_roofline(line["MLUPS"], inst, sm_mhz, line["roofline"])
         out[f"channel{size}_{name}"] = line
         lat.close()
         torch.cuda.empty_cache()
@@ -419,8 +445,8 @@ def _refined_form(nsteps, warmup, peak, peak_kind, precision="f32"):
                          "bytes_per_update": bpu, "ms_per_coarse_step": round(ms, 4)}}
 
 
-def _cpu_baseline(target_s=12.0):
-    """The FP64 oracle on this host's cores, on a 128x64x64 sub-lattice of the channel."""
+def _time_oracle(threads, target_s):
+    """(MLUPS, steps, seconds) of the FP64 oracle on a 128x64x64 sub-lattice of the channel."""
     import numpy as np
 
     import oracle
@@ -428,7 +454,6 @@ def _cpu_baseline(target_s=12.0):
 
     nx, ny, nz = 128, 64, 64
     par = inputs.channel_parameters(ny)
-    threads = os.cpu_count() or 1
     ora = oracle.Oracle(nx, ny, nz, q=19, tau=par["tau"], closure="smag", cs=0.1,
                         faces=FACES_CHANNEL, force=(par["force"], 0, 0))
     rho, u = inputs.channel_init(nx, ny, nz)
@@ -440,10 +465,20 @@ def _cpu_baseline(target_s=12.0):
     t = time.perf_counter()
     ora.step(steps, threads=threads)
     dt = time.perf_counter() - t
-    mlups = nx * ny * nz * steps / dt / 1e6
+    return nx * ny * nz * steps / dt / 1e6, steps, dt
+
+
+def _cpu_baseline(target_s=12.0, target_one_s=6.0):
+    """The FP64 oracle on this host's cores (all of them, and one), on a 128x64x64 sub-lattice
+    of the channel."""
+    threads = os.cpu_count() or 1
+    mlups, steps, dt = _time_oracle(threads, target_s)
+    m1, s1, d1 = _time_oracle(1, target_one_s)
     return {"value": round(mlups, 3), "unit": "MLUPS", "cores": threads, "kind": "oracle",
-            "sample": f"FP64 oracle, channel {nx}x{ny}x{nz} D3Q19 TRT+Smagorinsky, {steps} steps "
-                      f"({dt:.1f} s, OpenMP over z)"}
+            "sample": f"FP64 oracle, channel 128x64x64 D3Q19 TRT+Smagorinsky, {steps} steps "
+                      f"({dt:.1f} s, OpenMP over z on {threads} threads)",
+            "one_thread": {"value": round(m1, 3), "unit": "MLUPS", "cores": 1,
+                           "sample": f"the same sub-lattice, {s1} steps ({d1:.1f} s) on 1 thread"}}
 
 
 def run_reference(args):
@@ -537,6 +572,7 @@ def main():
     clocks.start()
     total_ms, per = _time_steps(lat, args.steps, 3, dist, stats_every=10 if channel else 0)
     clocks.stop()
+    clock_summary = clocks.summary()
     total_ms = _barrier_max(dist, total_ms)
     value = world * ncell * args.steps / (total_ms * 1e-3) / 1e6
     q = 19 if channel else 27
@@ -589,7 +625,8 @@ def main():
             forms[name] = _form_line(fl, nsteps, args.warmup, peak, peak_kind)
             fl.close()
             torch.cuda.empty_cache()
-        forms.update(_extra_forms(nsteps, args.warmup, peak, peak_kind))
+        sm_mhz = clock_summary.get("sm_mhz") or 2070.0
+        forms.update(_extra_forms(nsteps, args.warmup, peak, peak_kind, sm_mhz))
         forms["channel512_f32_2slabs_halo"] = _slab_form(2, nsteps, args.warmup, peak, peak_kind)
         for streaming in ("pull", "aa"):
             forms[f"poiseuille64_f32_{streaming}"] = _small_form(streaming)
@@ -620,7 +657,7 @@ def main():
                                 "inside the timed region") if channel else "none",
                       "l2": f"inputs larger than L2 ({lat_bytes / 1e9:.2f} GB population array vs 129 MB L2)"},
            "roofline": roof, "e2e": e2e, "gpu_launches": launches,
-           "clocks": clocks.summary(), "mass_after": mass, "forms": forms}
+           "clocks": clock_summary, "mass_after": mass, "forms": forms}
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = _cpu_baseline()
     if rank == 0:
