@@ -1,31 +1,32 @@
-// lbm_mlp.cuh -- the stream-collide step with the learned closure, its 32x32 hidden layer on
+// lbm_mlp.cuh -- the stream-collide step with the learned closure, its two hidden layers on
 // the fifth-generation tensor cores (tcgen05.mma, accumulator in tensor memory).
 //
-// Per tile of 128 cells (one CTA: 4 warps, each 32 x-consecutive cells of one row) every
-// thread loads its cell, forms the moments and the non-equilibrium stress, evaluates the
-// first layer (7 -> 32, GELU) in FP32 and writes the 32 hidden values, rounded to TF32, as
-// row t of a 128 x 32 operand tile in shared memory.  One thread issues four
-// tcgen05.mma.kind::tf32 (M = 128, N = 32, K = 8 each) against W2 (bf16 values, exact in TF32)
-// into 32 columns of tensor memory and commits them to an mbarrier.  Each warp then reads its
-// 32 TMEM lanes with tcgen05.ld -- lane t of the accumulator is exactly cell t's 32 outputs,
-// so the epilogue (bias, GELU, 32 -> 1 output layer, softplus) stays one thread per cell --
-// and the thread finishes the TRT update with the learned C_s^2.
+// Per tile of 128 cells (one group: 4 warps, each 32 x-consecutive cells of one row) every
+// thread loads its cell, forms the moments and the non-equilibrium stress, and writes its 7
+// scaled features and a constant 1 (which carries the bias b1), rounded to TF32, as row t of
+// a 128 x 8 operand tile in shared memory.  One thread issues tcgen05.mma.kind::tf32
+// (M = 128, N = 32, K = 8) against [W1 | b1] into 32 columns of tensor memory and commits it
+// to an mbarrier; each warp reads its 32 TMEM lanes with tcgen05.ld (lane t = cell t's 32
+// pre-activations), applies the GELU and writes row t of the 128 x 32 layer-2 operand, again
+// in TF32.  Four more MMAs (K = 4 x 8) against W2 overwrite the same TMEM columns; the
+// epilogue (bias b2, GELU, 32 -> 1 output layer, softplus) stays one thread per cell and the
+// thread finishes the TRT update with the learned C_s^2.  Weights are bfloat16 values, exact
+// in TF32.
 //
-// The CTA is persistent and holds MLP_NG independent groups of 128 threads (4 warps each):
-// the runtime schedules one CTA per multiprocessor for a kernel that allocates tensor memory,
-// so the groups are what keeps several tiles in flight per SM.  Group g owns TMEM columns
-// 32g .. 32g+31 (warp w of the CTA reads lanes 32 (w % 4) .. +31), its own operand tile and
-// mbarrier, and synchronises on named barrier 1 + g; TMEM (32 MLP_NG columns) is allocated
-// once and W2 staged once per CTA.  Operand
-// tiles use the no-swizzle K-major layout of 8-row x 16-byte core matrices: element (r, k) of
-// a 4-byte-element tile at (r / 8) * 1024 + (k / 4) * 128 + (r % 8) * 16 + (k % 4) * 4, i.e.
-// leading-dimension byte offset 128 (K-adjacent core matrices), stride byte offset 1024
-// (8-row groups).  Every mbarrier wait is bounded.  When a group's first wait for a tile's MMA
-// gives up (after p.wait_polls polls), the group sets status bit 1, waits again with the full
-// bound so that the tensor core has finished with its accumulator and operand tile, and leaves
-// its tile loop; the CTA then frees its tensor memory and returns.  Should that second wait
-// give up too, status bit 2 records that the MMA may still be running: the launch's results
-// and the tensor memory it held are then undefined.
+// The CTA is persistent and holds MLP_NG independent groups of 128 threads (4 warps each),
+// which keep several tiles in flight per SM.  Group g owns TMEM columns 32g .. 32g+31 (warp w
+// of the CTA reads lanes 32 (w % 4) .. +31), its own operand tiles and mbarrier, and
+// synchronises on named barrier 1 + g; TMEM (32 MLP_NG columns) is allocated once and the
+// weights staged once per CTA.  Operand tiles use the no-swizzle K-major layout of 8-row x
+// 16-byte core matrices: element (r, k) of a 4-byte-element tile of K columns at
+// (r / 8) * 32 K + (k / 4) * 128 + (r % 8) * 16 + (k % 4) * 4 bytes, i.e. leading-dimension
+// byte offset 128 (K-adjacent core matrices) and stride byte offset 32 K (8-row groups).
+// Every mbarrier wait is bounded.  When a group's first wait for a tile's MMA gives up
+// (after p.wait_polls polls), the group sets status bit 1, waits again with the full bound so
+// that the tensor core has finished with its accumulator and operand tiles, and leaves its
+// tile loop; the CTA then frees its tensor memory and returns.  Should that second wait give
+// up too, status bit 2 records that the MMA may still be running: the launch's results and
+// the tensor memory it held are then undefined.
 #pragma once
 
 #include "lbm_kernels.cuh"
@@ -46,15 +47,29 @@ __device__ __forceinline__ uint32_t cta_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// shared-memory matrix descriptor: start, leading byte offset 128, stride byte offset 1024,
-// descriptor version 1 (bit 46), no swizzle
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(1024u >> 4) << 32) |
+// shared-memory matrix descriptor: start, leading byte offset 128, stride byte offset sbo
+// (32 K bytes for a tile of K 4-byte columns), descriptor version 1 (bit 46), no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
          (1ull << 46);
 }
 
-__device__ __forceinline__ int core_off(int r, int k) {  // in floats
-  return (r >> 3) * 256 + (k >> 2) * 32 + (r & 7) * 4 + (k & 3);
+// offset (in floats) of element (r, k) of a tile of K columns in the core-matrix layout
+template <int K>
+__device__ __forceinline__ int core_off(int r, int k) {
+  return (r >> 3) * (8 * K) + (k >> 2) * 32 + (r & 7) * 4 + (k & 3);
+}
+
+// one tcgen05.mma.kind::tf32 (M = 128, N = 32, K = 8): D (+)= A B^T, D in tensor memory
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t da, uint64_t db, int accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(da), "l"(db), "r"(MLP_IDESC), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ void mbar_init1(uint32_t bar) {
@@ -100,11 +115,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int k = 0; k < 16; k++) v[k] = __uint_as_float(r[k]);
 }
 
+constexpr int MLP_K1 = 8;  // layer-1 operand columns: the 7 features and a constant 1
+
 struct MlpSmem {
-  float A[MLP_NG][MLP_TILE * MLP_NH];  // hidden layer 1 per group, TF32, core-matrix layout (16 KB each)
-  float B[MLP_NH * MLP_NH];            // W2, core-matrix layout (4 KB)
-  // layers 1 and 3 as pairs of hidden units (j, j+1) for the packed FP32x2 pipe
-  float2 W1[MLP_NH / 2][MLP_NIN], b1[MLP_NH / 2], b2[MLP_NH / 2], W3[MLP_NH / 2];
+  float A[MLP_NG][MLP_TILE * MLP_NH];  // layer-2 operand per group (hidden layer 1, TF32; 16 KB each)
+  float X[MLP_NG][MLP_TILE * MLP_K1];  // layer-1 operand per group (features and 1, TF32; 4 KB each)
+  float B[MLP_NH * MLP_NH];            // W2 (4 KB)
+  float B1[MLP_NH * MLP_K1];           // [W1 | b1] (1 KB)
+  // the output-layer epilogue as pairs of hidden units (j, j+1) for the packed FP32x2 pipe
+  float2 b2[MLP_NH / 2], W3[MLP_NH / 2];
   float b3;
   unsigned long long bar[MLP_NG];
   uint32_t tmem;
@@ -138,14 +157,13 @@ __global__ void __launch_bounds__(128 * MLP_NG, 1) k_step_mlp(const __grid_const
     const float* W3 = b2 + MLP_NH;
     for (int k = tc; k < MLP_NH * MLP_NH; k += 128 * MLP_NG) {
       const int n = k / MLP_NH, kk = k % MLP_NH;  // output n, input kk
-      sm.B[core_off(n, kk)] = W2[k];
+      sm.B[core_off<MLP_NH>(n, kk)] = W2[k];
     }
-    for (int k = tc; k < (MLP_NH / 2) * MLP_NIN; k += 128 * MLP_NG) {
-      const int jp = k / MLP_NIN, i = k % MLP_NIN;
-      sm.W1[jp][i] = make_float2(W1[(2 * jp) * MLP_NIN + i], W1[(2 * jp + 1) * MLP_NIN + i]);
+    for (int k = tc; k < MLP_NH * MLP_K1; k += 128 * MLP_NG) {
+      const int n = k / MLP_K1, kk = k % MLP_K1;  // output n, input kk (kk = 7: the bias)
+      sm.B1[core_off<MLP_K1>(n, kk)] = kk < MLP_NIN ? W1[n * MLP_NIN + kk] : b1[n];
     }
     if (tc < MLP_NH / 2) {
-      sm.b1[tc] = make_float2(b1[2 * tc], b1[2 * tc + 1]);
       sm.b2[tc] = make_float2(b2[2 * tc], b2[2 * tc + 1]);
       sm.W3[tc] = make_float2(W3[2 * tc], W3[2 * tc + 1]);
     }
@@ -160,7 +178,7 @@ __global__ void __launch_bounds__(128 * MLP_NG, 1) k_step_mlp(const __grid_const
                    : "memory");
       asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // W2 tile -> tensor core
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // weight tiles -> tensor core
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -170,10 +188,41 @@ __global__ void __launch_bounds__(128 * MLP_NG, 1) k_step_mlp(const __grid_const
   const uint32_t tl = dcol + ((uint32_t)((warp & 3) * 32) << 16);  // this warp's lanes
   const uint32_t bar = cta_addr(&sm.bar[g]);
   float* const A = sm.A[g];
-  const uint32_t a0 = cta_addr(A), b0 = cta_addr(sm.B);
+  float* const X = sm.X[g];
+  const uint32_t a0 = cta_addr(A), x0 = cta_addr(X), b0 = cta_addr(sm.B), b10 = cta_addr(sm.B1);
   const int nbx = p.nxp / 32, nby = (p.ny + 3) / 4;
   const int gbar = 1 + g;  // named barrier of the group (0 is __syncthreads)
   uint32_t phase = 0;
+  // Waits for the group's MMA; false (after the tensor core has finished) if the wait gave up.
+  auto wait_mma = [&]() -> bool {
+    const bool timed_out = !mbar_wait_parity(bar, phase, p.wait_polls);
+    if (group_any(gbar, timed_out)) {
+      if (t == 0) atomicOr(p.status, 2);
+      if (!mbar_wait_parity(bar, phase, MBAR_POLLS)) atomicOr(p.status, 4);
+      return false;
+    }
+    phase ^= 1u;
+    tc_fence_after();
+    return true;
+  };
+  // Makes the group's shared-memory operand rows visible to the tensor core, then has thread 0
+  // of the group issue the layer's MMAs and commit them to the group's mbarrier.
+  auto issue = [&](bool layer1) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    group_sync(gbar);
+    if (t == 0) {
+      tc_fence_after();
+      if (layer1) {
+        mma_tf32(dcol, umma_desc(x0, 32 * MLP_K1), umma_desc(b10, 32 * MLP_K1), 0);
+      } else {
+#pragma unroll
+        for (int kk = 0; kk < MLP_NH / 8; kk++)  // K = 8 per instruction: 2 core matrices = 256 B
+          mma_tf32(dcol, umma_desc(a0 + kk * 256, 32 * MLP_NH), umma_desc(b0 + kk * 256, 32 * MLP_NH), kk);
+      }
+      mma_commit(bar);
+    }
+  };
   for (long long tile = (long long)blockIdx.x * MLP_NG + g; tile < ntiles; tile += (long long)gridDim.x * MLP_NG) {
     const int bx = (int)(tile % nbx);
     const long long r = tile / nbx;
@@ -189,50 +238,35 @@ __global__ void __launch_bounds__(128 * MLP_NG, 1) k_step_mlp(const __grid_const
     load_state<Q, S, LOAD>(p, x, y, z, cell, cls, f, outmask);
     outflow_fix<Q>(p, x, f, outmask);
     const Macro<float> M = macro<Q, true, float>(p, f);
-    // layer 1 (FP32, two hidden units per packed FP32x2 operation), GELU, TF32 rounding,
-    // row t of the operand tile
-    float xin[MLP_NIN];
+    // layer 1 on the tensor core: row t of the feature tile = the 7 clipped, scaled features
+    // and 1 (the bias column), in TF32
+    {
+      float xin[MLP_NIN];
 #pragma unroll
-    for (int k = 0; k < 6; k++) xin[k] = fminf(fmaxf(p.mlp_scale[0] * M.pi[k], -MLP_XCLAMP), MLP_XCLAMP);
-    xin[6] = fminf(fmaxf(p.mlp_scale[1] * M.drho, -MLP_XCLAMP), MLP_XCLAMP);
+      for (int k = 0; k < 6; k++) xin[k] = fminf(fmaxf(p.mlp_scale[0] * M.pi[k], -MLP_XCLAMP), MLP_XCLAMP);
+      xin[6] = fminf(fmaxf(p.mlp_scale[1] * M.drho, -MLP_XCLAMP), MLP_XCLAMP);
+      *reinterpret_cast<uint4*>(X + core_off<MLP_K1>(t, 0)) =
+          make_uint4(to_tf32(xin[0]), to_tf32(xin[1]), to_tf32(xin[2]), to_tf32(xin[3]));
+      *reinterpret_cast<uint4*>(X + core_off<MLP_K1>(t, 4)) =
+          make_uint4(to_tf32(xin[4]), to_tf32(xin[5]), to_tf32(xin[6]), __float_as_uint(1.f));
+    }
+    issue(true);
+    if (!wait_mma()) break;
+    // GELU of the 32 pre-activations (this thread's TMEM lane), TF32, row t of the layer-2 tile
 #pragma unroll
-    for (int c4 = 0; c4 < MLP_NH / 4; c4++) {
-      float2 s01 = sm.b1[2 * c4], s23 = sm.b1[2 * c4 + 1];
+    for (int half = 0; half < 2; half++) {
+      float v[16];
+      tmem_ld16(tl + 16 * half, v);
 #pragma unroll
-      for (int k = 0; k < MLP_NIN; k++) {
-        const float2 xk = make_float2(xin[k], xin[k]);
-        s01 = vfma(sm.W1[2 * c4][k], xk, s01);
-        s23 = vfma(sm.W1[2 * c4 + 1][k], xk, s23);
+      for (int c = 0; c < 4; c++) {
+        const float2 g01 = gelu_v(make_float2(v[4 * c], v[4 * c + 1]));
+        const float2 g23 = gelu_v(make_float2(v[4 * c + 2], v[4 * c + 3]));
+        *reinterpret_cast<uint4*>(A + core_off<MLP_NH>(t, 16 * half + 4 * c)) =
+            make_uint4(to_tf32(g01.x), to_tf32(g01.y), to_tf32(g23.x), to_tf32(g23.y));
       }
-      const float2 g01 = gelu_v(s01), g23 = gelu_v(s23);
-      *reinterpret_cast<uint4*>(A + core_off(t, 4 * c4)) =
-          make_uint4(to_tf32(g01.x), to_tf32(g01.y), to_tf32(g23.x), to_tf32(g23.y));
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    tc_fence_before();
-    group_sync(gbar);
-    if (t == 0) {
-      tc_fence_after();
-#pragma unroll
-      for (int kk = 0; kk < MLP_NH / 8; kk++) {  // K = 8 per instruction: 2 core matrices = 256 B
-        const uint64_t da = umma_desc(a0 + kk * 256), db = umma_desc(b0 + kk * 256);
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dcol),
-            "l"(da), "l"(db), "r"(MLP_IDESC), "r"(kk)
-            : "memory");
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-    }
-    const bool timed_out = !mbar_wait_parity(bar, phase, p.wait_polls);
-    if (group_any(gbar, timed_out)) {
-      // give up on this launch, but only after the MMA has finished with the accumulator and
-      // the operand tile (the commit still arrives on the barrier)
-      if (t == 0) atomicOr(p.status, 2);
-      if (!mbar_wait_parity(bar, phase, MBAR_POLLS)) atomicOr(p.status, 4);
-      break;
-    }
-    phase ^= 1u;
-    tc_fence_after();
+    issue(false);  // (its barrier also orders every lane's layer-1 reads before the overwrite)
+    if (!wait_mma()) break;
     // epilogue: this thread's 32 accumulator columns, bias, GELU, output layer (pairs)
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
@@ -254,6 +288,8 @@ __global__ void __launch_bounds__(128 * MLP_NG, 1) k_step_mlp(const __grid_const
       if (!(M.rho > 0.f && M.rho < 3.0e38f)) atomicOr(p.status, 1);
       store_state<Q, S, STORE>(p, x, y, z, cell, cls, f);
     }
+    // the next tile's layer-1 MMA overwrites these TMEM columns: order this lane's reads first
+    tc_fence_before();
   }
   tc_fence_before();
   __syncthreads();
