@@ -33,10 +33,13 @@ static void step_mode_s(const KParams& p, int closure, const Launch& L, int coll
     else k_step<Q, S, CL_SMAG, LOAD, STORE, STATS, 2><<<L.grid, L.block, 0, L.stream>>>(p);
     return;
   }
-  // half storage, D3Q19: x-pairs, 64 x per warp (for D3Q27 the pair kernel needs more
-  // registers than it saves, and on the bluff body the warps at the inflow and outflow faces
-  // take its one-cell fallback: the one-cell kernel is faster, measured)
-  if constexpr (sizeof(S) == 2 && Q == 19) {
+  // half storage: x-pairs, 64 x per warp; D3Q27 only with two-grid pull, where boundary lanes
+  // load by the rules instead of sending the warp to the one-cell code and the populations
+  // stay packed in registers through the collision (its AA form keeps the one-cell kernel)
+#ifndef LBM_H2_Q27
+#define LBM_H2_Q27 0
+#endif
+  if constexpr (sizeof(S) == 2 && (Q == 19 || (LBM_H2_Q27 && STORE == 2))) {
     dim3 g = L.grid;
     g.x = (p.nxp + 63) / 64;
     if (nws) *nws = (int)g.x;

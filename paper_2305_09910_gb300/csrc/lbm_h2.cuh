@@ -121,6 +121,134 @@ __device__ __noinline__ void pair_fallback(const KParams& p, int x, int y, int z
   }
 }
 
+// ---- two-grid pull: every warp takes the pair path ---------------------------------------
+// A lane whose cells are not both interior loads them with the boundary rules of the one-cell
+// step (out of line, below); the collision and the own-cell stores are common to all lanes, a
+// lane with a skipped (solid or padding) cell storing only its other cell's half.
+
+// Both cells of a boundary lane with the one-cell loads (load_state), packed into hs (the
+// loaded values are exact in the storage precision).  Out of line: the rule-by-rule loads are
+// long, run for few lanes, and inlined they would crowd the instruction cache of every warp.
+template <int Q, class S, int PAR>
+__device__ __noinline__ void load_pair_rules(const KParams& p, int x, int y, int z, int cell, int clsA, int clsB,
+                                             uint32_t* hs, unsigned* oa, unsigned* ob) {
+  float f[Q];
+  load_state<Q, S, PAR>(p, x, y, z, cell, clsA, f, *oa);
+#pragma unroll
+  for (int i = 0; i < Q; i++) hs[i] = bits16<S>(f[i]);
+  load_state<Q, S, PAR>(p, x + 1, y, z, cell + 1, clsB, f, *ob);
+#pragma unroll
+  for (int i = 0; i < Q; i++) hs[i] |= bits16<S>(f[i]) << 16;
+}
+
+// Zero-gradient outflow on packed words: x = nx-1 takes what x-1 receives (the lane's own
+// first cell, or the previous lane's second).  Warp-uniform condition, full-mask shuffles.
+template <int Q>
+__device__ __forceinline__ void outflow_fix_packed(const KParams& p, int x0, uint32_t (&h)[Q], unsigned oa,
+                                                   unsigned ob) {
+  if (!p.outflow) return;
+  if (!(x0 <= p.nx - 1 && p.nx - 1 < x0 + 64)) return;
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    if (cx(i) != -1) continue;
+    const uint32_t prev = __shfl_up_sync(0xffffffffu, h[i], 1);
+    if (ob & (1u << i)) h[i] = (h[i] & 0xffffu) | (h[i] << 16);
+    if (oa & (1u << i)) h[i] = (h[i] & 0xffff0000u) | (prev >> 16);
+  }
+}
+
+#ifndef LBM_H2_PACKED19
+#define LBM_H2_PACKED19 0
+#endif
+#ifndef LBM_H2_PACKED27
+#define LBM_H2_PACKED27 1
+#endif
+#ifndef LBM_H2_MINB27
+#define LBM_H2_MINB27 5
+#endif
+
+// The collision of both cells (float2 lanes).  PACKED: the populations stay packed and are
+// unpacked at each use (fewer live registers); else they are unpacked once into float2 values.
+template <int Q, class S, int CL, bool PACKED>
+__device__ __forceinline__ float2 collide_pair(const KParams& p, uint32_t (&h)[Q], Macro<float2>* mout) {
+  if constexpr (PACKED) {
+    PackedPops<Q, S> a{h};
+    const Macro<float2> M = macro_acc<Q, CL != CL_NONE, float2>(p, a);
+    if (mout) *mout = M;
+    float2 wp = vset<float2>(p.omega_p), wm = vset<float2>(p.omega_m);
+    if (CL != CL_NONE) {
+      les_rates(p, M.qn.x, M.inv.x, p.cs2, wp.x, wm.x);
+      les_rates(p, M.qn.y, M.inv.y, p.cs2, wp.y, wm.y);
+    }
+    relax_lean<Q, float2>(p, a, M, wp, wm);
+    return M.rho;
+  } else {
+    float2 f[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) f[i] = unpack2<S>(h[i]);
+    const float2 rho = collide<Q, CL, float2, false>(p, f, mout);
+#pragma unroll
+    for (int i = 0; i < Q; i++) h[i] = pack2rn<S>(f[i]);
+    return rho;
+  }
+}
+
+template <int Q, class S, int CL, int LOAD, bool STATS>
+__device__ __forceinline__ void pair_pull(const KParams& p, int x, int y, int z, int cell, int clsA, int clsB,
+                                          bool fast, float (&v)[NSTAT]) {
+  constexpr bool PACKED = Q == 27 ? LBM_H2_PACKED27 : LBM_H2_PACKED19;
+  uint32_t h[Q];
+  unsigned oa = 0, ob = 0;
+  if (fast) {
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+      if (LOAD == 0) {
+        h[i] = ld32(p, plane_ptr<S>(p, i) + cell);
+      } else {
+        const S* base = static_cast<const S*>(p.gb[i]);
+        if (cx(i) == 0) {
+          h[i] = ld32(p, base + cell);
+        } else {
+          int a, b;
+          xsrc(cx(i), p, x, cell, a, b);
+          h[i] = ld16(p, base + a) | (ld16(p, base + b) << 16);
+        }
+      }
+    }
+  } else {
+    uint32_t hs[Q];
+    load_pair_rules<Q, S, LOAD>(p, x, y, z, cell, clsA, clsB, hs, &oa, &ob);
+#pragma unroll
+    for (int i = 0; i < Q; i++) h[i] = hs[i];
+  }
+  outflow_fix_packed<Q>(p, 64 * blockIdx.x, h, oa, ob);
+  Macro<float2> M2;
+  const float2 rho = collide_pair<Q, S, CL, PACKED>(p, h, STATS ? &M2 : nullptr);
+  const bool liveA = clsA != CLS_SKIP, liveB = clsB != CLS_SKIP;
+  if ((liveA && !(rho.x > 0.f && rho.x < 3.0e38f)) || (liveB && !(rho.y > 0.f && rho.y < 3.0e38f)))
+    atomicOr(p.status, 1);
+  if (STATS) {
+    float va[NSTAT], vb[NSTAT];
+    Macro<float> Ma, Mb;
+    Ma.ux = M2.ux.x; Ma.uy = M2.uy.x; Ma.uz = M2.uz.x;
+    Mb.ux = M2.ux.y; Mb.uy = M2.uy.y; Mb.uz = M2.uz.y;
+    stat_values(Ma, va);
+    stat_values(Mb, vb);
+#pragma unroll
+    for (int k = 0; k < NSTAT; k++) v[k] = (liveA ? va[k] : 0.f) + (liveB ? vb[k] : 0.f);
+  }
+  if (liveA && liveB) {
+#pragma unroll
+    for (int i = 0; i < Q; i++) st32(p, static_cast<S*>(p.fq[i]) + cell, h[i]);
+  } else if (liveA) {
+#pragma unroll
+    for (int i = 0; i < Q; i++) st16(p, static_cast<S*>(p.fq[i]) + cell, h[i] & 0xffffu);
+  } else if (liveB) {
+#pragma unroll
+    for (int i = 0; i < Q; i++) st16(p, static_cast<S*>(p.fq[i]) + cell + 1, h[i] >> 16);
+  }
+}
+
 #ifndef LBM_H2_VEC
 #define LBM_H2_VEC 1
 #endif
@@ -130,7 +258,7 @@ __device__ __noinline__ void pair_fallback(const KParams& p, int x, int y, int z
 // STATS: also write the plane statistics of the state this step starts from (warp slot
 // blockIdx.x of each row, ceil(nxp/64) slots per row).
 template <int Q, class S, int CL, int LOAD, int STORE, bool STATS = false>
-__global__ void __launch_bounds__(128, LBM_H2_MINB) k_step_h2(const __grid_constant__ KParams p) {
+__global__ void __launch_bounds__(128, Q == 27 ? LBM_H2_MINB27 : LBM_H2_MINB) k_step_h2(const __grid_constant__ KParams p) {
   static_assert(sizeof(S) == 2, "two 16-bit populations per word");
   const int x = 2 * (blockIdx.x * 32 + threadIdx.x);
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -149,7 +277,9 @@ __global__ void __launch_bounds__(128, LBM_H2_MINB) k_step_h2(const __grid_const
   float v[NSTAT];
 #pragma unroll
   for (int k = 0; k < NSTAT; k++) v[k] = 0.f;
-  if (__all_sync(0xffffffffu, fast)) {
+  if constexpr (STORE == 2) {
+    pair_pull<Q, S, CL, LOAD, STATS>(p, x, y, z, cell, clsA, clsB, fast, v);
+  } else if (__all_sync(0xffffffffu, fast)) {
     uint32_t h[Q];
 #pragma unroll
     for (int i = 0; i < Q; i++) {

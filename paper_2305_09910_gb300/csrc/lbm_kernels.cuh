@@ -551,12 +551,48 @@ __device__ __forceinline__ void macc(V (&m)[10], V v, int sign) {
   else m[K] = sign > 0 ? vadd(m[K], v) : vsub(m[K], v);
 }
 
+// Population accessors of the moment and lean collision code: an array of values (one cell
+// per thread, or two as float2), or two cells' half-precision values packed in 32-bit words,
+// unpacked at each use and packed (round to nearest even) at each store, so that only the
+// packed words stay live.  Both run the same operations in the same order.
+template <int Q, class V, class T = V>  // T = const V: read only
+struct ArrPops {
+  T (&f)[Q];
+  template <int I> __device__ __forceinline__ V get() const { return f[I]; }
+  template <int I> __device__ __forceinline__ void set(V v) { f[I] = v; }
+};
+
+template <class S> __device__ __forceinline__ float2 unpack2(uint32_t w);
+template <> __device__ __forceinline__ float2 unpack2<__half>(uint32_t w) {
+  return __half22float2(*reinterpret_cast<const __half2*>(&w));
+}
+template <> __device__ __forceinline__ float2 unpack2<__nv_bfloat16>(uint32_t w) {
+  return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+template <class S> __device__ __forceinline__ uint32_t pack2rn(float2 v);
+template <> __device__ __forceinline__ uint32_t pack2rn<__half>(float2 v) {
+  const __half2 h = __floats2half2_rn(v.x, v.y);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+template <> __device__ __forceinline__ uint32_t pack2rn<__nv_bfloat16>(float2 v) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+template <int Q, class S>
+struct PackedPops {
+  uint32_t (&h)[Q];
+  template <int I> __device__ __forceinline__ float2 get() const { return unpack2<S>(h[I]); }
+  template <int I> __device__ __forceinline__ void set(float2 v) { h[I] = pack2rn<S>(v); }
+};
+
 // Sums over the pair (I, I+1): s = f_I + f_I+1, d = f_P - f_R (P primary, R its opposite).
-template <int Q, int I, class V>
-__device__ __forceinline__ void pair_moments(const V (&f)[Q], V (&m)[10]) {
-  constexpr int P = prim(I), R = P == I ? I + 1 : I;
-  const V s = vadd(f[I], f[I + 1]);
-  const V d = vsub(f[P], f[R]);
+template <int Q, int I, class V, class A>
+__device__ __forceinline__ void pair_moments_acc(const A& a, V (&m)[10]) {
+  constexpr int P = prim(I);
+  const V fi = a.template get<I>(), fj = a.template get<I + 1>();
+  const V s = vadd(fi, fj);
+  const V d = P == I ? vsub(fi, fj) : vsub(fj, fi);
   macc<0, I>(m, s, 1);
 #pragma unroll
   for (int k = 1; k <= 3; k++) {
@@ -573,9 +609,9 @@ __device__ __forceinline__ void pair_moments(const V (&f)[Q], V (&m)[10]) {
   if (mcoef(9, P)) macc<9, I>(m, s, mcoef(9, P));
 }
 
-template <int Q, class V, int... P>
-__device__ __forceinline__ void all_pair_moments(const V (&f)[Q], V (&m)[10], std::integer_sequence<int, P...>) {
-  (pair_moments<Q, 2 * P + 1, V>(f, m), ...);
+template <int Q, class V, class A, int... P>
+__device__ __forceinline__ void all_pair_moments(const A& a, V (&m)[10], std::integer_sequence<int, P...>) {
+  (pair_moments_acc<Q, 2 * P + 1, V>(a, m), ...);
 }
 
 template <class V>
@@ -590,9 +626,11 @@ struct CollCtx {
 // One +/- pair of the TRT collision, written as f* = f + delta so that the only rounding at
 // the magnitude of f is the final addition.  The antisymmetric equilibrium 3 w (c.j) is
 // carried as an unevaluated sum eh + el (the FMA recovers the product's rounding error
-// exactly; eln = -el), and the non-equilibrium parts are formed by subtracting it from f
-// first, where the operands nearly cancel.  This keeps the per-step momentum error at the
-// level of one rounding of f, which matters at the small velocities of laminar runs.
+// exactly; eln = -el).  With a = f_P - eh and b = f_R + eh (exact when the operands are
+// within a factor two, as near equilibrium), the non-equilibrium parts of the pair are
+//   n+ = (a + b) - 2 w (A + B (c.u)^2)   and   n- = (a - b) + 2 eln,
+// a - b being exact as well.  This keeps the per-step momentum error at the level of one
+// rounding of f, which matters at the small velocities of laminar runs.
 template <int Q, int I, class V>
 __device__ __forceinline__ void trt_pair(const KParams& p, V (&f)[Q], const CollCtx<V>& c) {
   constexpr int P = prim(I), R = P == I ? I + 1 : I;
@@ -604,13 +642,14 @@ __device__ __forceinline__ void trt_pair(const KParams& p, V (&f)[Q], const Coll
   const V cj = cdot<X, Y, Z>(c.jx, c.jy, c.jz);
   const V eh = vmul(cj, vset<V>(khi));
   const V eln = vfma(cj, vset<V>(-klo), vfma(cj, vset<V>(-khi), eh));
-  const V es = vmul(vset<V>(w), vfma(c.B, vmul(cu, cu), c.A));
-  const V ni = vsub(vadd(vsub(f[P], eh), eln), es);
-  const V nj = vsub(vsub(vadd(f[R], eh), eln), es);
+  const V a = vsub(f[P], eh), b = vadd(f[R], eh);
+  const V es2 = vmul(vset<V>(2.f * w), vfma(c.B, vmul(cu, cu), c.A));
+  const V np = vsub(vadd(a, b), es2);
+  const V nm = vfma(eln, vset<V>(2.f), vsub(a, b));
   // Guo terms: symmetric w (9 (c.u)(c.F) - 3 u.F), antisymmetric 3 w (c.F)
   const V fsym = vfma(vmul(c.gp, vset<V>(p.F9w[P])), cu, vmul(c.gu3, vset<V>(-w)));
-  const V ds = vfma(c.nhwp, vadd(ni, nj), fsym);
-  const V da = vfma(c.nhwm, vsub(ni, nj), vmul(c.gm, vset<V>(p.F3w[P])));
+  const V ds = vfma(c.nhwp, np, fsym);
+  const V da = vfma(c.nhwm, nm, vmul(c.gm, vset<V>(p.F3w[P])));
   f[P] = vadd(f[P], vadd(ds, da));
   f[R] = vadd(f[R], vsub(ds, da));
 }
@@ -634,23 +673,24 @@ struct LeanCtx {
   V kb[3], kc[3], kr[3];
 };
 
-template <int Q, int I, class V>
-__device__ __forceinline__ void trt_pair_lean(const KParams& p, V (&f)[Q], const LeanCtx<V>& c) {
+template <int Q, int I, class V, class A>
+__device__ __forceinline__ void trt_pair_lean(const KParams& p, A& a, const LeanCtx<V>& c) {
   constexpr int P = prim(I), R = P == I ? I + 1 : I;
   constexpr int X = cx(P), Y = cy(P), Z = cz(P), K = csq(P) - 1;
   const V cu = cdot<X, Y, Z>(c.ux, c.uy, c.uz);
-  const V s = vadd(f[P], f[R]);
-  const V d = vsub(f[P], f[R]);
+  const V fP = a.template get<P>(), fR = a.template get<R>();
+  const V s = vadd(fP, fR);
+  const V d = vsub(fP, fR);
   const V S = vfma(c.hp, s, vfma(vmul(c.gp, vset<V>(p.F9w[P])), cu, vfma(c.kb[K], vmul(cu, cu), c.kc[K])));
   const V D = vfma(c.hm, d, vfma(c.kr[K], cu, vmul(c.gm, vset<V>(p.F3w[P]))));
-  f[P] = vadd(S, D);
-  f[R] = vsub(S, D);
+  a.template set<P>(vadd(S, D));
+  a.template set<R>(vsub(S, D));
 }
 
-template <int Q, class V, int... P>
-__device__ __forceinline__ void trt_pairs_lean(const KParams& p, V (&f)[Q], const LeanCtx<V>& c,
+template <int Q, class V, class A, int... P>
+__device__ __forceinline__ void trt_pairs_lean(const KParams& p, A& a, const LeanCtx<V>& c,
                                                std::integer_sequence<int, P...>) {
-  (trt_pair_lean<Q, 2 * P + 1, V>(p, f, c), ...);
+  (trt_pair_lean<Q, 2 * P + 1, V>(p, a, c), ...);
 }
 
 // sqrt of a non-negative value from the hardware reciprocal square root (x = 0 gives 0).
@@ -677,13 +717,13 @@ struct Macro {
   V pi[6], qn;
 };
 
-template <int Q, bool STRESS, class V>
-__device__ __forceinline__ Macro<V> macro(const KParams& p, const V (&f)[Q]) {
+template <int Q, bool STRESS, class V, class A>
+__device__ __forceinline__ Macro<V> macro_acc(const KParams& p, const A& a) {
   using Pairs = std::make_integer_sequence<int, (Q - 1) / 2>;
   using L = Lanes<V>;
   V m[10];
-  m[0] = f[0];
-  all_pair_moments<Q, V>(f, m, Pairs{});
+  m[0] = a.template get<0>();
+  all_pair_moments<Q, V>(a, m, Pairs{});
   Macro<V> M;
   M.drho = m[0];
   M.rho = vadd(M.drho, vset<V>(1.f));
@@ -710,6 +750,11 @@ __device__ __forceinline__ Macro<V> macro(const KParams& p, const V (&f)[Q]) {
   return M;
 }
 
+template <int Q, bool STRESS, class V>
+__device__ __forceinline__ Macro<V> macro(const KParams& p, const V (&f)[Q]) {
+  return macro_acc<Q, STRESS, V>(p, ArrPops<Q, V, const V>{f});
+}
+
 // Moments of one cell for the exports: the collision's macroscopic fields, so an export and
 // the statistics sampled inside a step see the same per-cell values.
 template <int Q>
@@ -725,6 +770,39 @@ __device__ __forceinline__ Mom<Q> moments(const KParams& p, const float (&f)[Q])
   m.uy = M.uy;
   m.uz = M.uz;
   return m;
+}
+
+// The lean TRT relaxation (half storage) of the populations behind accessor a, in place.
+template <int Q, class V, class A>
+__device__ __forceinline__ void relax_lean(const KParams& p, A& a, const Macro<V>& M, V wp, V wm) {
+  using Pairs = std::make_integer_sequence<int, (Q - 1) / 2>;
+  const V usq = vfma(M.uz, M.uz, vfma(M.uy, M.uy, vmul(M.ux, M.ux)));
+  const V uF = vfma(M.uz, vset<V>(p.F[2]), vfma(M.uy, vset<V>(p.F[1]), vmul(M.ux, vset<V>(p.F[0]))));
+  const V A_ = vfma(vmul(M.rho, vset<V>(-1.5f)), usq, M.drho);
+  const V nhwp = vmul(wp, vset<V>(-0.5f));
+  const V gp = vadd(nhwp, vset<V>(1.f)), gm = vadd(vmul(wm, vset<V>(-0.5f)), vset<V>(1.f));
+  const V gu3 = vmul(gp, vmul(uF, vset<V>(3.f)));
+  LeanCtx<V> c;
+  c.ux = M.ux;
+  c.uy = M.uy;
+  c.uz = M.uz;
+  c.gp = gp;
+  c.gm = gm;
+  c.hp = vfma(wp, vset<V>(-0.5f), vset<V>(0.5f));
+  c.hm = vfma(wm, vset<V>(-0.5f), vset<V>(0.5f));
+  const V wpA = vmul(wp, A_), wpB = vmul(wp, vmul(M.rho, vset<V>(4.5f))), wmr = vmul(wm, vmul(M.rho, vset<V>(3.f)));
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    const float w = (float)(k == 0 ? wgt_d<Q>(1) : k == 1 ? wgt_d<Q>(7) : wgt_d<Q>(19 % Q));
+    c.kb[k] = vmul(wpB, vset<V>(w));
+    c.kc[k] = vfma(wpA, vset<V>(w), vmul(gu3, vset<V>(-w)));
+    c.kr[k] = vmul(wmr, vset<V>(w));
+  }
+  {
+    constexpr float w0 = (float)wgt_d<Q>(0);
+    a.template set<0>(vfma(vadd(c.hp, c.hp), a.template get<0>(), vfma(wpA, vset<V>(w0), vmul(gu3, vset<V>(-w0)))));
+  }
+  trt_pairs_lean<Q, V>(p, a, c, Pairs{});
 }
 
 // TRT relaxation with Guo forcing at the rates omega+ (wp) and omega- (wm), in place.
@@ -760,27 +838,8 @@ __device__ __forceinline__ void relax(const KParams& p, V (&f)[Q], const Macro<V
     }
     trt_pairs<Q, V>(p, f, c, Pairs{});
   } else {
-    LeanCtx<V> c;
-    c.ux = M.ux;
-    c.uy = M.uy;
-    c.uz = M.uz;
-    c.gp = gp;
-    c.gm = gm;
-    c.hp = vfma(wp, vset<V>(-0.5f), vset<V>(0.5f));
-    c.hm = vfma(wm, vset<V>(-0.5f), vset<V>(0.5f));
-    const V wpA = vmul(wp, A), wpB = vmul(wp, vmul(M.rho, vset<V>(4.5f))), wmr = vmul(wm, vmul(M.rho, vset<V>(3.f)));
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-      const float w = (float)(k == 0 ? wgt_d<Q>(1) : k == 1 ? wgt_d<Q>(7) : wgt_d<Q>(19 % Q));
-      c.kb[k] = vmul(wpB, vset<V>(w));
-      c.kc[k] = vfma(wpA, vset<V>(w), vmul(gu3, vset<V>(-w)));
-      c.kr[k] = vmul(wmr, vset<V>(w));
-    }
-    {
-      constexpr float w0 = (float)wgt_d<Q>(0);
-      f[0] = vfma(vadd(c.hp, c.hp), f[0], vfma(wpA, vset<V>(w0), vmul(gu3, vset<V>(-w0))));
-    }
-    trt_pairs_lean<Q, V>(p, f, c, Pairs{});
+    ArrPops<Q, V> a{f};
+    relax_lean<Q, V>(p, a, M, wp, wm);
   }
 }
 
@@ -1056,19 +1115,39 @@ __device__ __forceinline__ void stat_values(const Macro<float>& M, float (&v)[NS
   v[9] = M.uy * M.uz;
 }
 
-// Sum of v over the warp (FP32) written by lane 0 to the warp's slot ws of row (y, z).
+// One round of a warp reduce-scatter: lanes with bit `bit` of their index set keep the upper
+// half of the N values (and receive their partner's upper half), the others the lower half;
+// N odd is padded with a zero.  Returns ceil(N / 2) partial sums.
+template <int N, int M = (N + 1) / 2>
+__device__ __forceinline__ void rs_round(const float (&in)[N], float (&out)[M], int bit) {
+  const bool hi = (threadIdx.x >> bit) & 1;
+#pragma unroll
+  for (int k = 0; k < M; k++) {
+    const float lo_v = in[k], hi_v = k + M < N ? in[k + M] : 0.f;
+    const float keep = hi ? hi_v : lo_v, send = hi ? lo_v : hi_v;
+    out[k] = keep + __shfl_xor_sync(0xffffffffu, send, 1 << bit);
+  }
+}
+
+// Sum of v over the warp (FP32), written to the warp's slot ws of row (y, z): a reduce-scatter
+// over lane bits 4, 3, 2, 1 leaves statistic k = b1 + 2 b2 + 3 b3 + 5 b4 (b_i the lane's
+// index bits; padding where that index is out of range) summed over the lane pairs (l, l^1),
+// which the last exchange completes; the even lane of each pair writes it.
 __device__ __forceinline__ void stat_warp_store(const KParams& p, int y, int z, int ws, int nws,
                                                 float (&v)[NSTAT]) {
-#pragma unroll
-  for (int k = 0; k < NSTAT; k++) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-  }
-  if ((threadIdx.x & 31) == 0) {
-    float* dst = p.stats_w + (((long long)z * p.ny + y) * nws + ws) * NSTAT;
-#pragma unroll
-    for (int k = 0; k < NSTAT; k++) dst[k] = v[k];
-  }
+  static_assert(NSTAT == 10, "the scatter below is laid out for 10 statistics");
+  float a[5], b[3], c[2], d[1];
+  rs_round<10>(v, a, 4);
+  rs_round<5>(a, b, 3);
+  rs_round<3>(b, c, 2);
+  rs_round<2>(c, d, 1);
+  const float s = d[0] + __shfl_xor_sync(0xffffffffu, d[0], 1);
+  const int lane = threadIdx.x & 31;
+  const int b1 = (lane >> 1) & 1, b2 = (lane >> 2) & 1, b3 = (lane >> 3) & 1, b4 = (lane >> 4) & 1;
+  const int j = b1 + 2 * b2;  // slot after round 2 (3 values)
+  const int k = j + 3 * b3;   // slot after round 1 (5 values)
+  if (!(lane & 1) && j < 3 && k < 5)
+    p.stats_w[(((long long)z * p.ny + y) * nws + ws) * NSTAT + k + 5 * b4] = s;
 }
 
 // Plane sums of the sampled statistics: sums[y * 10 + k] += sum over z and the nws warp
