@@ -33,13 +33,26 @@ static void step_mode_s(const KParams& p, int closure, const Launch& L, int coll
     else k_step<Q, S, CL_SMAG, LOAD, STORE, STATS, 2><<<L.grid, L.block, 0, L.stream>>>(p);
     return;
   }
-  // half storage: x-pairs, 64 x per warp; D3Q27 only with two-grid pull, where boundary lanes
-  // load by the rules instead of sending the warp to the one-cell code and the populations
-  // stay packed in registers through the collision (its AA form keeps the one-cell kernel)
-#ifndef LBM_H2_Q27
-#define LBM_H2_Q27 0
-#endif
-  if constexpr (sizeof(S) == 2 && (Q == 19 || (LBM_H2_Q27 && STORE == 2))) {
+  // half storage, D3Q27, gather step of two-grid pull without statistics: the x-pair step over
+  // the interior cells (populations packed in registers through the collision) and
+  // k_step_list over the cells the handle listed (rules, y/z wraps); the other D3Q27 half
+  // steps take the one-cell kernel
+  if constexpr (sizeof(S) == 2 && Q == 27 && LOAD == 2 && STORE == 2 && !STATS) {
+    if (p.split && coll == 0) {
+      dim3 g = L.grid;
+      g.x = (p.nxp + 63) / 64;
+      if (closure == CL_NONE) k_step_h2<Q, S, CL_NONE, 2, 2, false, true><<<g, L.block, 0, L.stream>>>(p);
+      else k_step_h2<Q, S, CL_SMAG, 2, 2, false, true><<<g, L.block, 0, L.stream>>>(p);
+      if (p.nblist > 0) {
+        const unsigned nb = (unsigned)((p.nblist + 127) / 128);
+        if (closure == CL_NONE) k_step_list<Q, S, CL_NONE><<<nb, 128, 0, L.stream>>>(p);
+        else k_step_list<Q, S, CL_SMAG><<<nb, 128, 0, L.stream>>>(p);
+      }
+      return;
+    }
+  }
+  // half storage, D3Q19: x-pairs, 64 x per warp
+  if constexpr (sizeof(S) == 2 && Q == 19) {
     dim3 g = L.grid;
     g.x = (p.nxp + 63) / 64;
     if (nws) *nws = (int)g.x;

@@ -11,6 +11,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/lbm.h"
 #include "lbm_launch.cuh"
@@ -35,6 +36,8 @@ struct lbm_s {
   double* sums = nullptr;     // 4 doubles (lbm_reduce)
   double* partial = nullptr;  // nz * ny * 10 doubles: per-row sums of the reductions
   float* stats_w = nullptr;   // per-warp plane statistics of sampling steps (allocated on first use)
+  int* blist = nullptr;       // cells the x-pair step leaves to k_step_list (see uses_blist)
+  long long nblist = 0;
   // CUDA graph of GRAPH_STEPS plain steps that lbm_step replays (captured on a private
   // stream, keyed by the kernel parameters of its first step and the streaming state)
   cudaStream_t cap = nullptr;
@@ -128,6 +131,10 @@ static KParams kparams(const lbm_s* h) {
   p.cls = h->cls;
   p.rules = h->rules;
   p.stats_w = h->stats_w;
+  p.blist = h->blist;
+  p.nblist = h->nblist;
+  p.split = h->q == 27 && h->prm.precision != LBM_F32 && h->prm.streaming == LBM_PULL &&
+            h->prm.collision == LBM_COLL_TRT && h->prm.closure != LBM_CLOSURE_MLP;
   {
     const size_t fbytes = (size_t)plane_alloc(h) * h->q * store_bytes(h->prm.precision);
     p.chk_lo[0] = (const char*)h->f;
@@ -286,6 +293,26 @@ __global__ void k_classify(const __grid_constant__ KParams p, uint8_t* cls, unsi
   }
 }
 
+// Cells of one (y, z) row that need boundary rules or a periodic y/z wrap: counted, then listed
+// in x order at the row's offset (one thread per row; a set-up pass).
+__device__ __forceinline__ bool listed_class(int c) { return c == CLS_BOUNDARY || c == CLS_WRAP; }
+
+__global__ void k_list_count(const uint8_t* cls, int nx, long long rows, int nxp, int* counts) {
+  const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  int n = 0;
+  for (int x = 0; x < nx; x++) n += listed_class(cls[r * nxp + x]);
+  counts[r] = n;
+}
+
+__global__ void k_list_fill(const uint8_t* cls, int nx, long long rows, int nxp, const long long* offsets, int* list) {
+  const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  long long o = offsets[r];
+  for (int x = 0; x < nx; x++)
+    if (listed_class(cls[r * nxp + x])) list[o++] = (int)(r * nxp + x);
+}
+
 // ---- accessors used by the other translation units (closure training) -------------------------
 KParams lbm_internal_kparams(lbm_handle h) { return kparams(h); }
 
@@ -408,11 +435,51 @@ int lbm_stencil(int q, int* c, double* w) {
 
 const char* lbm_last_error(lbm_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
+// Handles whose pull step splits into the x-pair kernel over interior cells and k_step_list over
+// the listed ones: half storage, two-grid pull, TRT without the learned closure, D3Q27 (where
+// the warps that hold an inflow or outflow cell would otherwise diverge through the boundary
+// loads of one lane; measured 32.2k MLUPS one-cell vs 30.0k unsplit pairs on the bluff body).
+static bool uses_blist(const lbm_s* h) { return kparams(h).split != 0; }
+
+// The list of cells needing rules or a y/z wrap, in row order (rebuilt with the classes).
+static lbm_status build_blist(lbm_handle h) {
+  if (h->blist) CUDA_TRY(h, cudaFreeAsync(h->blist, h->stream));
+  h->blist = nullptr;
+  h->nblist = 0;
+  const long long rows = (long long)h->ny * h->nz;
+  long long* offsets = nullptr;
+  CUDA_TRY(h, cudaMallocAsync((void**)&offsets, (size_t)rows * sizeof(long long), h->stream));
+  int* counts = reinterpret_cast<int*>(offsets);  // counts first, then the offsets over them
+  const unsigned blocks = (unsigned)((rows + 255) / 256);
+  k_list_count<<<blocks, 256, 0, h->stream>>>(h->cls, h->nx, rows, h->nxp, counts);
+  CUDA_TRY(h, cudaGetLastError());
+  std::vector<int> hc((size_t)rows);
+  std::vector<long long> ho((size_t)rows);
+  CUDA_TRY(h, cudaMemcpyAsync(hc.data(), counts, (size_t)rows * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  long long total = 0;
+  for (long long r = 0; r < rows; r++) {
+    ho[(size_t)r] = total;
+    total += hc[(size_t)r];
+  }
+  if (total > 0) {
+    CUDA_TRY(h, cudaMemcpyAsync(offsets, ho.data(), (size_t)rows * sizeof(long long), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaMallocAsync((void**)&h->blist, (size_t)total * sizeof(int), h->stream));
+    k_list_fill<<<blocks, 256, 0, h->stream>>>(h->cls, h->nx, rows, h->nxp, offsets, h->blist);
+    CUDA_TRY(h, cudaGetLastError());
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));  // ho must outlive the copy
+  }
+  CUDA_TRY(h, cudaFreeAsync(offsets, h->stream));
+  h->nblist = total;
+  return LBM_OK;
+}
+
 static lbm_status launch_classify(lbm_handle h) {
   KParams p = kparams(h);
   Launch L = launch_cfg(h);
   k_classify<<<L.grid, L.block, 0, h->stream>>>(p, h->cls, h->rules, h->q);
   CUDA_TRY(h, cudaGetLastError());
+  if (uses_blist(h)) return build_blist(h);
   return LBM_OK;
 }
 
@@ -430,6 +497,7 @@ lbm_status lbm_destroy(lbm_handle h) {
   if (h->stats_w) cudaFreeAsync(h->stats_w, h->stream);
   if (h->stats) cudaFreeAsync(h->stats, h->stream);
   if (h->mlp) cudaFreeAsync(h->mlp, h->stream);
+  if (h->blist) cudaFreeAsync(h->blist, h->stream);
   cudaStreamSynchronize(h->stream);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->cap) cudaStreamDestroy(h->cap);

@@ -193,12 +193,20 @@ __device__ __forceinline__ float2 collide_pair(const KParams& p, uint32_t (&h)[Q
   }
 }
 
-template <int Q, class S, int CL, int LOAD, bool STATS>
+// SPLIT (gather step of a handle with a cell list, no statistics): only the interior cells are
+// updated here, the listed ones by k_step_list.  A lane with one interior cell loads both cells'
+// words (the other cell's sources, one x further, stay inside the arrays) and stores one half.
+template <int Q, class S, int CL, int LOAD, bool STATS, bool SPLIT>
 __device__ __forceinline__ void pair_pull(const KParams& p, int x, int y, int z, int cell, int clsA, int clsB,
                                           bool fast, float (&v)[NSTAT]) {
   constexpr bool PACKED = Q == 27 ? LBM_H2_PACKED27 : LBM_H2_PACKED19;
+  static_assert(!SPLIT || (LOAD == 2 && !STATS), "the split runs the gather step without statistics");
   uint32_t h[Q];
   unsigned oa = 0, ob = 0;
+  if (SPLIT) {
+    if (clsA != CLS_INTERIOR && clsB != CLS_INTERIOR) return;
+    fast = true;
+  }
   if (fast) {
 #pragma unroll
     for (int i = 0; i < Q; i++) {
@@ -221,10 +229,11 @@ __device__ __forceinline__ void pair_pull(const KParams& p, int x, int y, int z,
 #pragma unroll
     for (int i = 0; i < Q; i++) h[i] = hs[i];
   }
-  outflow_fix_packed<Q>(p, 64 * blockIdx.x, h, oa, ob);
+  if (!SPLIT) outflow_fix_packed<Q>(p, 64 * blockIdx.x, h, oa, ob);
   Macro<float2> M2;
   const float2 rho = collide_pair<Q, S, CL, PACKED>(p, h, STATS ? &M2 : nullptr);
-  const bool liveA = clsA != CLS_SKIP, liveB = clsB != CLS_SKIP;
+  const bool liveA = SPLIT ? clsA == CLS_INTERIOR : clsA != CLS_SKIP;
+  const bool liveB = SPLIT ? clsB == CLS_INTERIOR : clsB != CLS_SKIP;
   if ((liveA && !(rho.x > 0.f && rho.x < 3.0e38f)) || (liveB && !(rho.y > 0.f && rho.y < 3.0e38f)))
     atomicOr(p.status, 1);
   if (STATS) {
@@ -257,7 +266,7 @@ __device__ __forceinline__ void pair_pull(const KParams& p, int x, int y, int z,
 #endif
 // STATS: also write the plane statistics of the state this step starts from (warp slot
 // blockIdx.x of each row, ceil(nxp/64) slots per row).
-template <int Q, class S, int CL, int LOAD, int STORE, bool STATS = false>
+template <int Q, class S, int CL, int LOAD, int STORE, bool STATS = false, bool SPLIT = false>
 __global__ void __launch_bounds__(128, Q == 27 ? LBM_H2_MINB27 : LBM_H2_MINB) k_step_h2(const __grid_constant__ KParams p) {
   static_assert(sizeof(S) == 2, "two 16-bit populations per word");
   const int x = 2 * (blockIdx.x * 32 + threadIdx.x);
@@ -278,7 +287,7 @@ __global__ void __launch_bounds__(128, Q == 27 ? LBM_H2_MINB27 : LBM_H2_MINB) k_
 #pragma unroll
   for (int k = 0; k < NSTAT; k++) v[k] = 0.f;
   if constexpr (STORE == 2) {
-    pair_pull<Q, S, CL, LOAD, STATS>(p, x, y, z, cell, clsA, clsB, fast, v);
+    pair_pull<Q, S, CL, LOAD, STATS, SPLIT>(p, x, y, z, cell, clsA, clsB, fast, v);
   } else if (__all_sync(0xffffffffu, fast)) {
     uint32_t h[Q];
 #pragma unroll
@@ -365,6 +374,59 @@ __global__ void __launch_bounds__(128, Q == 27 ? LBM_H2_MINB27 : LBM_H2_MINB) k_
     pair_fallback<Q, S, CL, LOAD, STORE, STATS>(p, x, y, z, cell, clsA, clsB, v);
   }
   if (STATS) stat_warp_store(p, y, z, blockIdx.x, (p.nxp + 63) / 64, v);
+}
+
+// ---- the listed cells of a split pull step ---------------------------------------------------
+// What cell (x, y, z) receives in direction i (a runtime direction) in the gather step, as
+// load_state gives it: the zero-gradient outflow copy of the list kernel, whose cells have no
+// x-neighbour in their warp.  Never called for an outflow cell itself.
+template <class S>
+__device__ __noinline__ float pull_one(const KParams& p, int x, int y, int z, int i) {
+  const int cell = cidx(p, x, y, z);
+  const int cls = cls_at(p, cell);
+  if (cls == CLS_SKIP) return 0.f;
+  const int dx = cx(i), dy = cy(i), dz = cz(i);
+  // the periodic-wrapped source x - c_i (as Nbr: x and y always wrap, z across periodic faces)
+  int sx = x - dx, sy = y - dy, sz = z - dz;
+  sx = sx < 0 ? sx + p.nx : sx >= p.nx ? sx - p.nx : sx;
+  sy = sy < 0 ? sy + p.ny : sy >= p.ny ? sy - p.ny : sy;
+  if (sz < 0 && p.face[4] == FACE_PERIODIC) sz += p.nz;
+  if (sz >= p.nz && p.face[5] == FACE_PERIODIC) sz -= p.nz;
+  const int src = (sz * p.ny + sy) * p.nxp + sx;
+  if (cls == CLS_INTERIOR || cls == CLS_WRAP) return ldp<S>(p, plane_ptr<S>(p, i) + src);
+  const int k = (int)((rule_at(p, cell) >> (2 * i)) & 3);
+  if (k == R_STREAM) return ldp<S>(p, plane_ptr<S>(p, i) + src);
+  if (k == R_SPECIAL) {
+    int pl, ce;
+    resolve_special(p, x, y, z, i, pl, ce);
+    return ldp<S>(p, plane_ptr<S>(p, opp(pl)) + ce);
+  }
+  float v = ldp<S>(p, plane_ptr<S>(p, opp(i)) + cell);
+  if (k == R_INFLOW) v = rnd<S>(v + p.inflow_term[i]);
+  return v;
+}
+
+// One listed cell per thread: the one-cell gather step (rules, outflow copy, collision of the
+// storage precision's form, own-cell store).
+template <int Q, class S, int CL>
+__global__ void __launch_bounds__(128) k_step_list(const __grid_constant__ KParams p) {
+  const long long t = blockIdx.x * 128ll + threadIdx.x;
+  if (t >= p.nblist) return;
+  const int cell = p.blist[t];
+  const int x = cell % p.nxp, r = cell / p.nxp, y = r % p.ny, z = r / p.ny;
+  const int cls = cls_at(p, cell);
+  float f[Q];
+  unsigned outmask;
+  load_state<Q, S, 2>(p, x, y, z, cell, cls, f, outmask);
+  if (outmask) {
+#pragma unroll
+    for (int i = 0; i < Q; i++)
+      if (outmask & (1u << i)) f[i] = pull_one<S>(p, x - 1, y, z, i);
+  }
+  if (cls == CLS_SKIP) return;
+  const float rho = collide<Q, CL, float, acc_form<S>>(p, f, nullptr);
+  if (!(rho > 0.f && rho < 3.0e38f)) atomicOr(p.status, 1);
+  store_state<Q, S, 2>(p, x, y, z, cell, cls, f);
 }
 
 }  // namespace lbm

@@ -84,6 +84,12 @@ struct KParams {
   // zero-gradient outflow copy, resolved from the geometry alone)
   const unsigned long long* rules;
   const float* mlp;      // MLP parameters (bf16 values widened to float), device
+  // two-grid pull, half storage, D3Q27: the cells that need boundary rules or a periodic y/z
+  // wrap (classes BOUNDARY and WRAP), padded cell indices in row order; the x-pair step then
+  // updates the interior cells and k_step_list these (null: no split)
+  const int* blist;
+  long long nblist;
+  int split;             // the pull gather step runs as the interior x-pair step + k_step_list
   int* status;           // bit 0: non-finite or non-positive density seen; bits 1, 2: a
                          // bounded wait of the learned-closure step gave up (once, twice)
   int wait_polls;        // polls of the closure step's first wait for each tile's MMA
