@@ -285,17 +285,32 @@ __global__ void k_classify(const __grid_constant__ KParams p, uint8_t* cls, unsi
     if (c == CLS_INTERIOR && flag_at(p, cidx(p, s[0], s[1], s[2])) != CELL_FLUID) c = CLS_BOUNDARY;
   }
   if (c == CLS_INTERIOR && wrap_yz) c = CLS_WRAP;
-  cls[cell] = (uint8_t)c;
+  int xf = 0;
   if (c == CLS_BOUNDARY) {
     unsigned long long r = 0;
     for (int i = 1; i < q; i++) r |= (unsigned long long)rule_of(p, x, y, z, i) << (2 * i);
     rules[cell] = r;
+    // an inflow or outflow face cell whose directions crossing the face are its only rules
+    const bool in_face = x == 0 && p.face[0] == FACE_INFLOW;
+    const bool out_face = x == p.nx - 1 && p.face[1] == FACE_OUTFLOW;
+    if (p.nx >= 4 && (in_face || out_face)) {
+      const int dc = in_face ? 1 : -1, want = in_face ? R_INFLOW : R_SPECIAL;
+      bool simple = true;
+      for (int i = 1; i < q; i++) {
+        const int k = (int)((r >> (2 * i)) & 3);
+        const int sy = y - cy(i), sz = z - cz(i);
+        simple = simple && sy >= 0 && sy < p.ny && sz >= 0 && sz < p.nz && k == (cx(i) == dc ? want : R_STREAM);
+      }
+      if (simple) xf = CLS_XFACE;
+    }
   }
+  cls[cell] = (uint8_t)(c | xf);
 }
 
-// Cells of one (y, z) row that need boundary rules or a periodic y/z wrap: counted, then listed
-// in x order at the row's offset (one thread per row; a set-up pass).
-__device__ __forceinline__ bool listed_class(int c) { return c == CLS_BOUNDARY || c == CLS_WRAP; }
+// Cells of one (y, z) row that need boundary rules or a periodic y/z wrap, except the simple
+// inflow/outflow face cells (CLS_XFACE, updated by the x-pair kernel): counted, then listed in
+// x order at the row's offset (one thread per row; a set-up pass).
+__device__ __forceinline__ bool listed_class(int c) { return c == CLS_BOUNDARY || c == CLS_WRAP; }  // x-face cells excluded
 
 __global__ void k_list_count(const uint8_t* cls, int nx, long long rows, int nxp, int* counts) {
   const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;

@@ -57,6 +57,11 @@ enum : int { FACE_PERIODIC = 0, FACE_WALL = 1, FACE_FREESLIP = 2, FACE_INFLOW = 
 // periodic wrap in x), wrap fluid (as interior, but a source wraps across a periodic y or z
 // face), boundary fluid (some source needs a rule), and everything that is not updated.
 enum : int { CLS_INTERIOR = 0, CLS_BOUNDARY = 1, CLS_SKIP = 2, CLS_WRAP = 3 };
+// Class byte = class | CLS_XFACE: a boundary cell on an inflow (-x) or outflow (+x) face whose
+// only rules are those of the directions crossing that face (every other source a fluid cell
+// inside the lattice).  The split half-storage pull step updates such cells in its x-pair
+// kernel; everywhere else they are plain boundary cells (cls_at drops the bit).
+constexpr int CLS_MASK = 0x0f, CLS_XFACE = 0x10;
 enum : int { CL_NONE = 0, CL_SMAG = 1, CL_MLP = 2 };
 enum : int { K_STREAM = 0, K_BB = 1, K_INFLOW = 2, K_OUTCOPY = 3 };
 enum : int { R_STREAM = 0, R_BB = 1, R_INFLOW = 2, R_SPECIAL = 3 };
@@ -138,7 +143,7 @@ __device__ __forceinline__ bool chk(const KParams& p, const void* a, int bytes, 
 }
 
 __device__ __forceinline__ int cls_at(const KParams& p, long long cell) {
-  return chk(p, p.cls + cell, 1, CHK_CLS) ? p.cls[cell] : CLS_SKIP;
+  return chk(p, p.cls + cell, 1, CHK_CLS) ? (p.cls[cell] & CLS_MASK) : CLS_SKIP;
 }
 __device__ __forceinline__ int flag_at(const KParams& p, long long cell) {
   return chk(p, p.flags + cell, 1, CHK_FLAGS) ? p.flags[cell] : CELL_SOLID;
@@ -364,6 +369,21 @@ __device__ __forceinline__ void load_state(const KParams& p, int x, int y, int z
       }
     }
   }
+}
+
+// A cell off every lattice face (1 <= x, y, z <= n-2): the gather of an interior cell reads
+// inside the arrays whatever the cell's class, so the step kernels issue it together with the
+// class load instead of after it, and keep it if the cell is interior.
+__device__ __forceinline__ bool off_faces(const KParams& p, int x, int y, int z) {
+  return x >= 1 && x < p.nx - 1 && y >= 1 && y < p.ny - 1 && z >= 1 && z < p.nz - 1;
+}
+
+// The interior-cell gather of load_state (PAR 1: AA swapped layout, 2: pull) for a cell off the
+// faces (no x wrap there).
+template <int Q, class S, int PAR>
+__device__ __forceinline__ void gather_interior(const KParams& p, int cell, float (&f)[Q]) {
+#pragma unroll
+  for (int i = 0; i < Q; i++) f[i] = ldp<S>(p, static_cast<const S*>(PAR == 2 ? p.gb[i] : p.ga[i]) + cell);
 }
 
 // Zero-gradient outflow: lane x = nx-1 takes the incoming c_x = -1 populations of lane x-1.
@@ -1202,10 +1222,17 @@ static __global__ void __launch_bounds__(256) k_stats_total(const float* stats_w
 template <int Q, class S, int CL, int LOAD, int STORE, bool STATS = false, int COLL = 0>
 __global__ void __launch_bounds__(128, Q == 19 ? (COLL == 1 ? 8 : LBM_STEP_MINB19) : LBM_STEP_MINB27)
     k_step(const __grid_constant__ KParams p) {
-  LBM_CELL_COORDS
+  const int x = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (y >= p.ny) return;  // whole warp
+  const int cell = cidx(p, x, y, z);
   float f[Q];
-  unsigned outmask;
-  load_state<Q, S, LOAD>(p, x, y, z, cell, cls, f, outmask);
+  unsigned outmask = 0;
+  const bool early = LOAD != 0 && off_faces(p, x, y, z);
+  if (early) gather_interior<Q, S, LOAD>(p, cell, f);  // in flight with the class load below
+  const int cls = x < p.nx ? cls_at(p, cell) : CLS_SKIP;
+  if (!(early && cls == CLS_INTERIOR)) load_state<Q, S, LOAD>(p, x, y, z, cell, cls, f, outmask);
   outflow_fix<Q>(p, x, f, outmask);
   if (!STATS && cls == CLS_SKIP) return;
   float v[NSTAT];
