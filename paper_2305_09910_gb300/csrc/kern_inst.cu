@@ -37,7 +37,7 @@ static void step_mode_s(const KParams& p, int closure, const Launch& L, int coll
   // the interior cells (populations packed in registers through the collision) and
   // k_step_list over the cells the handle listed (rules, y/z wraps); the other D3Q27 half
   // steps take the one-cell kernel
-  if constexpr (sizeof(S) == 2 && Q == 27 && LOAD == 2 && STORE == 2 && !STATS) {
+  if constexpr (sizeof(S) == 2 && (Q == 27 || LBM_SPLIT19) && LOAD == 2 && STORE == 2 && !STATS) {
     if (p.split && coll == 0) {
       dim3 g = L.grid;
       g.x = (p.nxp + 63) / 64;
@@ -139,6 +139,7 @@ static cudaError_t mlp_one(const KParams& p, cudaStream_t stream, int nsm) {
     if (blocks_per_sm < 1) blocks_per_sm = 1;
   }
   const long long ntiles = (long long)(p.nxp / 32) * ((p.ny + 3) / 4) * p.nz;
+  if (ntiles >= (1ll << 31)) return cudaErrorInvalidValue;  // tile indices are 32-bit in the kernel
   const long long groups = (ntiles + MLP_NG - 1) / MLP_NG;
   const long long grid = std::min<long long>(groups, (long long)nsm * blocks_per_sm);
   kern<<<(unsigned)grid, dim3(32, 4 * MLP_NG, 1), smem, stream>>>(p, ntiles);

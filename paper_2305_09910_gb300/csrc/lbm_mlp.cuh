@@ -7,10 +7,11 @@
 // a 128 x 8 operand tile in shared memory.  One thread issues tcgen05.mma.kind::tf32
 // (M = 128, N = 32, K = 8) against [W1 | b1] into 32 columns of tensor memory and commits it
 // to an mbarrier; each warp reads its 32 TMEM lanes with tcgen05.ld (lane t = cell t's 32
-// pre-activations), applies the GELU and writes row t of the 128 x 32 layer-2 operand, again
-// in TF32.  Four more MMAs (K = 4 x 8) against W2 overwrite the same TMEM columns; the
-// epilogue (bias b2, GELU, 32 -> 1 output layer, softplus) stays one thread per cell and the
-// thread finishes the TRT update with the learned C_s^2.  Weights are bfloat16 values, exact
+// pre-activations), applies the GELU and writes row t of the 128 x 40 layer-2 operand, again
+// in TF32 (columns 32..39 hold a constant 1, carrying b2, and zeros, written once per CTA).
+// Five more MMAs (K = 5 x 8) against [W2 | b2 | 0] overwrite the same TMEM columns; the
+// epilogue (GELU, 32 -> 1 output layer, softplus) stays one thread per cell and the thread
+// finishes the TRT update with the learned C_s^2.  Weights are bfloat16 values, exact
 // in TF32.
 //
 // The CTA is persistent and holds MLP_NG independent groups of 128 threads (4 warps each),
@@ -115,15 +116,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int k = 0; k < 16; k++) v[k] = __uint_as_float(r[k]);
 }
 
-constexpr int MLP_K1 = 8;  // layer-1 operand columns: the 7 features and a constant 1
+constexpr int MLP_K1 = 8;   // layer-1 operand columns: the 7 features and a constant 1
+constexpr int MLP_K2 = 40;  // layer-2 operand columns: 32 hidden values, a constant 1 and 7 zeros
 
 struct MlpSmem {
-  float A[MLP_NG][MLP_TILE * MLP_NH];  // layer-2 operand per group (hidden layer 1, TF32; 16 KB each)
+  float A[MLP_NG][MLP_TILE * MLP_K2];  // layer-2 operand per group (hidden layer 1, 1; TF32; 20 KB each)
   float X[MLP_NG][MLP_TILE * MLP_K1];  // layer-1 operand per group (features and 1, TF32; 4 KB each)
-  float B[MLP_NH * MLP_NH];            // W2 (4 KB)
+  float B[MLP_NH * MLP_K2];            // [W2 | b2 | 0] (5 KB)
   float B1[MLP_NH * MLP_K1];           // [W1 | b1] (1 KB)
-  // the output-layer epilogue as pairs of hidden units (j, j+1) for the packed FP32x2 pipe
-  float2 b2[MLP_NH / 2], W3[MLP_NH / 2];
+  // the output layer as pairs of hidden units (j, j+1) for the packed FP32x2 pipe
+  float2 W3[MLP_NH / 2];
   float b3;
   unsigned long long bar[MLP_NG];
   uint32_t tmem;
@@ -155,16 +157,22 @@ __global__ void __launch_bounds__(128 * MLP_NG, 1) k_step_mlp(const __grid_const
     const float* W2 = b1 + MLP_NH;
     const float* b2 = W2 + MLP_NH * MLP_NH;
     const float* W3 = b2 + MLP_NH;
-    for (int k = tc; k < MLP_NH * MLP_NH; k += 128 * MLP_NG) {
-      const int n = k / MLP_NH, kk = k % MLP_NH;  // output n, input kk
-      sm.B[core_off<MLP_NH>(n, kk)] = W2[k];
+    for (int k = tc; k < MLP_NH * MLP_K2; k += 128 * MLP_NG) {
+      const int n = k / MLP_K2, kk = k % MLP_K2;  // output n, input kk (kk = 32: the bias)
+      sm.B[core_off<MLP_K2>(n, kk)] = kk < MLP_NH ? W2[n * MLP_NH + kk] : kk == MLP_NH ? b2[n] : 0.f;
+    }
+    // the constant columns of every group's layer-2 operand: 1 (carrying b2), then zeros
+    for (int k = tc; k < MLP_NG * MLP_TILE; k += 128 * MLP_NG) {
+      float* A = sm.A[k / MLP_TILE];
+      const int r = k % MLP_TILE;
+      *reinterpret_cast<uint4*>(A + core_off<MLP_K2>(r, MLP_NH)) = make_uint4(__float_as_uint(1.f), 0u, 0u, 0u);
+      *reinterpret_cast<uint4*>(A + core_off<MLP_K2>(r, MLP_NH + 4)) = make_uint4(0u, 0u, 0u, 0u);
     }
     for (int k = tc; k < MLP_NH * MLP_K1; k += 128 * MLP_NG) {
       const int n = k / MLP_K1, kk = k % MLP_K1;  // output n, input kk (kk = 7: the bias)
       sm.B1[core_off<MLP_K1>(n, kk)] = kk < MLP_NIN ? W1[n * MLP_NIN + kk] : b1[n];
     }
     if (tc < MLP_NH / 2) {
-      sm.b2[tc] = make_float2(b2[2 * tc], b2[2 * tc + 1]);
       sm.W3[tc] = make_float2(W3[2 * tc], W3[2 * tc + 1]);
     }
     if (tc == 0) {
@@ -217,25 +225,31 @@ __global__ void __launch_bounds__(128 * MLP_NG, 1) k_step_mlp(const __grid_const
         mma_tf32(dcol, umma_desc(x0, 32 * MLP_K1), umma_desc(b10, 32 * MLP_K1), 0);
       } else {
 #pragma unroll
-        for (int kk = 0; kk < MLP_NH / 8; kk++)  // K = 8 per instruction: 2 core matrices = 256 B
-          mma_tf32(dcol, umma_desc(a0 + kk * 256, 32 * MLP_NH), umma_desc(b0 + kk * 256, 32 * MLP_NH), kk);
+        for (int kk = 0; kk < MLP_K2 / 8; kk++)  // K = 8 per instruction: 2 core matrices = 256 B
+          mma_tf32(dcol, umma_desc(a0 + kk * 256, 32 * MLP_K2), umma_desc(b0 + kk * 256, 32 * MLP_K2), kk);
       }
       mma_commit(bar);
     }
   };
-  for (long long tile = (long long)blockIdx.x * MLP_NG + g; tile < ntiles; tile += (long long)gridDim.x * MLP_NG) {
-    const int bx = (int)(tile % nbx);
-    const long long r = tile / nbx;
-    const int by = (int)(r % nby);
-    const int z = (int)(r / nby);
+  // tile coordinates in 32-bit unsigned arithmetic (the launcher keeps ntiles below 2^31): a
+  // 64-bit division by a runtime value costs far more instructions
+  const unsigned nt = (unsigned)ntiles, unbx = (unsigned)nbx, unby = (unsigned)nby;
+  for (unsigned tile = blockIdx.x * MLP_NG + g; tile < nt; tile += gridDim.x * MLP_NG) {
+    const unsigned r = tile / unbx;
+    const int bx = (int)(tile - r * unbx);
+    const unsigned zq = r / unby;
+    const int by = (int)(r - zq * unby);
+    const int z = (int)zq;
     const int x = bx * 32 + threadIdx.x;
     const int y = by * 4 + (warp & 3);
     const bool row = y < p.ny;  // warp-uniform
     const int cell = row ? cidx(p, x, y, z) : 0;
-    const int cls = (row && x < p.nx) ? cls_at(p, cell) : CLS_SKIP;
     float f[Q];
-    unsigned outmask;
-    load_state<Q, S, LOAD>(p, x, y, z, cell, cls, f, outmask);
+    unsigned outmask = 0;
+    const bool early = LOAD != 0 && row && off_faces(p, x, y, z);
+    if (early) gather_interior<Q, S, LOAD>(p, cell, f);  // in flight with the class load below
+    const int cls = (row && x < p.nx) ? cls_at(p, cell) : CLS_SKIP;
+    if (!(early && cls == CLS_INTERIOR)) load_state<Q, S, LOAD>(p, x, y, z, cell, cls, f, outmask);
     outflow_fix<Q>(p, x, f, outmask);
     const Macro<float> M = macro<Q, true, float>(p, f);
     // layer 1 on the tensor core: row t of the feature tile = the 7 clipped, scaled features
@@ -261,23 +275,21 @@ __global__ void __launch_bounds__(128 * MLP_NG, 1) k_step_mlp(const __grid_const
       for (int c = 0; c < 4; c++) {
         const float2 g01 = gelu_v(make_float2(v[4 * c], v[4 * c + 1]));
         const float2 g23 = gelu_v(make_float2(v[4 * c + 2], v[4 * c + 3]));
-        *reinterpret_cast<uint4*>(A + core_off<MLP_NH>(t, 16 * half + 4 * c)) =
+        *reinterpret_cast<uint4*>(A + core_off<MLP_K2>(t, 16 * half + 4 * c)) =
             make_uint4(to_tf32(g01.x), to_tf32(g01.y), to_tf32(g23.x), to_tf32(g23.y));
       }
     }
     issue(false);  // (its barrier also orders every lane's layer-1 reads before the overwrite)
     if (!wait_mma()) break;
-    // epilogue: this thread's 32 accumulator columns, bias, GELU, output layer (pairs)
+    // epilogue: this thread's 32 accumulator columns (b2 included), GELU, output layer (pairs)
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
     for (int half = 0; half < 2; half++) {
       float v[16];
       tmem_ld16(tl + 16 * half, v);
 #pragma unroll
-      for (int pr = 0; pr < 8; pr++) {
-        const float2 a2 = vadd(make_float2(v[2 * pr], v[2 * pr + 1]), sm.b2[8 * half + pr]);
-        acc = vfma(sm.W3[8 * half + pr], gelu_v(a2), acc);
-      }
+      for (int pr = 0; pr < 8; pr++)
+        acc = vfma(sm.W3[8 * half + pr], gelu_v(make_float2(v[2 * pr], v[2 * pr + 1])), acc);
     }
     const float yv = sm.b3 + (acc.x + acc.y);
     const float cs2 = fmaxf(softplus_f(yv) * p.cs2 * 1.4426950408889634f, p.cs2_min);  // / ln 2
