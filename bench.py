@@ -533,6 +533,8 @@ def main():
                     help="closure of the main line (profiling runs of the learned-closure kernel)")
     ap.add_argument("--workload", default="channel", choices=["channel", "bluffbody"],
                     help="main-line workload (profiling runs of the D3Q27 bluff-body kernel)")
+    ap.add_argument("--collision", default="trt", choices=["trt", "mrt", "reg"],
+                    help="collision of the channel main line (profiling runs of the MRT / regularised steps)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -558,7 +560,8 @@ def main():
     ncell = nx * ny * nz
     channel = args.workload == "channel"
     if channel:
-        lat, par = _channel_lattice(nx, ny, nz, args.form, closure=args.closure, streaming=args.streaming)
+        lat, par = _channel_lattice(nx, ny, nz, args.form, closure=args.closure, streaming=args.streaming,
+                                    collision=args.collision)
         if args.closure == "mlp":
             lbm.lbm_set_closure_f32(lat.h, _closure_params(), 600.0, 3000.0)
             lbm.lbm_set_closure_floor(lat.h, 0.1)
@@ -576,7 +579,8 @@ def main():
     total_ms = _barrier_max(dist, total_ms)
     value = world * ncell * args.steps / (total_ms * 1e-3) / 1e6
     q = 19 if channel else 27
-    tag = f"k_step_q{q}_{args.form}_{args.closure}_{args.streaming}_{args.workload}{nx}"
+    coll = "" if args.collision == "trt" else f"_{args.collision}"
+    tag = f"k_step_q{q}_{args.form}_{args.closure}{coll}_{args.streaming}_{args.workload}{nx}"
     traffic = _profile_traffic(tag)
     roof = _roofline(ncell, lat.bytes_per_update, per, peak, peak_kind, traffic)
     mass = lat.reduce()[0]
@@ -639,10 +643,11 @@ def main():
             fl.close()
             torch.cuda.empty_cache()
 
-    if (nx, ny, nz, args.form, args.streaming, args.closure, channel) == (512, 256, 256, "f32", "pull", "smag", True):
+    if (nx, ny, nz, args.form, args.streaming, args.closure, args.collision, channel) == \
+            (512, 256, 256, "f32", "pull", "smag", "trt", True):
         workload = WORKLOAD
     elif channel:
-        workload = (f"turbulent channel {nx}x{ny}x{nz} D3Q19 TRT+" +
+        workload = (f"turbulent channel {nx}x{ny}x{nz} D3Q19 {args.collision.upper()}+" +
                     ("learned closure" if args.closure == "mlp" else "Smagorinsky") + f" {args.form} ({args.streaming})")
     else:
         workload = f"bluff body {nx}x{ny}x{nz} D3Q27 TRT+Smagorinsky {args.form} ({args.streaming})"

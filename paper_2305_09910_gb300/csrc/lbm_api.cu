@@ -133,7 +133,7 @@ static KParams kparams(const lbm_s* h) {
   p.stats_w = h->stats_w;
   p.blist = h->blist;
   p.nblist = h->nblist;
-  p.split = h->q == 27 && h->prm.precision != LBM_F32 && h->prm.streaming == LBM_PULL &&
+  p.split = (h->q == 27 || LBM_SPLIT19) && h->prm.precision != LBM_F32 && h->prm.streaming == LBM_PULL &&
             h->prm.collision == LBM_COLL_TRT && h->prm.closure != LBM_CLOSURE_MLP;
   {
     const size_t fbytes = (size_t)plane_alloc(h) * h->q * store_bytes(h->prm.precision);
@@ -452,8 +452,8 @@ const char* lbm_last_error(lbm_handle h) { return h ? h->err.c_str() : g_create_
 
 // Handles whose pull step splits into the x-pair kernel over interior cells and k_step_list over
 // the listed ones: half storage, two-grid pull, TRT without the learned closure, D3Q27 (where
-// the warps that hold an inflow or outflow cell would otherwise diverge through the boundary
-// loads of one lane; measured 32.2k MLUPS one-cell vs 30.0k unsplit pairs on the bluff body).
+// the warps that hold a boundary lane would otherwise diverge through its boundary loads;
+// measured 32.2k MLUPS one-cell vs 30.0k unsplit pairs on the bluff body, 43.7k split).
 static bool uses_blist(const lbm_s* h) { return kparams(h).split != 0; }
 
 // The list of cells needing rules or a y/z wrap, in row order (rebuilt with the classes).

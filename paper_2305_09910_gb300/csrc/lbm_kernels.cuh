@@ -62,6 +62,13 @@ enum : int { CLS_INTERIOR = 0, CLS_BOUNDARY = 1, CLS_SKIP = 2, CLS_WRAP = 3 };
 // inside the lattice).  The split half-storage pull step updates such cells in its x-pair
 // kernel; everywhere else they are plain boundary cells (cls_at drops the bit).
 constexpr int CLS_MASK = 0x0f, CLS_XFACE = 0x10;
+
+// The split half-storage pull step (x-pair kernel over interior cells + k_step_list) for D3Q27
+// always, for D3Q19 with LBM_SPLIT19 (its boundary cells are whole rows and planes, which the
+// unsplit pair kernel already serves without divergence).
+#ifndef LBM_SPLIT19
+#define LBM_SPLIT19 0
+#endif
 enum : int { CL_NONE = 0, CL_SMAG = 1, CL_MLP = 2 };
 enum : int { K_STREAM = 0, K_BB = 1, K_INFLOW = 2, K_OUTCOPY = 3 };
 enum : int { R_STREAM = 0, R_BB = 1, R_INFLOW = 2, R_SPECIAL = 3 };
