@@ -251,7 +251,8 @@ lbm_status lbm_init_equilibrium(lbm_handle h, const float* rho, const float* u, 
  * after enqueuing; instability is reported by lbm_sync.  Once the state is steady, several
  * steps go into one launch: on small lattices (up to 2^17 padded cells for two-grid pull,
  * 2^15 for AA) cooperative launches of up to 4096 steps separated by grid-wide barriers,
- * above that replays of a CUDA graph of 8 steps; the result has the bits of n single steps.
+ * above that, up to 2^22 padded cells, replays of a CUDA graph of 8 steps, and single
+ * launches on larger lattices; the result has the bits of n single steps.
  * LBM_ECUDA on a handle that lbm_sync has declared unusable. */
 lbm_status lbm_step(lbm_handle h, int64_t n);
 
@@ -259,9 +260,9 @@ lbm_status lbm_step(lbm_handle h, int64_t n);
  * (failure detection; the paper has no counterpart).  LBM_EUNSTABLE: a non-finite or
  * non-positive density (the state is kept for inspection).  LBM_ECUDA: a learned-closure step
  * gave up its bounded wait for a tile's tensor-core result (an event that should not occur;
- * the step stopped early and the state is incomplete, but the device is usable once the
- * state is set again); or that step's second, draining wait gave up as well, after which the
- * tensor-core work may still have been running when the kernel left: the handle is then marked
+ * the step then waited again, with a longer bound, for the tensor core to finish and completed
+ * its tiles); or that second wait gave up as well, after which the tensor-core work may still
+ * have been running when the results were read and the kernel left: the handle is then marked
  * unusable and every later step returns LBM_ECUDA; or, in a library built with
  * LBM_BOUNDS_CHECK (liblbm_check.so), a kernel skipped an access outside its array. */
 lbm_status lbm_sync(lbm_handle h);
@@ -270,8 +271,8 @@ lbm_status lbm_sync(lbm_handle h);
  * closure step makes in its first wait for each tile's tensor-core result before it gives up;
  * default 2^22 (far longer than any MMA takes), polls = -1 restores it, 0 makes every first
  * wait give up at once, which drives the timeout path of lbm_sync without a device fault
- * (the step still waits, with the full bound, for the tensor core to finish before its
- * kernel leaves).  EINVAL outside [-1, 2^22].  Failure detection; the paper has no
+ * (the step still waits, with the full bound, for the tensor core to finish before it reads
+ * the results).  EINVAL outside [-1, 2^22].  Failure detection; the paper has no
  * counterpart. */
 lbm_status lbm_debug_set_wait_polls(lbm_handle h, int64_t polls);
 

@@ -812,8 +812,15 @@ static void advance_state(lbm_handle h) {
   }
 }
 
+// Lattices above this many padded cells step as single launches: a step takes long enough there
+// (0.1 ms at 2^22 cells) that a replay saves nothing, while a capture costs milliseconds.
+#ifndef LBM_GRAPH_MAX_CELLS
+#define LBM_GRAPH_MAX_CELLS (1ll << 22)
+#endif
+
 static bool graph_ready(lbm_handle h) {
   if (h->graphs_off || h->prm.closure == LBM_CLOSURE_MLP) return false;
+  if ((long long)h->nxp * h->ny * h->nz > LBM_GRAPH_MAX_CELLS) return false;
   if (h->prm.streaming == LBM_PULL ? h->parity != 2 : (h->prm.face_bc[1] == LBM_FACE_OUTFLOW && h->nat_valid))
     return false;
   KParams p = kparams(h);
@@ -1149,7 +1156,7 @@ lbm_status lbm_sync(lbm_handle h) {
   }
   if (*h->status_host & 2)
     return fail(h, LBM_ECUDA,
-                "a learned-closure step gave up waiting for its tensor-core result; the state is incomplete");
+                "a learned-closure step gave up waiting for its tensor-core result (then waited with the full bound)");
 #ifdef LBM_BOUNDS_CHECK
   int bad = 0;
   CUDA_TRY(h, cudaMemcpy(&bad, h->chk_bad, sizeof(int), cudaMemcpyDeviceToHost));

@@ -22,12 +22,12 @@
 // 16-byte core matrices: element (r, k) of a 4-byte-element tile of K columns at
 // (r / 8) * 32 K + (k / 4) * 128 + (r % 8) * 16 + (k % 4) * 4 bytes, i.e. leading-dimension
 // byte offset 128 (K-adjacent core matrices) and stride byte offset 32 K (8-row groups).
-// Every mbarrier wait is bounded.  When a group's first wait for a tile's MMA gives up
-// (after p.wait_polls polls), the group sets status bit 1, waits again with the full bound so
-// that the tensor core has finished with its accumulator and operand tiles, and leaves its
-// tile loop; the CTA then frees its tensor memory and returns.  Should that second wait give
-// up too, status bit 2 records that the MMA may still be running: the launch's results and
-// the tensor memory it held are then undefined.
+// Every mbarrier wait is bounded.  When a thread's first wait for a tile's MMA gives up (after
+// p.wait_polls polls), it sets status bit 1 and waits again with the full bound, so that the
+// tensor core has finished with its accumulator and operand tiles before it reads them; the
+// tile is then completed as usual.  Should that second wait give up too, status bit 2 records
+// that the MMA may still be running: the launch's results and the tensor memory it held are
+// then undefined.
 #pragma once
 
 #include "lbm_kernels.cuh"
@@ -132,14 +132,6 @@ struct MlpSmem {
 };
 
 __device__ __forceinline__ void group_sync(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
-__device__ __forceinline__ bool group_any(int id, bool v) {
-  uint32_t r;
-  asm volatile("{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, %2, 128, q;\n selp.u32 %0, 1, 0, p;\n}\n"
-               : "=r"(r)
-               : "r"((uint32_t)v), "r"(id)
-               : "memory");
-  return r != 0;
-}
 
 // LOAD / STORE modes as in k_step.  Grid: persistent CTAs whose groups walk tiles (bx, by, z)
 // of (nxp/32) x ceil(ny/4) x nz; block (32, 4 MLP_NG).
@@ -201,17 +193,18 @@ __global__ void __launch_bounds__(128 * MLP_NG, 1) k_step_mlp(const __grid_const
   const int nbx = p.nxp / 32, nby = (p.ny + 3) / 4;
   const int gbar = 1 + g;  // named barrier of the group (0 is __syncthreads)
   uint32_t phase = 0;
-  // Waits for the group's MMA; false (after the tensor core has finished) if the wait gave up.
-  auto wait_mma = [&]() -> bool {
-    const bool timed_out = !mbar_wait_parity(bar, phase, p.wait_polls);
-    if (group_any(gbar, timed_out)) {
-      if (t == 0) atomicOr(p.status, 2);
+  // Waits for the group's MMA.  A thread whose first wait gives up records it (status bit 1)
+  // and waits again with the full bound, so that the tensor core has finished with the
+  // accumulator and operand tiles before the thread goes on; every thread then keeps the
+  // group's barrier sequence (no thread leaves the loop on its own).  Should that wait give up
+  // too, status bit 2 records that the MMA may still be running.
+  auto wait_mma = [&]() {
+    if (!mbar_wait_parity(bar, phase, p.wait_polls)) {
+      atomicOr(p.status, 2);
       if (!mbar_wait_parity(bar, phase, MBAR_POLLS)) atomicOr(p.status, 4);
-      return false;
     }
     phase ^= 1u;
     tc_fence_after();
-    return true;
   };
   // Makes the group's shared-memory operand rows visible to the tensor core, then has thread 0
   // of the group issue the layer's MMAs and commit them to the group's mbarrier.
@@ -265,7 +258,7 @@ __global__ void __launch_bounds__(128 * MLP_NG, 1) k_step_mlp(const __grid_const
           make_uint4(to_tf32(xin[4]), to_tf32(xin[5]), to_tf32(xin[6]), __float_as_uint(1.f));
     }
     issue(true);
-    if (!wait_mma()) break;
+    wait_mma();
     // GELU of the 32 pre-activations (this thread's TMEM lane), TF32, row t of the layer-2 tile
 #pragma unroll
     for (int half = 0; half < 2; half++) {
@@ -280,7 +273,7 @@ __global__ void __launch_bounds__(128 * MLP_NG, 1) k_step_mlp(const __grid_const
       }
     }
     issue(false);  // (its barrier also orders every lane's layer-1 reads before the overwrite)
-    if (!wait_mma()) break;
+    wait_mma();
     // epilogue: this thread's 32 accumulator columns (b2 included), GELU, output layer (pairs)
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll

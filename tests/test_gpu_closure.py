@@ -221,9 +221,11 @@ def test_filter2_matches_oracle():
 
 def test_closure_wait_timeout_is_reported_and_the_device_stays_usable():
     """Failure detection without a device fault: with a first-wait limit of 0 polls every tile
-    of the tensor-core closure step gives up waiting for its MMA at once; the step still lets
-    the tensor core finish before the kernel leaves, lbm_sync reports LBM_ECUDA, and after the
-    limit is restored and the state set again the handle steps to the bits of a fresh one."""
+    of the tensor-core closure step gives up waiting for its MMA at once.  Each thread then
+    waits again, with the full bound, for the tensor core to finish before it reads the
+    results, so the step still completes its tiles: lbm_sync reports LBM_ECUDA, the populations
+    have the bits of a normal step, and after the limit is restored and the state set again the
+    handle steps to the bits of a fresh one."""
     from paper_2305_09910_gb300 import inputs, lbm
 
     p = _bf16_round(_params(46))
@@ -232,18 +234,21 @@ def test_closure_wait_timeout_is_reported_and_the_device_stays_usable():
     lat = lbm.Lattice(nx, ny, nz, tau=0.52, closure="mlp", cs_smag=0.1, faces=FACES_CHANNEL)
     lbm.lbm_set_closure_f32(lat.h, p, 100.0, 10.0)
     lat.init_equilibrium(rho, u)
+    fresh = lbm.Lattice(nx, ny, nz, tau=0.52, closure="mlp", cs_smag=0.1, faces=FACES_CHANNEL)
+    lbm.lbm_set_closure_f32(fresh.h, p, 100.0, 10.0)
+    fresh.init_equilibrium(rho, u)
     lbm.lbm_debug_set_wait_polls(lat.h, 0)
     lat.step(1)
     with pytest.raises(lbm.LbmError) as e:
         lat.sync()
     assert e.value.status == lbm.LBM_ECUDA and "gave up waiting" in str(e.value), e.value
+    fresh.step(1)
+    assert np.array_equal(lat.get_populations(), fresh.get_populations())
     lbm.lbm_debug_set_wait_polls(lat.h, -1)
     lat.init_equilibrium(rho, u)
+    fresh.init_equilibrium(rho, u)
     lat.step(3)
     lat.sync()
-    fresh = lbm.Lattice(nx, ny, nz, tau=0.52, closure="mlp", cs_smag=0.1, faces=FACES_CHANNEL)
-    lbm.lbm_set_closure_f32(fresh.h, p, 100.0, 10.0)
-    fresh.init_equilibrium(rho, u)
     fresh.step(3)
     assert np.array_equal(lat.get_populations(), fresh.get_populations())
     with pytest.raises(lbm.LbmError):
