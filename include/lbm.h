@@ -306,7 +306,8 @@ lbm_status lbm_reduce(lbm_handle h, double out[4]);
  * turbulent channel of Sec. 5.1 assesses: the symmetry and regularity of the solution and the
  * shear stresses along the wall normal, i.e. mean and fluctuation profiles over the
  * homogeneous x-z planes.  Per-cell values are float32 (the moments of lbm_moments); sums are
- * FP64. */
+ * FP64.  lbm_stats_reset also allocates, once per handle, the device scratch that the
+ * sampling steps of lbm_step_stats write their per-warp partial sums to. */
 lbm_status lbm_stats_reset(lbm_handle h);
 lbm_status lbm_stats_sample(lbm_handle h);
 lbm_status lbm_stats_get(lbm_handle h, double* out, int64_t* nsamples);

@@ -756,12 +756,21 @@ static void advance_state(lbm_handle h);
 
 // n steps; with every > 0 the plane statistics of the state each step k (k % every == 0)
 // starts from are added to the accumulated sums, inside that step's kernel where it can.
+// The per-warp scratch of sampling steps; lbm_stats_reset allocates it ahead of the steps (the
+// first allocation from the stream-ordered pool maps memory, which takes a while).
+static lbm_status ensure_stats_w(lbm_handle h) {
+  if (!fused_stats(h) || h->stats_w) return LBM_OK;
+  const size_t slots = (size_t)((h->nxp + 31) / 32) * h->ny * h->nz;
+  CUDA_TRY(h, cudaMallocAsync((void**)&h->stats_w, slots * 10 * sizeof(float), h->stream));
+  return LBM_OK;
+}
+
 static lbm_status run_steps(lbm_handle h, int64_t n, int64_t every) {
   if (h->prm.closure == LBM_CLOSURE_MLP && !h->mlp_set)
     return fail(h, LBM_ESTATE, "MLP closure selected but lbm_set_closure was not called");
-  if (every > 0 && fused_stats(h) && !h->stats_w) {
-    const size_t slots = (size_t)((h->nxp + 31) / 32) * h->ny * h->nz;
-    CUDA_TRY(h, cudaMallocAsync((void**)&h->stats_w, slots * 10 * sizeof(float), h->stream));
+  if (every > 0) {
+    const lbm_status s = ensure_stats_w(h);
+    if (s != LBM_OK) return s;
   }
   KParams p = kparams(h);
   for (int64_t k = 0; k < n; k++) {
@@ -1271,7 +1280,7 @@ lbm_status lbm_stats_reset(lbm_handle h) {
   if (!h) return fail(nullptr, LBM_EINVAL, "handle is NULL");
   CUDA_TRY(h, cudaMemsetAsync(h->stats, 0, (size_t)h->ny * LBM_STATS_K * sizeof(double), h->stream));
   h->nsamples = 0;
-  return LBM_OK;
+  return ensure_stats_w(h);
 }
 
 lbm_status lbm_stats_sample(lbm_handle h) {

@@ -212,11 +212,13 @@ __device__ __forceinline__ void pair_loads(const KParams& p, int x, int cell, ui
     } else {
       const S* base = static_cast<const S*>(p.gb[i]);
       if (cx(i) == 0) {
-        h[i] = ld32(p, base + cell);
+        h[i] = chk(p, base + cell, 4, CHK_POP) ? ldh_u32(base + cell) : 0u;
       } else {
         int a, b;
         xsrc(cx(i), p, x, cell, a, b);
-        h[i] = ld16(p, base + a) | (ld16(p, base + b) << 16);
+        const uint32_t lo = chk(p, base + a, 2, CHK_POP) ? ldh_u16(base + a) : 0u;
+        const uint32_t hi = chk(p, base + b, 2, CHK_POP) ? ldh_u16(base + b) : 0u;
+        h[i] = lo | (hi << 16);
       }
     }
   }

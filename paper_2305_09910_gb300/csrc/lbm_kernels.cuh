@@ -182,6 +182,33 @@ template <class S>
 __device__ __forceinline__ float ldp(const KParams& p, const S* a) {
   return chk(p, a, (int)sizeof(S), CHK_POP) ? ld<S>(a) : 0.f;
 }
+// Gather loads of the step kernels with the 256-byte L2 prefetch size: the L2 fetches the
+// aligned 256 bytes around a warp's 128-byte row segment of one direction, whose other half the
+// neighbouring block in x reads next.  Measured 0.5-1.2 % faster than plain loads on the pull
+// and AA steps (a 128-byte prefetch size gains nothing, the non-coherent path nothing more, and
+// bypassing L1 costs up to 15 %: the shifted directions of x-neighbouring warps share lines).
+__device__ __forceinline__ float ldh_f32(const float* a) {
+  float v;
+  asm volatile("ld.global.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(a));
+  return v;
+}
+__device__ __forceinline__ uint32_t ldh_u32(const void* a) {
+  uint32_t v;
+  asm volatile("ld.global.L2::256B.u32 %0, [%1];" : "=r"(v) : "l"(a));
+  return v;
+}
+__device__ __forceinline__ uint32_t ldh_u16(const void* a) {
+  unsigned short v;
+  asm volatile("ld.global.L2::256B.u16 %0, [%1];" : "=h"(v) : "l"(a));
+  return v;
+}
+// A checked gather load (the hinted form for FP32 storage).
+template <class S>
+__device__ __forceinline__ float ldg_pop(const KParams& p, const S* a) {
+  if constexpr (sizeof(S) == 4) return chk(p, a, 4, CHK_POP) ? ldh_f32(reinterpret_cast<const float*>(a)) : 0.f;
+  else return ldp<S>(p, a);
+}
+
 template <class S>
 __device__ __forceinline__ void stp(const KParams& p, S* a, float v) {
   if (chk(p, a, (int)sizeof(S), CHK_POP)) st<S>(a, v);
@@ -390,7 +417,7 @@ __device__ __forceinline__ bool off_faces(const KParams& p, int x, int y, int z)
 template <int Q, class S, int PAR>
 __device__ __forceinline__ void gather_interior(const KParams& p, int cell, float (&f)[Q]) {
 #pragma unroll
-  for (int i = 0; i < Q; i++) f[i] = ldp<S>(p, static_cast<const S*>(PAR == 2 ? p.gb[i] : p.ga[i]) + cell);
+  for (int i = 0; i < Q; i++) f[i] = ldg_pop<S>(p, static_cast<const S*>(PAR == 2 ? p.gb[i] : p.ga[i]) + cell);
 }
 
 // Zero-gradient outflow: lane x = nx-1 takes the incoming c_x = -1 populations of lane x-1.
@@ -1190,10 +1217,11 @@ static __global__ void __launch_bounds__(256) k_stats_total(const float* stats_w
   double acc[NSTAT];
 #pragma unroll
   for (int k = 0; k < NSTAT; k++) acc[k] = 0.0;
-  const long long n = (long long)nz * nws;
-  for (long long r = threadIdx.x; r < n; r += blockDim.x) {
-    const long long z = r / nws, ws = r % nws;
-    const float* src = stats_w + ((z * ny + y) * nws + ws) * NSTAT;
+  const int n = nz * nws;  // below 2^31: a warp slot per 32 cells of a lattice under 2^31 cells
+#pragma unroll 4
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    const int z = r / nws, ws = r - z * nws;
+    const float* src = stats_w + (((long long)z * ny + y) * nws + ws) * NSTAT;
 #pragma unroll
     for (int k = 0; k < NSTAT; k++) acc[k] += (double)src[k];
   }
