@@ -33,10 +33,10 @@ static void step_mode_s(const KParams& p, int closure, const Launch& L, int coll
     else k_step<Q, S, CL_SMAG, LOAD, STORE, STATS, 2><<<L.grid, L.block, 0, L.stream>>>(p);
     return;
   }
-  // half storage, D3Q27, gather step of two-grid pull without statistics: the x-pair step over
-  // the interior cells (populations packed in registers through the collision) and
-  // k_step_list over the cells the handle listed (rules, y/z wraps); the other D3Q27 half
-  // steps take the one-cell kernel
+  // half storage, gather step of two-grid pull without statistics (both stencils; D3Q19 unless
+  // built with LBM_SPLIT19=0): the x-pair step over the interior cells (populations packed in
+  // registers through the collision for D3Q27) and k_step_list over the cells the handle listed
+  // (rules, wraps); the other D3Q27 half steps take the one-cell kernel
   if constexpr (sizeof(S) == 2 && (Q == 27 || LBM_SPLIT19) && LOAD == 2 && STORE == 2 && !STATS) {
     if (p.split && coll == 0) {
       dim3 g = L.grid;

@@ -37,6 +37,7 @@ struct lbm_s {
   double* partial = nullptr;  // nz * ny * 10 doubles: per-row sums of the reductions
   float* stats_w = nullptr;   // per-warp plane statistics of sampling steps (allocated on first use)
   int* blist = nullptr;       // cells the x-pair step leaves to k_step_list (see uses_blist)
+  void* blaux = nullptr;      // their source table: q x nblist cells (int32), then q x nblist codes
   long long nblist = 0;
   // CUDA graph of GRAPH_STEPS plain steps that lbm_step replays (captured on a private
   // stream, keyed by the kernel parameters of its first step and the streaming state)
@@ -132,7 +133,10 @@ static KParams kparams(const lbm_s* h) {
   p.rules = h->rules;
   p.stats_w = h->stats_w;
   p.blist = h->blist;
+  p.bltab = static_cast<const int*>(h->blaux);
+  p.blcode = h->blaux ? static_cast<const uint8_t*>(h->blaux) + 4 * (size_t)h->q * h->nblist : nullptr;
   p.nblist = h->nblist;
+  p.pstride = plane_alloc(h);
   p.split = (h->q == 27 || LBM_SPLIT19) && h->prm.precision != LBM_F32 && h->prm.streaming == LBM_PULL &&
             h->prm.collision == LBM_COLL_TRT && h->prm.closure != LBM_CLOSURE_MLP;
   {
@@ -328,6 +332,24 @@ __global__ void k_list_fill(const uint8_t* cls, int nx, long long rows, int nxp,
     if (listed_class(cls[r * nxp + x])) list[o++] = (int)(r * nxp + x);
 }
 
+// The source table of the listed cells (list_source for every direction; a set-up pass after
+// the fill, one thread per listed cell).
+__global__ void k_list_table(const __grid_constant__ KParams p, const int* list, long long n, int q, int* tab,
+                             uint8_t* code) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int cell = list[t];
+  const int x = cell % p.nxp, r = cell / p.nxp, y = r % p.ny, z = r / p.ny;
+  const int cls = cls_at(p, cell);
+  const unsigned long long rule = cls == CLS_BOUNDARY ? rule_at(p, cell) : 0ull;
+  for (int i = 0; i < q; i++) {
+    int src, c;
+    list_source(p, x, y, z, cell, cls, rule, i, src, c);
+    tab[i * n + t] = src;
+    code[i * n + t] = (uint8_t)c;
+  }
+}
+
 // ---- accessors used by the other translation units (closure training) -------------------------
 KParams lbm_internal_kparams(lbm_handle h) { return kparams(h); }
 
@@ -459,7 +481,9 @@ static bool uses_blist(const lbm_s* h) { return kparams(h).split != 0; }
 // The list of cells needing rules or a y/z wrap, in row order (rebuilt with the classes).
 static lbm_status build_blist(lbm_handle h) {
   if (h->blist) CUDA_TRY(h, cudaFreeAsync(h->blist, h->stream));
+  if (h->blaux) CUDA_TRY(h, cudaFreeAsync(h->blaux, h->stream));
   h->blist = nullptr;
+  h->blaux = nullptr;
   h->nblist = 0;
   const long long rows = (long long)h->ny * h->nz;
   long long* offsets = nullptr;
@@ -480,7 +504,13 @@ static lbm_status build_blist(lbm_handle h) {
   if (total > 0) {
     CUDA_TRY(h, cudaMemcpyAsync(offsets, ho.data(), (size_t)rows * sizeof(long long), cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(h, cudaMallocAsync((void**)&h->blist, (size_t)total * sizeof(int), h->stream));
+    CUDA_TRY(h, cudaMallocAsync(&h->blaux, (size_t)total * h->q * 5, h->stream));
     k_list_fill<<<blocks, 256, 0, h->stream>>>(h->cls, h->nx, rows, h->nxp, offsets, h->blist);
+    CUDA_TRY(h, cudaGetLastError());
+    int* tab = static_cast<int*>(h->blaux);
+    KParams p = kparams(h);
+    k_list_table<<<(unsigned)((total + 127) / 128), 128, 0, h->stream>>>(
+        p, h->blist, total, h->q, tab, reinterpret_cast<uint8_t*>(tab + (size_t)h->q * total));
     CUDA_TRY(h, cudaGetLastError());
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));  // ho must outlive the copy
   }
@@ -513,6 +543,7 @@ lbm_status lbm_destroy(lbm_handle h) {
   if (h->stats) cudaFreeAsync(h->stats, h->stream);
   if (h->mlp) cudaFreeAsync(h->mlp, h->stream);
   if (h->blist) cudaFreeAsync(h->blist, h->stream);
+  if (h->blaux) cudaFreeAsync(h->blaux, h->stream);
   cudaStreamSynchronize(h->stream);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->cap) cudaStreamDestroy(h->cap);

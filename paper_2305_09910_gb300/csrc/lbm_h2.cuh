@@ -433,56 +433,74 @@ __global__ void __launch_bounds__(128, Q == 27 ? LBM_H2_MINB27 : LBM_H2_MINB) k_
 }
 
 // ---- the listed cells of a split pull step ---------------------------------------------------
-// What cell (x, y, z) receives in direction i (a runtime direction) in the gather step, as
-// load_state gives it: the zero-gradient outflow copy of the list kernel, whose cells have no
-// x-neighbour in their warp.  Never called for an outflow cell itself.
-template <class S>
-__device__ __noinline__ float pull_one(const KParams& p, int x, int y, int z, int i) {
-  const int cell = cidx(p, x, y, z);
-  const int cls = cls_at(p, cell);
-  if (cls == CLS_SKIP) return 0.f;
-  const int dx = cx(i), dy = cy(i), dz = cz(i);
-  // the periodic-wrapped source x - c_i (as Nbr: x and y always wrap, z across periodic faces)
-  int sx = x - dx, sy = y - dy, sz = z - dz;
-  sx = sx < 0 ? sx + p.nx : sx >= p.nx ? sx - p.nx : sx;
-  sy = sy < 0 ? sy + p.ny : sy >= p.ny ? sy - p.ny : sy;
-  if (sz < 0 && p.face[4] == FACE_PERIODIC) sz += p.nz;
-  if (sz >= p.nz && p.face[5] == FACE_PERIODIC) sz -= p.nz;
-  const int src = (sz * p.ny + sy) * p.nxp + sx;
-  if (cls == CLS_INTERIOR || cls == CLS_WRAP) return ldp<S>(p, plane_ptr<S>(p, i) + src);
-  const int k = (int)((rule_at(p, cell) >> (2 * i)) & 3);
-  if (k == R_STREAM) return ldp<S>(p, plane_ptr<S>(p, i) + src);
+// A listed cell reads each incoming population through a table built with the list: for
+// direction i, the cell the value is read from and a code byte holding the plane (bits 0-4),
+// LT_INFLOW (the moving-wall term is added and the sum rounded to the storage precision, as
+// for a bounce-back from a moving wall) or LT_ZERO (the value is 0).  The entry is what
+// load_state of the gather step and its zero-gradient outflow copy read.
+constexpr int LT_INFLOW = 0x40, LT_ZERO = 0x80;
+
+// The table entry of direction i of the cell at `cell` with class cls and rule word r; false
+// (and no entry) for a zero-gradient outflow copy, which reads what the upstream cell receives.
+__device__ inline bool list_source_at(const KParams& p, int x, int y, int z, int cell, int cls, unsigned long long r,
+                                      int i, int& src, int& code) {
+  src = cell;
+  code = LT_ZERO;
+  if (cls == CLS_SKIP) return true;  // the upstream cell of an outflow copy is not fluid: 0
+  Nbr nb;
+  nb.init(p, x, y, z);
+  src = nb.src(p, i);
+  code = i;
+  if (cls == CLS_INTERIOR || cls == CLS_WRAP) return true;
+  const int k = (int)((r >> (2 * i)) & 3);
+  if (k == R_STREAM) return true;
   if (k == R_SPECIAL) {
     int pl, ce;
-    resolve_special(p, x, y, z, i, pl, ce);
-    return ldp<S>(p, plane_ptr<S>(p, opp(pl)) + ce);
+    if (resolve_special(p, x, y, z, i, pl, ce) == K_OUTCOPY) return false;
+    src = ce;
+    code = opp(pl);
+    return true;
   }
-  float v = ldp<S>(p, plane_ptr<S>(p, opp(i)) + cell);
-  if (k == R_INFLOW) v = rnd<S>(v + p.inflow_term[i]);
-  return v;
+  src = cell;  // bounce-back from the own cell (moving wall: plus the inflow term)
+  code = opp(i) | (k == R_INFLOW ? LT_INFLOW : 0);
+  return true;
 }
 
-// One listed cell per thread: the one-cell gather step (rules, outflow copy, collision of the
-// storage precision's form, own-cell store).
+// The table entry of direction i of a listed cell (set-up): an outflow copy takes the entry of
+// the upstream cell x - 1, which is never an outflow cell itself.
+__device__ inline void list_source(const KParams& p, int x, int y, int z, int cell, int cls, unsigned long long r,
+                                   int i, int& src, int& code) {
+  if (list_source_at(p, x, y, z, cell, cls, r, i, src, code)) return;
+  const int cu = cidx(p, x - 1, y, z);
+  const int cl = cls_at(p, cu);
+  if (!list_source_at(p, x - 1, y, z, cu, cl, cl == CLS_BOUNDARY ? rule_at(p, cu) : 0ull, i, src, code)) {
+    src = cell;  // not reached (x - 1 is off the outflow face)
+    code = LT_ZERO;
+  }
+}
+
+// One listed cell per thread: loads through the table, the collision of the storage
+// precision's form, own-cell store (the one-cell gather step's bits).
 template <int Q, class S, int CL>
 __global__ void __launch_bounds__(128) k_step_list(const __grid_constant__ KParams p) {
   const long long t = blockIdx.x * 128ll + threadIdx.x;
   if (t >= p.nblist) return;
   const int cell = p.blist[t];
-  const int x = cell % p.nxp, r = cell / p.nxp, y = r % p.ny, z = r / p.ny;
-  const int cls = cls_at(p, cell);
+  const S* base = plane_ptr<S>(p, 0);
   float f[Q];
-  unsigned outmask;
-  load_state<Q, S, 2>(p, x, y, z, cell, cls, f, outmask);
-  if (outmask) {
 #pragma unroll
-    for (int i = 0; i < Q; i++)
-      if (outmask & (1u << i)) f[i] = pull_one<S>(p, x - 1, y, z, i);
+  for (int i = 0; i < Q; i++) {
+    const long long e = i * p.nblist + t;
+    const int src = p.bltab[e];
+    const int code = p.blcode[e];
+    float v = 0.f;
+    if (!(code & LT_ZERO)) v = ldp<S>(p, base + (code & 31) * p.pstride + src);
+    if (code & LT_INFLOW) v = rnd<S>(v + p.inflow_term[i]);
+    f[i] = v;
   }
-  if (cls == CLS_SKIP) return;
   const float rho = collide<Q, CL, float, acc_form<S>>(p, f, nullptr);
   if (!(rho > 0.f && rho < 3.0e38f)) atomicOr(p.status, 1);
-  store_state<Q, S, 2>(p, x, y, z, cell, cls, f);
+  store_state<Q, S, 2>(p, 0, 0, 0, cell, CLS_BOUNDARY, f);
 }
 
 }  // namespace lbm

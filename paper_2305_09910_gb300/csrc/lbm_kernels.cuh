@@ -64,10 +64,10 @@ enum : int { CLS_INTERIOR = 0, CLS_BOUNDARY = 1, CLS_SKIP = 2, CLS_WRAP = 3 };
 constexpr int CLS_MASK = 0x0f, CLS_XFACE = 0x10;
 
 // The split half-storage pull step (x-pair kernel over interior cells + k_step_list) for D3Q27
-// always, for D3Q19 with LBM_SPLIT19 (its boundary cells are whole rows and planes, which the
-// unsplit pair kernel already serves without divergence).
+// always, for D3Q19 with LBM_SPLIT19 (on by default: the FP16 channel measured 77.4 % of the copy
+// bandwidth split against 74.7 % with the boundary rows and planes in the pair kernel).
 #ifndef LBM_SPLIT19
-#define LBM_SPLIT19 0
+#define LBM_SPLIT19 1
 #endif
 enum : int { CL_NONE = 0, CL_SMAG = 1, CL_MLP = 2 };
 enum : int { K_STREAM = 0, K_BB = 1, K_INFLOW = 2, K_OUTCOPY = 3 };
@@ -100,7 +100,12 @@ struct KParams {
   // wrap (classes BOUNDARY and WRAP), padded cell indices in row order; the x-pair step then
   // updates the interior cells and k_step_list these (null: no split)
   const int* blist;
+  // per direction i and listed cell t (index i nblist + t): the cell its incoming population
+  // is read from, and a code byte: the plane (bits 0-4), LT_INFLOW, LT_ZERO (see k_step_list)
+  const int* bltab;
+  const uint8_t* blcode;
   long long nblist;
+  long long pstride;     // elements from one population plane to the next
   int split;             // the pull gather step runs as the interior x-pair step + k_step_list
   int* status;           // bit 0: non-finite or non-positive density seen; bits 1, 2: a
                          // bounded wait of the learned-closure step gave up (once, twice)

@@ -50,11 +50,11 @@ def test_multi_step_launches_match_single_launches(name, streaming, precision, c
 
 
 @pytest.mark.parametrize("name,streaming,precision", [("channel19", "pull", "f32"), ("channel19", "aa", "f16"),
-                                                     ("tunnel27", "pull", "f16")])
+                                                     ("channel19", "pull", "f16"), ("tunnel27", "pull", "f16")])
 def test_graph_replays_on_a_larger_lattice_match_single_launches(name, streaming, precision):
     # 160 x 128 x 128 = 2.6 M cells: above the multi-step limits, below the graph limit, so
-    # lbm_step replays graphs (for the D3Q27 half-storage pull step, graphs of the x-pair and
-    # the boundary-list kernels)
+    # lbm_step replays graphs (for the half-storage pull steps, graphs of the x-pair and the
+    # boundary-list kernels)
     a, b = _pair(CASES[name], streaming, precision, "trt", size=(160, 128, 128))
     try:
         for n in (24, 9):

@@ -465,12 +465,13 @@ def test_pull_two_grid_matches_oracle(name):
 
 
 @pytest.mark.parametrize("precision", ["f32", "f16", "bf16"])
-@pytest.mark.parametrize("name,nx", [("tunnel19", None), ("tunnel27", None), ("tunnel27", 46)])
+@pytest.mark.parametrize("name,nx", [("tunnel19", None), ("tunnel19", 46), ("tunnel27", None), ("tunnel27", 46)])
 def test_pull_and_aa_agree_bit_for_bit(precision, name, nx):
     """AA (one cell per thread, or D3Q19 x-pairs) and two-grid pull give the same bits.  For
-    D3Q27 half storage the pull gather step is the split one (interior and simple inflow/outflow
+    half storage the pull gather step is the split one (interior and simple inflow/outflow
     face cells as x-pairs, the listed boundary cells in their own kernel) and AA the one-cell
-    kernel; odd and even nx put the outflow cell first or second in its lane."""
+    kernel (D3Q27) or the unsplit x-pair kernel (D3Q19); odd and even nx put the outflow cell
+    first or second in its lane."""
     from paper_2305_09910_gb300 import lbm
 
     case = dict(CASES[name])
