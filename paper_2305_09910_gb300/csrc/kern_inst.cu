@@ -17,6 +17,11 @@ namespace lbm {
 // stats: also write the warp-slot plane statistics of the starting state (p.stats_w); *nws
 // receives the number of warp slots per row.  coll: 0 TRT, 1 MRT (D3Q19, one cell per thread),
 // 2 regularised (one cell per thread).
+// listed cells up to which a split step runs them in its x-pair grid
+#ifndef LBM_LIST_FUSE_MAX
+#define LBM_LIST_FUSE_MAX (1ll << 18)
+#endif
+
 template <int Q, class S, int LOAD, int STORE, bool STATS>
 static void step_mode_s(const KParams& p, int closure, const Launch& L, int coll, int* nws) {
   if constexpr (Q == 19) {
@@ -35,15 +40,23 @@ static void step_mode_s(const KParams& p, int closure, const Launch& L, int coll
   }
   // half storage, gather step of two-grid pull without statistics (both stencils; D3Q19 unless
   // built with LBM_SPLIT19=0): the x-pair step over the interior cells (populations packed in
-  // registers through the collision for D3Q27) and k_step_list over the cells the handle listed
-  // (rules, wraps); the other D3Q27 half steps take the one-cell kernel
+  // registers through the collision for D3Q27) and the cells the handle listed (rules, wraps):
+  // a short list in extra z slices of the pair grid (no launch of its own: the 2:1 refined box's
+  // small FP16 lattices 69.5 -> 71.9 % of the copy bandwidth), a long one as k_step_list at its
+  // own occupancy (the D3Q27 bluff body's 1.5 M listed cells: 74.6 % against 73.0 % in the pair
+  // grid, whose 95 registers leave fewer warps for the latency-bound list).  The other D3Q27
+  // half steps take the one-cell kernel.
   if constexpr (sizeof(S) == 2 && (Q == 27 || LBM_SPLIT19) && LOAD == 2 && STORE == 2 && !STATS) {
     if (p.split && coll == 0) {
       dim3 g = L.grid;
       g.x = (p.nxp + 63) / 64;
+      const long long per = 128ll * g.x * g.y;  // listed cells per extra z slice
+      const long long extra = (p.nblist + per - 1) / per;
+      const bool fused = p.nblist <= LBM_LIST_FUSE_MAX && g.z + extra <= 65535;
+      if (fused) g.z += (unsigned)extra;
       if (closure == CL_NONE) k_step_h2<Q, S, CL_NONE, 2, 2, false, true><<<g, L.block, 0, L.stream>>>(p);
       else k_step_h2<Q, S, CL_SMAG, 2, 2, false, true><<<g, L.block, 0, L.stream>>>(p);
-      if (p.nblist > 0) {
+      if (!fused) {
         const unsigned nb = (unsigned)((p.nblist + 127) / 128);
         if (closure == CL_NONE) k_step_list<Q, S, CL_NONE><<<nb, 128, 0, L.stream>>>(p);
         else k_step_list<Q, S, CL_SMAG><<<nb, 128, 0, L.stream>>>(p);

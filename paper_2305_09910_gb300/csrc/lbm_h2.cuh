@@ -306,6 +306,9 @@ __device__ __forceinline__ void pair_pull(const KParams& p, int x, int y, int z,
   }
 }
 
+template <int Q, class S, int CL>
+__device__ __noinline__ void list_cell(const KParams& p, long long t);
+
 #ifndef LBM_H2_VEC
 #define LBM_H2_VEC 1
 #endif
@@ -317,6 +320,15 @@ __device__ __forceinline__ void pair_pull(const KParams& p, int x, int y, int z,
 template <int Q, class S, int CL, int LOAD, int STORE, bool STATS = false, bool SPLIT = false>
 __global__ void __launch_bounds__(128, Q == 27 ? LBM_H2_MINB27 : LBM_H2_MINB) k_step_h2(const __grid_constant__ KParams p) {
   static_assert(sizeof(S) == 2, "two 16-bit populations per word");
+  if constexpr (SPLIT) {
+    // blocks past the last z plane take the listed cells, 128 per block: they follow the pair
+    // blocks in launch order and fill the SMs the pair grid's tail leaves idle
+    if (blockIdx.z >= (unsigned)p.nz) {
+      const long long b = ((long long)(blockIdx.z - p.nz) * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+      list_cell<Q, S, CL>(p, b * 128 + threadIdx.y * 32 + threadIdx.x);
+      return;
+    }
+  }
   const int x = 2 * (blockIdx.x * 32 + threadIdx.x);
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
@@ -479,11 +491,10 @@ __device__ inline void list_source(const KParams& p, int x, int y, int z, int ce
   }
 }
 
-// One listed cell per thread: loads through the table, the collision of the storage
-// precision's form, own-cell store (the one-cell gather step's bits).
+// Listed cell t: loads through the table, the collision of the storage precision's form,
+// own-cell store (the one-cell gather step's bits).
 template <int Q, class S, int CL>
-__global__ void __launch_bounds__(128) k_step_list(const __grid_constant__ KParams p) {
-  const long long t = blockIdx.x * 128ll + threadIdx.x;
+__device__ __noinline__ void list_cell(const KParams& p, long long t) {
   if (t >= p.nblist) return;
   const int cell = p.blist[t];
   const S* base = plane_ptr<S>(p, 0);
@@ -501,6 +512,13 @@ __global__ void __launch_bounds__(128) k_step_list(const __grid_constant__ KPara
   const float rho = collide<Q, CL, float, acc_form<S>>(p, f, nullptr);
   if (!(rho > 0.f && rho < 3.0e38f)) atomicOr(p.status, 1);
   store_state<Q, S, 2>(p, 0, 0, 0, cell, CLS_BOUNDARY, f);
+}
+
+// The listed cells as a launch of their own (one per thread), for a list too long to follow the
+// x-pair grid in its z dimension.
+template <int Q, class S, int CL>
+__global__ void __launch_bounds__(128) k_step_list(const __grid_constant__ KParams p) {
+  list_cell<Q, S, CL>(p, blockIdx.x * 128ll + threadIdx.x);
 }
 
 }  // namespace lbm

@@ -1216,20 +1216,33 @@ __device__ __forceinline__ void stat_warp_store(const KParams& p, int y, int z, 
 }
 
 // Plane sums of the sampled statistics: sums[y * 10 + k] += sum over z and the nws warp
-// slots of each row (FP64).  One block per plane y.
+// slots of each row (FP64).  One block per plane y.  A thread sums its slots in FP32 with the
+// rounding error of every addition carried along (Knuth's TwoSum: hi + lo is the exact sum up
+// to the rounding of lo, about 2^-48 of it), then widens hi and lo once: FP64 arithmetic, which
+// is slow on this GPU, is left to the block's final reduction.
 static __global__ void __launch_bounds__(256) k_stats_total(const float* stats_w, int ny, int nz, int nws, double* sums) {
   const int y = blockIdx.x;
-  double acc[NSTAT];
+  float hi[NSTAT], lo[NSTAT];
 #pragma unroll
-  for (int k = 0; k < NSTAT; k++) acc[k] = 0.0;
+  for (int k = 0; k < NSTAT; k++) hi[k] = lo[k] = 0.f;
   const int n = nz * nws;  // below 2^31: a warp slot per 32 cells of a lattice under 2^31 cells
 #pragma unroll 4
   for (int r = threadIdx.x; r < n; r += blockDim.x) {
     const int z = r / nws, ws = r - z * nws;
     const float* src = stats_w + (((long long)z * ny + y) * nws + ws) * NSTAT;
 #pragma unroll
-    for (int k = 0; k < NSTAT; k++) acc[k] += (double)src[k];
+    for (int k = 0; k < NSTAT; k++) {
+      const float v = src[k];
+      const float s = __fadd_rn(hi[k], v);
+      const float bp = __fsub_rn(s, hi[k]);
+      const float err = __fadd_rn(__fsub_rn(hi[k], __fsub_rn(s, bp)), __fsub_rn(v, bp));
+      lo[k] = __fadd_rn(lo[k], err);
+      hi[k] = s;
+    }
   }
+  double acc[NSTAT];
+#pragma unroll
+  for (int k = 0; k < NSTAT; k++) acc[k] = (double)hi[k] + (double)lo[k];
   __shared__ double red[NSTAT][8];
 #pragma unroll
   for (int k = 0; k < NSTAT; k++) {

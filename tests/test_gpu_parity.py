@@ -496,6 +496,43 @@ def test_pull_and_aa_agree_bit_for_bit(precision, name, nx):
         assert np.array_equal(a.get_populations(), b.get_populations()), n
 
 
+def test_long_boundary_list_pull_matches_aa_bit_for_bit():
+    """The landing-gear tunnel at 512 x 160 x 160, D3Q27 FP16: its free-slip faces alone list
+    2 x 512 x 160 + 2 x 512 x 158 = 325,632 cells, more than a split pull step runs inside its
+    x-pair grid (2^18), so the listed cells get a launch of their own.  Six pull steps give the
+    bits of six AA (one-cell kernel) steps; populations compared on the device."""
+    import torch
+
+    from paper_2305_09910_gb300 import inputs, lbm
+
+    nx, ny, nz = 512, 160, 160
+    flags = torch.from_numpy(inputs.landing_gear_flags(nx, ny, nz, scale=nx / 768)).cuda()
+    u = torch.zeros((3, nz, ny, nx), dtype=torch.float32, device="cuda")
+    u[0] = 0.05
+    lats = []
+    for streaming in ("aa", "pull"):
+        lat = lbm.Lattice(nx, ny, nz, stencil=27, tau=0.52, precision="f16", closure="smag", cs_smag=0.1,
+                          faces=("inflow", "outflow", "freeslip", "freeslip", "freeslip", "freeslip"),
+                          u_inflow=(0.05, 0.0, 0.0), streaming=streaming)
+        lat.set_flags(flags)
+        lat.init_equilibrium(None, u)
+        lats.append(lat)
+    del u
+    a, b = lats
+    da = torch.empty((27, nz, ny, nx), dtype=torch.float32, device="cuda")
+    db = torch.empty_like(da)
+    for n in (1, 2, 3):
+        a.step(n)
+        b.step(n)
+        lbm.lbm_get_populations(a.h, da)
+        lbm.lbm_get_populations(b.h, db)
+        torch.cuda.synchronize()
+        assert torch.equal(da, db), n
+    for lat in lats:
+        lat.sync()
+        lat.close()
+
+
 @pytest.mark.parametrize("precision", ["f32", "f16", "bf16"])
 @pytest.mark.parametrize("streaming", ["aa", "pull"])
 @pytest.mark.parametrize("closure", ["smag", "mlp"])
