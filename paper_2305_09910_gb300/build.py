@@ -10,6 +10,7 @@ from __future__ import annotations
 import concurrent.futures as cf
 import hashlib
 import os
+import re
 import shutil
 import subprocess
 import sys
@@ -58,13 +59,22 @@ def _kernel_sources():
         [os.path.join(CSRC, "kern_inst.cu")]
 
 
+def _code_only(text: str) -> str:
+    """The source without its comments, trailing blanks and empty lines (the kernel sources hold
+    no comment markers inside string literals)."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    lines = (re.sub(r"//.*$", "", line).rstrip() for line in text.splitlines())
+    return "\n".join(line for line in lines if line)
+
+
 def kernel_digest(extra=()) -> str:
-    """Hash of the step kernels' sources and flags: ncu summaries taken on one build stay valid
-    for another with the same kernels (host-side API changes do not touch them)."""
+    """Hash of the step kernels' code (comments excluded) and flags: ncu summaries taken on one
+    build stay valid for another with the same kernels (host-side API changes and comment edits
+    do not touch them)."""
     h = hashlib.sha256()
     for path in _kernel_sources():
-        with open(path, "rb") as fh:
-            h.update(os.path.relpath(path, ROOT).encode() + b"\0" + fh.read())
+        with open(path, encoding="utf-8") as fh:
+            h.update(os.path.relpath(path, ROOT).encode() + b"\0" + _code_only(fh.read()).encode())
     h.update(" ".join(ARCH + NVFLAGS + list(extra)).replace(ROOT, ".").encode())
     return h.hexdigest()
 

@@ -514,8 +514,9 @@ __device__ __noinline__ void list_cell(const KParams& p, long long t) {
   store_state<Q, S, 2>(p, 0, 0, 0, cell, CLS_BOUNDARY, f);
 }
 
-// The listed cells as a launch of their own (one per thread), for a list too long to follow the
-// x-pair grid in its z dimension.
+// The listed cells as a launch of their own (one per thread), for a long list: above 2^18 cells
+// (it then runs at the list code's own occupancy rather than the x-pair kernel's), or too many
+// blocks to follow the x-pair grid in its z dimension.
 template <int Q, class S, int CL>
 __global__ void __launch_bounds__(128) k_step_list(const __grid_constant__ KParams p) {
   list_cell<Q, S, CL>(p, blockIdx.x * 128ll + threadIdx.x);

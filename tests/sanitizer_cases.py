@@ -1,7 +1,8 @@
 """Tiny lattices through every step, export and exchange kernel with every boundary type:
 D3Q19/D3Q27, FP32/FP16/BF16, AA and two-grid pull, TRT/MRT/Smagorinsky/learned closure,
 statistics sampled in the step, moments, sums, population export/import, z slabs with halo
-exchange, graph replays and the allocation-free sums.  Run against the bounds-checked library
+exchange, graph replays, a boundary list long enough for its own launch and the
+allocation-free sums.  Run against the bounds-checked library
 (``LBM_LIBRARY=.../liblbm_check.so python -m tests.sanitizer_cases``), every global access of
 these kernels is checked against its array and lbm_sync fails on any skipped access.  Not a
 pytest module (no test_ prefix): tests/test_gpu_bounds.py runs it."""
@@ -72,6 +73,18 @@ def run():
         digest.update(sl.get_populations().tobytes())
         sl.close()
         n += 1
+    # a boundary list too long to ride in the x-pair grid (D3Q27 FP16 pull tunnel with the
+    # landing gear: 325k cells on the free-slip faces alone), so the listed cells get their own launch
+    bx, by, bz = 512, 160, 160
+    lat = lbm.Lattice(bx, by, bz, stencil=27, tau=0.52, precision="f16", closure="smag", cs_smag=0.1,
+                      faces=TUNNEL, u_inflow=(0.05, 0, 0), streaming="pull")
+    lat.set_flags(inputs.landing_gear_flags(bx, by, bz, scale=bx / 768))
+    lat.init_equilibrium()
+    lat.step(3)
+    lat.sync()
+    digest.update(np.asarray(lat.reduce()).tobytes())
+    lat.close()
+    n += 1
     # the allocation-free sums read the caller's exported populations and flags
     import torch
 
