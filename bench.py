@@ -215,12 +215,13 @@ def _bluff_lattice(nx, ny, nz, precision, streaming="pull"):
     lat = lbm.Lattice(nx, ny, nz, stencil=27, tau=tau, precision=precision, closure="smag", cs_smag=0.1,
                       faces=("inflow", "outflow", "freeslip", "freeslip", "freeslip", "freeslip"),
                       u_inflow=(0.05, 0.0, 0.0), streaming=streaming)
-    lat.set_flags(torch.from_numpy(inputs.landing_gear_flags(nx, ny, nz, scale=scale)).cuda())
+    flags = inputs.landing_gear_flags(nx, ny, nz, scale=scale)
+    lat.set_flags(torch.from_numpy(flags).cuda())
     u = torch.zeros((3, nz, ny, nx), dtype=torch.float32, device="cuda")
     u[0] = 0.05
     lat.init_equilibrium(None, u)
     del u
-    return lat, {"tau": tau, "force": 0.0}
+    return lat, {"tau": tau, "force": 0.0, "fluid_cells": int((flags == 0).sum())}
 
 
 def _closure_params():
@@ -285,10 +286,16 @@ def _roofline(ncell, bytes_per_update, per_launch_ms, peak, peak_kind, traffic):
             "bytes_per_update": bytes_per_update, "avg_launch_ms": round(avg_s * 1e3, 4)}
 
 
-def _form_line(lat, nsteps, warmup, peak, peak_kind):
+def _form_line(lat, nsteps, warmup, peak, peak_kind, fluid=None):
+    """MLUPS over all cells (as the paper counts), MFLUPS over the fluid cells when some are
+    solid, and the HBM roofline of the mean launch."""
     ms, per = _time_steps(lat, nsteps, warmup, None)
-    return {"MLUPS": round(lat.ncell * nsteps / (ms * 1e-3) / 1e6, 1), "cells": lat.ncell,
-            "roofline": _roofline(lat.ncell, lat.bytes_per_update, per, peak, peak_kind, None)}
+    line = {"MLUPS": round(lat.ncell * nsteps / (ms * 1e-3) / 1e6, 1), "cells": lat.ncell}
+    if fluid is not None:
+        line["MFLUPS"] = round(fluid * nsteps / (ms * 1e-3) / 1e6, 1)
+        line["fluid_cells"] = int(fluid)
+    line["roofline"] = _roofline(lat.ncell, lat.bytes_per_update, per, peak, peak_kind, None)
+    return line
 
 
 def _extra_forms(nsteps, warmup, peak, peak_kind, sm_mhz):
@@ -327,7 +334,8 @@ def _extra_forms(nsteps, warmup, peak, peak_kind, sm_mhz):
         u[0] = 0.05
         lat.init_equilibrium(None, u)
         del u
-        out[f"bluffbody768_q27_{prec}"] = _form_line(lat, max(20, nsteps // 4), warmup, peak, peak_kind)
+        out[f"bluffbody768_q27_{prec}"] = _form_line(lat, max(20, nsteps // 4), warmup, peak, peak_kind,
+                                                     fluid=int((flags == 0).sum().item()))
         lat.close()
         torch.cuda.empty_cache()
     params = _closure_params()
@@ -406,7 +414,9 @@ def _small_form(streaming, nsteps=2000):
     lat.sync()
     us = t0.elapsed_time(t1) * 1e3 / nsteps
     lat.close()
-    return {"MLUPS": round(nx * ny * nz / us, 1), "us_per_step": round(us, 2), "steps": nsteps}
+    fluid = nx * (ny - 2) * nz  # rows y = 0 and ny - 1 are solid
+    return {"MLUPS": round(nx * ny * nz / us, 1), "MFLUPS": round(fluid / us, 1), "fluid_cells": fluid,
+            "us_per_step": round(us, 2), "steps": nsteps}
 
 
 def _refined_form(nsteps, warmup, peak, peak_kind, precision="f32"):
@@ -578,6 +588,8 @@ def main():
     clock_summary = clocks.summary()
     total_ms = _barrier_max(dist, total_ms)
     value = world * ncell * args.steps / (total_ms * 1e-3) / 1e6
+    fluid = ncell if channel else par["fluid_cells"]  # the channel's walls are faces: every cell is fluid
+    mflups = world * fluid * args.steps / (total_ms * 1e-3) / 1e6
     q = 19 if channel else 27
     coll = "" if args.collision == "trt" else f"_{args.collision}"
     tag = f"k_step_q{q}_{args.form}_{args.closure}{coll}_{args.streaming}_{args.workload}{nx}"
@@ -661,7 +673,7 @@ def main():
                       "stats": ("mean/RMS profile sample (FP64 plane sums) every 10 steps, taken by the step kernel, "
                                 "inside the timed region") if channel else "none",
                       "l2": f"inputs larger than L2 ({lat_bytes / 1e9:.2f} GB population array vs 129 MB L2)"},
-           "roofline": roof, "e2e": e2e, "gpu_launches": launches,
+           "mflups": round(mflups, 1), "roofline": roof, "e2e": e2e, "gpu_launches": launches,
            "clocks": clock_summary, "mass_after": mass, "forms": forms}
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = _cpu_baseline()
