@@ -35,8 +35,8 @@ struct lbm_s {
   int* status_host = nullptr; // pinned copy
   double* sums = nullptr;     // 4 doubles (lbm_reduce)
   double* partial = nullptr;  // nz * ny * 10 doubles: per-row sums of the reductions
-  float* stats_w = nullptr;   // per-warp plane statistics of sampling steps (allocated on first use)
-  int* blist = nullptr;       // cells the x-pair step leaves to k_step_list (see uses_blist)
+  float* stats_w = nullptr;   // per-warp plane statistics of sampling steps (see ensure_stats_w)
+  int* blist = nullptr;       // cells the x-pair step leaves to the list code (see uses_blist)
   void* blaux = nullptr;      // their source table: q x nblist cells (int32), then q x nblist codes
   long long nblist = 0;
   // CUDA graph of GRAPH_STEPS plain steps that lbm_step replays (captured on a private
@@ -472,13 +472,15 @@ int lbm_stencil(int q, int* c, double* w) {
 
 const char* lbm_last_error(lbm_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
-// Handles whose pull step splits into the x-pair kernel over interior cells and k_step_list over
-// the listed ones: half storage, two-grid pull, TRT without the learned closure, D3Q27 (where
-// the warps that hold a boundary lane would otherwise diverge through its boundary loads;
-// measured 32.2k MLUPS one-cell vs 30.0k unsplit pairs on the bluff body, 43.7k split).
+// Handles whose pull step splits into the x-pair kernel over interior cells and the list code
+// over the listed ones: half storage, two-grid pull, TRT without the learned closure, both
+// stencils (the warps that hold a boundary lane would otherwise diverge through its boundary
+// loads; D3Q27 bluff body 32.2k MLUPS one-cell, 30.0k unsplit pairs, 43.7k split; D3Q19 FP16
+// channel 65.1k unsplit, 67.4k split).
 static bool uses_blist(const lbm_s* h) { return kparams(h).split != 0; }
 
-// The list of cells needing rules or a y/z wrap, in row order (rebuilt with the classes).
+// The list of cells needing rules or a y/z wrap, in row order, and its source table (rebuilt
+// with the classes).
 static lbm_status build_blist(lbm_handle h) {
   if (h->blist) CUDA_TRY(h, cudaFreeAsync(h->blist, h->stream));
   if (h->blaux) CUDA_TRY(h, cudaFreeAsync(h->blaux, h->stream));
@@ -785,8 +787,6 @@ lbm_status lbm_set_populations(lbm_handle h, const float* df, int on_device) {
 static lbm_status run_export(lbm_handle h, int mode, const ExportArgs& a, bool raw = false);
 static void advance_state(lbm_handle h);
 
-// n steps; with every > 0 the plane statistics of the state each step k (k % every == 0)
-// starts from are added to the accumulated sums, inside that step's kernel where it can.
 // The per-warp scratch of sampling steps; lbm_stats_reset allocates it ahead of the steps (the
 // first allocation from the stream-ordered pool maps memory, which takes a while).
 static lbm_status ensure_stats_w(lbm_handle h) {
@@ -796,6 +796,8 @@ static lbm_status ensure_stats_w(lbm_handle h) {
   return LBM_OK;
 }
 
+// n steps; with every > 0 the plane statistics of the state each step k (k % every == 0)
+// starts from are added to the accumulated sums, inside that step's kernel where it can.
 static lbm_status run_steps(lbm_handle h, int64_t n, int64_t every) {
   if (h->prm.closure == LBM_CLOSURE_MLP && !h->mlp_set)
     return fail(h, LBM_ESTATE, "MLP closure selected but lbm_set_closure was not called");
