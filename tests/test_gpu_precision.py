@@ -2,8 +2,8 @@
 
 The perturbed channel (Re_tau ~ 180, walls at the y faces, Smagorinsky C_s = 0.1) is run
 for 300 steps from the same initial fields by the FP64 oracle and by the GPU with float32,
-float16-shifted and bfloat16-shifted populations (float32 arithmetic in every case).  For
-each form the test states (prints) and bounds:
+float16-shifted and bfloat16-shifted populations (float32 arithmetic in every case), each in
+AA and in two-grid pull streaming.  For each form the test states (prints) and bounds:
   * the largest population error against the oracle,
   * the relative errors of the mean u_x and RMS velocity profiles (x-z plane statistics),
   * the relative drift of the total mass (FP64 sums on the GPU).
@@ -55,31 +55,36 @@ def test_precision_forms_against_oracle():
     ref_mean, ref_rms = _profiles(ur)
     ref_df = ora.shifted()
     report = {}
-    for prec, (b_pop, b_mean, b_rms, b_mass) in BOUNDS.items():
-        lat = lbm.Lattice(nx, ny, nz, stencil=19, tau=par["tau"], precision=prec, closure="smag",
-                          cs_smag=0.1, faces=FACES_CHANNEL)
-        lat.set_force(par["force"])
-        lat.init_equilibrium(rho, u)
-        g0 = lat.reduce()[0]
-        lat.step(STEPS)
-        lat.sync()
-        _, ug = lat.moments()
-        mean, rms = _profiles(ug.astype(np.float64))
-        pop = float(np.abs(lat.get_populations() - ref_df).max())
-        e_mean = float(np.linalg.norm(mean - ref_mean) / np.linalg.norm(ref_mean))
-        e_rms = float(np.linalg.norm(rms - ref_rms) / np.linalg.norm(ref_rms))
-        drift = float(abs(lat.reduce()[0] - g0) / g0)
-        report[prec] = {"pop_err": pop, "mean_profile_err": e_mean, "rms_profile_err": e_rms,
-                        "mass_drift": drift}
-        lat.close()
+    # AA in place (one-cell kernel / x-pairs) and two-grid pull (the half forms: the split step,
+    # x-pairs with the wall rows and periodic z planes as listed cells)
+    for streaming in ("aa", "pull"):
+        for prec in BOUNDS:
+            lat = lbm.Lattice(nx, ny, nz, stencil=19, tau=par["tau"], precision=prec, closure="smag",
+                              cs_smag=0.1, faces=FACES_CHANNEL, streaming=streaming)
+            lat.set_force(par["force"])
+            lat.init_equilibrium(rho, u)
+            g0 = lat.reduce()[0]
+            lat.step(STEPS)
+            lat.sync()
+            _, ug = lat.moments()
+            mean, rms = _profiles(ug.astype(np.float64))
+            pop = float(np.abs(lat.get_populations() - ref_df).max())
+            e_mean = float(np.linalg.norm(mean - ref_mean) / np.linalg.norm(ref_mean))
+            e_rms = float(np.linalg.norm(rms - ref_rms) / np.linalg.norm(ref_rms))
+            drift = float(abs(lat.reduce()[0] - g0) / g0)
+            report[f"{prec}/{streaming}"] = {"pop_err": pop, "mean_profile_err": e_mean, "rms_profile_err": e_rms,
+                                             "mass_drift": drift}
+            lat.close()
     report["oracle_mass_drift"] = float(abs(ora.mass_momentum()[0] - m0) / m0)
     print("precision forms vs FP64 oracle after", STEPS, "steps:", report)
-    for prec, (b_pop, b_mean, b_rms, b_mass) in BOUNDS.items():
-        r = report[prec]
-        assert r["pop_err"] <= b_pop, (prec, r)
-        assert r["mean_profile_err"] <= b_mean, (prec, r)
-        assert r["rms_profile_err"] <= b_rms, (prec, r)
-        assert r["mass_drift"] <= b_mass, (prec, r)
+    for key, r in report.items():
+        if "/" not in key:
+            continue
+        b_pop, b_mean, b_rms, b_mass = BOUNDS[key.split("/")[0]]
+        assert r["pop_err"] <= b_pop, (key, r)
+        assert r["mean_profile_err"] <= b_mean, (key, r)
+        assert r["rms_profile_err"] <= b_rms, (key, r)
+        assert r["mass_drift"] <= b_mass, (key, r)
 
 
 # Bluff-body sub-case: D3Q27, 96 x 48 x 48 with the landing-gear geometry scaled by 1/8, inflow
@@ -117,23 +122,26 @@ def test_bluff_body_precision_forms_against_oracle():
     ref_df = ora.shifted()
     m_ref = ora.mass_momentum()[0]
     report = {}
-    for prec in BLUFF_BOUNDS:
-        lat = lbm.Lattice(nx, ny, nz, stencil=27, tau=tau, precision=prec, closure="smag", cs_smag=0.1,
-                          faces=faces, u_inflow=(0.05, 0, 0))
-        lat.set_flags(flags)
-        lat.init_equilibrium(None, u0.astype(np.float32))
-        lat.step(steps)
-        lat.sync()
-        _, ug = lat.moments()
-        report[prec] = {
-            "pop_err": float(np.abs(lat.get_populations() - ref_df).max()),
-            "u_rel_err": float(np.linalg.norm(ug - ur) / np.linalg.norm(ur)),
-            "mass_rel_diff": float(abs(lat.reduce()[0] - m_ref) / m_ref),
-        }
-        lat.close()
+    # AA (one-cell kernel) and two-grid pull (the half forms: the split step, x-pairs and the
+    # listed boundary cells read through their source table)
+    for streaming in ("aa", "pull"):
+        for prec in BLUFF_BOUNDS:
+            lat = lbm.Lattice(nx, ny, nz, stencil=27, tau=tau, precision=prec, closure="smag", cs_smag=0.1,
+                              faces=faces, u_inflow=(0.05, 0, 0), streaming=streaming)
+            lat.set_flags(flags)
+            lat.init_equilibrium(None, u0.astype(np.float32))
+            lat.step(steps)
+            lat.sync()
+            _, ug = lat.moments()
+            report[f"{prec}/{streaming}"] = {
+                "pop_err": float(np.abs(lat.get_populations() - ref_df).max()),
+                "u_rel_err": float(np.linalg.norm(ug - ur) / np.linalg.norm(ur)),
+                "mass_rel_diff": float(abs(lat.reduce()[0] - m_ref) / m_ref),
+            }
+            lat.close()
     print("bluff-body precision forms vs FP64 oracle after", steps, "steps:", report)
-    for prec, (b_pop, b_u, b_m) in BLUFF_BOUNDS.items():
-        r = report[prec]
-        assert r["pop_err"] <= b_pop, (prec, r)
-        assert r["u_rel_err"] <= b_u, (prec, r)
-        assert r["mass_rel_diff"] <= b_m, (prec, r)
+    for key, r in report.items():
+        b_pop, b_u, b_m = BLUFF_BOUNDS[key.split("/")[0]]
+        assert r["pop_err"] <= b_pop, (key, r)
+        assert r["u_rel_err"] <= b_u, (key, r)
+        assert r["mass_rel_diff"] <= b_m, (key, r)
