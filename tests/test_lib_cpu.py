@@ -145,3 +145,20 @@ def test_sample_cells_distinct_sorted():
 
     c = inputs.sample_cells(10 ** 6, 300)
     assert c.size == 300 and np.all(np.diff(c) > 0) and c.min() >= 0 and c.max() < 10 ** 6
+
+
+def test_kernel_digest_ignores_comments_and_sees_code(tmp_path, monkeypatch):
+    """The digest that gates the committed ncu summaries: unchanged by comment and blank-line
+    edits of the kernel sources, changed by any change of their code."""
+    from paper_2305_09910_gb300 import build
+
+    assert build._code_only("a = 1; // note\n\n/* block\n comment */ b = 2;  \n") == "a = 1;\n  b = 2;"
+    src = tmp_path / "k.cuh"
+    monkeypatch.setattr(build, "_kernel_sources", lambda: [str(src)])
+    src.write_text("int f(int x) {\n  return x + 1;  // add one\n}\n")
+    d0 = build.kernel_digest()
+    src.write_text("// a header comment\nint f(int x) {\n\n  return x + 1;  /* add one */\n}\n")
+    assert build.kernel_digest() == d0
+    src.write_text("int f(int x) {\n  return x + 2;\n}\n")
+    assert build.kernel_digest() != d0
+    assert build.kernel_digest(extra=("-DX",)) != build.kernel_digest()
