@@ -4,7 +4,8 @@ The paper's channel assesses the symmetry and regularity of the solution and the
 stresses along the wall normal.  No DNS data are available here, so the FP64 plane
 statistics of a developed turbulent run (Re_tau = 180, 256 x 128 x 128, D3Q19 TRT +
 Smagorinsky, two-grid pull with the statistics sampled inside the step kernel, as in the
-benchmark) are checked against what the equations themselves fix:
+benchmark; FP32 storage, and FP16-shifted storage through the split half-storage step) are
+checked against what the equations themselves fix:
 
 * the flow is turbulent: the streamwise RMS peak lies between 2 and 3.5 u_tau and the wall-
   normal one between 0.5 and 1.3 u_tau (channel-flow values are about 2.7 and 0.9);
@@ -16,7 +17,8 @@ benchmark) are checked against what the equations themselves fix:
 Tolerances: the averages cover 100k steps (10 eddy turnovers delta / u_tau, 10,000 samples
 of 32,768-cell planes).  Over 20k-step windows the same quantities fluctuated by symmetry
 2-6 %, stress-line residual 5-14 % of g delta, slope 0.87-1.02 g and wall u_tau 0.90-0.95
-sqrt(g delta) (the unresolved Smagorinsky stress, about 8 % of the wall stress at this
+sqrt(g delta); over the 100k steps FP32 gave 0.016 / 0.073 / 0.949 / 0.938 and FP16
+0.022 / 0.080 / 0.931 / 0.933 (the unresolved Smagorinsky stress, about 8 % of the wall stress at this
 resolution, is not in the statistics).
 """
 import numpy as np
@@ -25,7 +27,8 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 
-def test_turbulent_channel_statistics_are_self_consistent():
+@pytest.mark.parametrize("precision", ["f32", "f16"])
+def test_turbulent_channel_statistics_are_self_consistent(precision):
     import torch
 
     from paper_2305_09910_gb300 import build, closure, inputs, lbm
@@ -35,7 +38,8 @@ def test_turbulent_channel_statistics_are_self_consistent():
     nx, ny, nz, ub = 256, 128, 128, 0.1
     par = inputs.channel_parameters(ny, u_bulk=ub)
     nu, g, delta, utau = (par["tau"] - 0.5) / 3, par["force"], par["delta"], par["u_tau"]
-    lat = closure.channel(nx, ny, nz, closure="smag", cs0=0.1, u_bulk=ub, amp=0.5, streaming="pull")
+    lat = closure.channel(nx, ny, nz, closure="smag", cs0=0.1, u_bulk=ub, amp=0.5, streaming="pull",
+                          precision=precision)
     lat.step(60000)
     lbm.lbm_stats_reset(lat.h)
     lbm.lbm_step_stats(lat.h, 100000, 10)
@@ -61,7 +65,7 @@ def test_turbulent_channel_statistics_are_self_consistent():
         return (2.25 * u0 - 0.25 * u1) / 0.75
 
     utau_wall = float(np.sqrt(nu * 0.5 * (grad(u[0], u[1]) + grad(u[-1], u[-2]))) / np.sqrt(g * delta))
-    print(f"channel statistics: u'/u_tau {rms.round(3).tolist()}, symmetry {sym:.3f}, stress-line residual "
+    print(f"channel statistics ({precision}): u'/u_tau {rms.round(3).tolist()}, symmetry {sym:.3f}, stress-line residual "
           f"{resid:.3f} g delta, slope {slope:.3f} g, wall u_tau {utau_wall:.3f} sqrt(g delta), "
           f"bulk velocity {u.mean():.4f}")
     assert 2.0 <= rms[0] <= 3.5 and 0.5 <= rms[1] <= 1.3
