@@ -599,7 +599,9 @@ def main():
     lat_bytes = ncell * q * lat.bytes_per_pop
     nsample = (args.steps + 9) // 10 if channel else 0
     # our kernel launches in the timed region: one per step, plus per statistics sample the
-    # plane-sum pass (fused sampling) or the two reduction kernels (learned closure)
+    # plane-sum pass (fused sampling) or the two reduction kernels (learned closure).  (With
+    # --form f16/bf16 a pull step whose boundary list exceeds 2^18 cells launches the list on
+    # its own; the default FP32 line never does.)
     launches = args.steps + (2 * nsample if args.closure == "mlp" else nsample)
 
     # end to end through the C ABI with host buffers: upload (rho, u) from pinned memory,
