@@ -1209,8 +1209,8 @@ __device__ __forceinline__ void stat_warp_store(const KParams& p, int y, int z, 
   const float s = d[0] + __shfl_xor_sync(0xffffffffu, d[0], 1);
   const int lane = threadIdx.x & 31;
   const int b1 = (lane >> 1) & 1, b2 = (lane >> 2) & 1, b3 = (lane >> 3) & 1, b4 = (lane >> 4) & 1;
-  const int j = b1 + 2 * b2;  // slot after round 2 (3 values)
-  const int k = j + 3 * b3;   // slot after round 1 (5 values)
+  const int j = b1 + 2 * b2;  // slot after the second exchange (3 values)
+  const int k = j + 3 * b3;   // slot after the first exchange (5 values)
   if (!(lane & 1) && j < 3 && k < 5)
     p.stats_w[(((long long)z * p.ny + y) * nws + ws) * NSTAT + k + 5 * b4] = s;
 }
